@@ -1,0 +1,300 @@
+"""ctypes front end of the FP64 CPU oracle (``amg_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the CPU-baseline
+leg of the benchmark use this module.  The GPU library never imports it.
+
+``build()`` compiles the C oracle with ``-O2 -ffp-contract=off`` (no fused
+multiply-add, so every operation is rounded exactly as written).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "amg_oracle.c")
+LIB = os.path.join(HERE, "_build", "libamg_oracle.so")
+
+_i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+_u32p = np.ctypeslib.ndpointer(dtype=np.uint32, flags="C_CONTIGUOUS")
+_i8p = np.ctypeslib.ndpointer(dtype=np.int8, flags="C_CONTIGUOUS")
+_u8p = np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS")
+_f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+
+
+class ORParams(C.Structure):
+    _fields_ = [
+        ("alpha", C.c_double),
+        ("seed", C.c_uint64),
+        ("coarse_max", C.c_int32),
+        ("max_levels", C.c_int32),
+        ("kcycle_levels", C.c_int32),
+        ("kcycle_t", C.c_double),
+        ("omega_mode", C.c_int32),
+        ("omega", C.c_double),
+        ("outer", C.c_int32),
+        ("restart", C.c_int32),
+        ("smoother", C.c_int32),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library (idempotent)."""
+    os.makedirs(os.path.dirname(LIB), exist_ok=True)
+    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= max(
+            os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "amg_oracle.h"))):
+        return LIB
+    tmp = LIB + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+                           "-shared", "-o", tmp, SRC, "-lm"])
+    os.replace(tmp, LIB)
+    return LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(LIB)
+        L.or_strength.argtypes = [C.c_int32, _i32p, _i32p, _f64p, C.c_double, _u8p]
+        L.or_col_count.argtypes = [C.c_int32, _i32p, _i32p, _u8p, _i32p]
+        L.or_sym_graph.argtypes = [C.c_int32, _i32p, _i32p, _u8p, _i32p, C.c_void_p, C.c_int64]
+        L.or_sym_graph.restype = C.c_int64
+        L.or_mis_hash.argtypes = [C.c_uint64, C.c_int32, C.c_int32]
+        L.or_mis_hash.restype = C.c_uint32
+        L.or_splitmix64.argtypes = [C.c_uint64]
+        L.or_splitmix64.restype = C.c_uint64
+        L.or_pmis2.argtypes = [C.c_int32, _i32p, _i32p, _i32p, _u32p, _i8p]
+        L.or_pmis2.restype = C.c_int32
+        L.or_aggregate.argtypes = [C.c_int32, _i32p, _i32p, _i32p, _u32p, _i8p, _i32p]
+        L.or_aggregate.restype = C.c_int32
+        L.or_interp.argtypes = [C.c_int32, C.c_int32, _i32p, _f64p, _f64p, _f64p]
+        L.or_galerkin.argtypes = [C.c_int32, _i32p, _i32p, _f64p, C.c_int32, _i32p, C.c_void_p, _i32p,
+                                  C.c_void_p, C.c_void_p, C.c_int64]
+        L.or_galerkin.restype = C.c_int64
+        L.or_rho_estimate.argtypes = [C.c_int32, _i32p, _i32p, _f64p, C.c_uint64, C.c_int32, C.c_int32,
+                                      C.c_void_p]
+        L.or_rho_estimate.restype = C.c_double
+        L.or_sym_eig.argtypes = [C.c_int32, _f64p, _f64p]
+        L.or_cholesky.argtypes = [C.c_int32, _f64p]
+        L.or_cholesky.restype = C.c_int32
+        L.or_chol_solve.argtypes = [C.c_int32, _f64p, _f64p]
+        L.or_default_params.argtypes = [C.POINTER(ORParams)]
+        L.or_setup.argtypes = [C.c_int32, _i32p, _i32p, _f64p, C.POINTER(ORParams), C.POINTER(C.c_int32)]
+        L.or_setup.restype = C.c_void_p
+        L.or_nlevels.argtypes = [C.c_void_p]
+        L.or_nlevels.restype = C.c_int32
+        L.or_level_info.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int64),
+                                    C.POINTER(C.c_double), C.POINTER(C.c_int32)]
+        L.or_level_copy.argtypes = [C.c_void_p, C.c_int32] + [C.c_void_p] * 6
+        L.or_set_poly.argtypes = [C.c_void_p, C.c_int32, _f64p]
+        L.or_set_poly.restype = C.c_int32
+        L.or_precond.argtypes = [C.c_void_p, _f64p, _f64p]
+        L.or_solve.argtypes = [C.c_void_p, _f64p, _f64p, C.c_double, C.c_int32, C.POINTER(C.c_int32), _f64p,
+                               C.POINTER(C.c_double)]
+        L.or_solve.restype = C.c_int32
+        L.or_free.argtypes = [C.c_void_p]
+        L.or_krylov2_probe.argtypes = [C.c_void_p, C.c_int32, _f64p, _f64p, _f64p, _f64p]
+        L.or_krylov2_probe.restype = C.c_int32
+        _lib = L
+    return _lib
+
+
+def _csr_args(A):
+    return (int(A.n), np.ascontiguousarray(A.rowptr, np.int32), np.ascontiguousarray(A.col, np.int32),
+            np.ascontiguousarray(A.val, np.float64))
+
+
+# ---------------------------------------------------------------- setup steps
+def strength(A, alpha: float) -> np.ndarray:
+    n, rp, ci, v = _csr_args(A)
+    Cm = np.zeros(max(A.nnz, 1), np.uint8)
+    lib().or_strength(n, rp, ci, v, alpha, Cm)
+    return Cm[:A.nnz]
+
+
+def col_count(A, Cm: np.ndarray) -> np.ndarray:
+    n, rp, ci, _ = _csr_args(A)
+    cnt = np.zeros(n, np.int32)
+    lib().or_col_count(n, rp, ci, np.ascontiguousarray(Cm, np.uint8), cnt)
+    return cnt
+
+
+def sym_graph(A, Cm: np.ndarray):
+    n, rp, ci, _ = _csr_args(A)
+    Cm = np.ascontiguousarray(Cm, np.uint8)
+    Sptr = np.zeros(n + 1, np.int32)
+    ns = lib().or_sym_graph(n, rp, ci, Cm, Sptr, None, 0)
+    Scol = np.zeros(max(ns, 1), np.int32)
+    lib().or_sym_graph(n, rp, ci, Cm, Sptr, Scol.ctypes.data, ns)
+    return Sptr, Scol[:ns]
+
+
+def mis_hash(seed: int, level: int, n: int) -> np.ndarray:
+    L = lib()
+    return np.array([L.or_mis_hash(seed, level, i) for i in range(n)], dtype=np.uint32)
+
+
+def splitmix64(x: int) -> int:
+    return int(lib().or_splitmix64(x))
+
+
+def pmis2(Sptr, Scol, count, h):
+    n = len(Sptr) - 1
+    s = np.zeros(n, np.int8)
+    Scol = np.ascontiguousarray(Scol, np.int32) if len(Scol) else np.zeros(1, np.int32)
+    rounds = lib().or_pmis2(n, np.ascontiguousarray(Sptr, np.int32), Scol, np.ascontiguousarray(count, np.int32),
+                            np.ascontiguousarray(h, np.uint32), s)
+    return s, rounds
+
+
+def aggregate(Sptr, Scol, count, h, s):
+    n = len(Sptr) - 1
+    agg = np.zeros(n, np.int32)
+    Scol = np.ascontiguousarray(Scol, np.int32) if len(Scol) else np.zeros(1, np.int32)
+    nc = lib().or_aggregate(n, np.ascontiguousarray(Sptr, np.int32), Scol, np.ascontiguousarray(count, np.int32),
+                            np.ascontiguousarray(h, np.uint32), np.ascontiguousarray(s, np.int8), agg)
+    return agg, nc
+
+
+def interp(agg, nc: int, B):
+    n = len(agg)
+    P = np.zeros(n)
+    Bc = np.zeros(max(nc, 1))
+    lib().or_interp(n, nc, np.ascontiguousarray(agg, np.int32), np.ascontiguousarray(B, np.float64), P, Bc)
+    return P, Bc[:nc]
+
+
+def galerkin(A, agg, nc: int, P=None):
+    from paper_1403_1649_gb300.problems import CSR
+    n, rp, ci, v = _csr_args(A)
+    agg = np.ascontiguousarray(agg, np.int32)
+    Pp = None if P is None else np.ascontiguousarray(P, np.float64)
+    crp = np.zeros(nc + 1, np.int32)
+    L = lib()
+    cn = L.or_galerkin(n, rp, ci, v, nc, agg, None if Pp is None else Pp.ctypes.data, crp, None, None, 0)
+    cci = np.zeros(max(cn, 1), np.int32)
+    cval = np.zeros(max(cn, 1))
+    L.or_galerkin(n, rp, ci, v, nc, agg, None if Pp is None else Pp.ctypes.data, crp, cci.ctypes.data,
+                  cval.ctypes.data, cn)
+    return CSR(nc, crp, cci[:cn], cval[:cn])
+
+
+def rho_estimate(A, seed: int = 0, level: int = 0, m: int = 5):
+    n, rp, ci, v = _csr_args(A)
+    H = np.zeros(64)
+    rho = lib().or_rho_estimate(n, rp, ci, v, seed, level, m, H.ctypes.data)
+    mm = min(m, n)
+    return rho, H[:mm * mm].reshape(mm, mm)
+
+
+def sym_eig(a: np.ndarray) -> np.ndarray:
+    a = np.ascontiguousarray(a, np.float64)
+    w = np.zeros(a.shape[0])
+    lib().or_sym_eig(a.shape[0], a.reshape(-1), w)
+    return w
+
+
+def cholesky(a: np.ndarray):
+    L = np.ascontiguousarray(a, np.float64).copy()
+    rc = lib().or_cholesky(L.shape[0], L.reshape(-1))
+    return (L if rc == 0 else None)
+
+
+def chol_solve(L: np.ndarray, b: np.ndarray) -> np.ndarray:
+    x = np.ascontiguousarray(b, np.float64).copy()
+    lib().or_chol_solve(L.shape[0], np.ascontiguousarray(L).reshape(-1), x)
+    return x
+
+
+# ------------------------------------------------------------ whole method
+@dataclass
+class Level:
+    n: int
+    nnz: int
+    omega: float
+    mis_rounds: int
+    rowptr: np.ndarray
+    col: np.ndarray
+    val: np.ndarray
+    agg: np.ndarray | None = None
+    P: np.ndarray | None = None
+    B: np.ndarray | None = None
+
+
+def default_params(**kw) -> ORParams:
+    p = ORParams()
+    lib().or_default_params(C.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+class Hierarchy:
+    """Aggregation AMG hierarchy (Alg. 1) and its solve phase, on the CPU in FP64."""
+
+    def __init__(self, A, **params):
+        self.params = default_params(**params)
+        n, rp, ci, v = _csr_args(A)
+        err = C.c_int32(0)
+        self.h = lib().or_setup(n, rp, ci, v, C.byref(self.params), C.byref(err))
+        if not self.h:
+            raise RuntimeError(f"oracle setup failed: {err.value}")
+        self.n = n
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().or_free(self.h)
+            self.h = None
+
+    @property
+    def nlevels(self) -> int:
+        return lib().or_nlevels(self.h)
+
+    def level(self, k: int) -> Level:
+        n, nnz, om, mr = C.c_int32(), C.c_int64(), C.c_double(), C.c_int32()
+        lib().or_level_info(self.h, k, C.byref(n), C.byref(nnz), C.byref(om), C.byref(mr))
+        n, nnz = n.value, nnz.value
+        rp = np.zeros(n + 1, np.int32)
+        ci = np.zeros(max(nnz, 1), np.int32)
+        val = np.zeros(max(nnz, 1))
+        last = k == self.nlevels - 1
+        agg = None if last else np.zeros(n, np.int32)
+        P = None if last else np.zeros(n)
+        B = np.zeros(n)
+        lib().or_level_copy(self.h, k, rp.ctypes.data, ci.ctypes.data, val.ctypes.data,
+                            None if last else agg.ctypes.data, None if last else P.ctypes.data, B.ctypes.data)
+        return Level(n, nnz, om.value, mr.value, rp, ci[:nnz], val[:nnz], agg, P, B)
+
+    def set_poly(self, k: int, coef: np.ndarray) -> None:
+        coef = np.ascontiguousarray(coef, np.float64).reshape(-1)
+        if lib().or_set_poly(self.h, k, coef) != 0:
+            raise ValueError("bad level for polynomial smoother")
+
+    def precond(self, b: np.ndarray) -> np.ndarray:
+        x = np.zeros(self.n)
+        lib().or_precond(self.h, np.ascontiguousarray(b, np.float64), x)
+        return x
+
+    def krylov2_probe(self, m: int, r: np.ndarray):
+        n = self.level(m).n
+        x, c, d = np.zeros(n), np.zeros(n), np.zeros(n)
+        if lib().or_krylov2_probe(self.h, m, np.ascontiguousarray(r, np.float64), x, c, d) != 0:
+            raise ValueError("level has no K-cycle coarse part")
+        return x, c, d
+
+    def solve(self, b: np.ndarray, x0: np.ndarray | None = None, tol: float = 1e-8, max_iter: int = 200):
+        x = np.zeros(self.n) if x0 is None else np.ascontiguousarray(x0, np.float64).copy()
+        hist = np.zeros(max_iter + 2)
+        it = C.c_int32()
+        fr = C.c_double()
+        st = lib().or_solve(self.h, np.ascontiguousarray(b, np.float64), x, tol, max_iter, C.byref(it), hist,
+                            C.byref(fr))
+        return x, {"status": st, "iters": it.value, "hist": hist[:it.value + 1].copy(), "relres": fr.value}

@@ -1,0 +1,511 @@
+"""Pins of the FP64 CPU oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: a value the
+paper prints (the Sec. 3.1 worked example, Table 1's level-0 size), a closed form
+(the spectrum of the 1D/2D Laplacian), a different algorithm with a provably
+identical result (greedy MIS on the square graph), a library routine on a special
+case (numpy dense products, eigvalsh, solve), or an invariant that a plausible
+mistake would break.
+"""
+import os
+from collections import deque
+
+import numpy as np
+import pytest
+
+from paper_1403_1649_gb300 import problems as P
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------- helpers
+def csr_from_rows(rows: dict, n: int, vals: dict):
+    rp = [0]
+    ci, va = [], []
+    for i in range(n):
+        for j in sorted(rows[i]):
+            ci.append(j)
+            va.append(vals[(i, j)])
+        rp.append(len(ci))
+    return P.CSR(n, np.array(rp, np.int32), np.array(ci, np.int32), np.array(va, np.float64))
+
+
+def adjacency(Sptr, Scol):
+    n = len(Sptr) - 1
+    return [set(Scol[Sptr[i]:Sptr[i + 1]].tolist()) for i in range(n)]
+
+
+def bfs_dist(adj, src, cap=3):
+    dist = {src: 0}
+    dq = deque([src])
+    while dq:
+        u = dq.popleft()
+        if dist[u] >= cap:
+            continue
+        for v in adj[u]:
+            if v not in dist:
+                dist[v] = dist[u] + 1
+                dq.append(v)
+    return dist
+
+
+def random_sym_graph(n, deg, seed):
+    rng = np.random.default_rng(seed)
+    adj = [set() for _ in range(n)]
+    for _ in range(n * deg // 2):
+        a, b = rng.integers(0, n, 2)
+        if a != b:
+            adj[a].add(int(b))
+            adj[b].add(int(a))
+    Sptr = np.zeros(n + 1, np.int32)
+    cols = []
+    for i in range(n):
+        cols.extend(sorted(adj[i]))
+        Sptr[i + 1] = len(cols)
+    return Sptr, np.array(cols, np.int32), adj
+
+
+# ----------------------------------------------------------------- strength
+def test_strength_1d_poisson_all_offdiag_strong(oracle_mod):
+    A = P.poisson1d(7)
+    Cm = oracle_mod.strength(A, 0.25)
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    assert np.array_equal(Cm.astype(bool), rows != A.col)
+
+
+def test_strength_anisotropic_keeps_only_strong_direction(oracle_mod):
+    # -u_xx - 0.1 u_yy: |a_y| = 0.1 < 0.25 * |a_x| = 0.25, so only x-neighbours are strong
+    m = 6
+    A = P.aniso2d(m, 0.1)
+    Cm = oracle_mod.strength(A, 0.25)
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    dx = np.abs(A.col - rows)
+    assert np.array_equal(Cm.astype(bool), dx == 1)
+    # with alpha = 0.05 the y-connections (0.1 > 0.05) become strong too
+    Cm2 = oracle_mod.strength(A, 0.05)
+    assert np.array_equal(Cm2.astype(bool), rows != A.col)
+
+
+def test_strength_signs_and_strict_threshold(oracle_mod):
+    # row 0: positive diagonal; -A_01 = -1 < 0 (not strong), -A_02 = 2 strong,
+    #        -A_03 = 0.5 = 0.25*2 exactly -> not strong (strict inequality)
+    # row 1: negative diagonal, s = -1: -s*A_10 = 1 (strong, the max),
+    #        -s*A_12 = -3 (opposite sign: never strong)
+    # row 2: only same-sign off-diagonals -> no strong connection at all
+    # row 3: 1x diagonal only
+    rows = {0: [0, 1, 2, 3], 1: [0, 1, 2], 2: [1, 2, 3], 3: [3]}
+    vals = {(0, 0): 4.0, (0, 1): 1.0, (0, 2): -2.0, (0, 3): -0.5,
+            (1, 0): 1.0, (1, 1): -5.0, (1, 2): -3.0,
+            (2, 1): 1.0, (2, 2): 3.0, (2, 3): 1.0,
+            (3, 3): 1.0}
+    A = csr_from_rows(rows, 4, vals)
+    Cm = oracle_mod.strength(A, 0.25)
+    expect = [0, 0, 1, 0,   1, 0, 0,   0, 0, 0,   0]
+    assert Cm.tolist() == expect
+
+
+def test_col_count_and_sym_graph(oracle_mod):
+    # asymmetric strength pattern: C_01 = 1, C_10 = 0, C_21 = 1, C_12 = 1
+    rows = {0: [0, 1], 1: [0, 1, 2], 2: [1, 2]}
+    vals = {(0, 0): 2.0, (0, 1): -1.0, (1, 0): -0.1, (1, 1): 2.0, (1, 2): -1.0, (2, 1): -1.0, (2, 2): 2.0}
+    A = csr_from_rows(rows, 3, vals)
+    Cm = oracle_mod.strength(A, 0.25)
+    assert Cm.tolist() == [0, 1, 0, 0, 1, 1, 0]
+    assert oracle_mod.col_count(A, Cm).tolist() == [0, 2, 1]
+    Sptr, Scol = oracle_mod.sym_graph(A, Cm)
+    assert adjacency(Sptr, Scol) == [{1}, {0, 2}, {1}]
+
+
+# ----------------------------------------------------------------- PMIS(2)
+def greedy_mis2(adj, count, h):
+    """Sequential greedy MIS on the square graph, nodes in descending (count, h, i)."""
+    n = len(adj)
+    order = sorted(range(n), key=lambda i: (int(count[i]), int(h[i]), i), reverse=True)
+    blocked = np.zeros(n, bool)
+    s = -np.ones(n, np.int8)
+    for i in order:
+        if blocked[i]:
+            continue
+        s[i] = 1
+        for j, dd in bfs_dist(adj, i, 2).items():
+            blocked[j] = True
+    return s
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_pmis2_equals_greedy_mis_on_square_graph(oracle_mod, seed):
+    n = 300
+    Sptr, Scol, adj = random_sym_graph(n, 4, seed)
+    rng = np.random.default_rng(100 + seed)
+    count = rng.integers(0, 5, n).astype(np.int32)
+    h = oracle_mod.mis_hash(seed, 0, n)
+    s, rounds = oracle_mod.pmis2(Sptr, Scol, count, h)
+    assert rounds >= 1
+    assert np.array_equal(s, greedy_mis2(adj, count, h))
+
+
+def test_pmis2_ties_broken_by_index(oracle_mod):
+    # all priorities equal: the largest index wins every distance-2 ball (path graph)
+    n = 10
+    adj = [set() for _ in range(n)]
+    for i in range(n - 1):
+        adj[i].add(i + 1)
+        adj[i + 1].add(i)
+    Sptr = np.zeros(n + 1, np.int32)
+    cols = []
+    for i in range(n):
+        cols.extend(sorted(adj[i]))
+        Sptr[i + 1] = len(cols)
+    s, _ = oracle_mod.pmis2(Sptr, np.array(cols, np.int32), np.zeros(n, np.int32), np.zeros(n, np.uint32))
+    assert np.flatnonzero(s == 1).tolist() == [0, 3, 6, 9]
+
+
+def test_pmis2_isolated_nodes_are_roots(oracle_mod):
+    n = 5
+    Sptr = np.zeros(n + 1, np.int32)
+    s, _ = oracle_mod.pmis2(Sptr, np.zeros(0, np.int32), np.zeros(n, np.int32), np.arange(n, dtype=np.uint32))
+    assert (s == 1).all()
+
+
+def mis_invariants(adj, s):
+    roots = np.flatnonzero(s == 1)
+    rootset = set(roots.tolist())
+    for r in roots:
+        d = bfs_dist(adj, int(r), 2)
+        assert not (set(d) - {int(r)}) & rootset, "two roots within distance 2"
+    for i in np.flatnonzero(s != 1):
+        d = bfs_dist(adj, int(i), 2)
+        assert set(d) & rootset, "non-root farther than 2 from every root"
+
+
+@pytest.mark.parametrize("seed", [5, 6])
+def test_mis_and_aggregate_invariants_random(oracle_mod, seed):
+    n = 400
+    Sptr, Scol, adj = random_sym_graph(n, 5, seed)
+    count = np.array([len(a) for a in adj], np.int32)
+    h = oracle_mod.mis_hash(seed, 1, n)
+    s, _ = oracle_mod.pmis2(Sptr, Scol, count, h)
+    mis_invariants(adj, s)
+    agg, nc = oracle_mod.aggregate(Sptr, Scol, count, h, s)
+    check_aggregates(adj, s, agg, nc, count, h)
+
+
+def check_aggregates(adj, s, agg, nc, count, h):
+    roots = np.flatnonzero(s == 1)
+    assert nc == len(roots)
+    # roots numbered in ascending fine index, one root per aggregate
+    assert agg[roots].tolist() == list(range(nc))
+    assert (agg >= 0).all() and (agg < nc).all()
+    root_of = {int(agg[r]): int(r) for r in roots}
+    key = lambda r: (int(count[r]), int(h[r]), r)
+    rootset = set(roots.tolist())
+    for i in np.flatnonzero(s != 1):
+        i = int(i)
+        r = root_of[int(agg[i])]
+        d = bfs_dist(adj, i, 2)
+        assert r in d, "member farther than 2 from its root"
+        near1 = [j for j in adj[i] if j in rootset]
+        if near1:  # nearest root first; among those the largest priority
+            assert d[r] == 1 and r == max(near1, key=key)
+        else:
+            cands = [max([q for q in adj[j] if q in rootset], key=key)
+                     for j in adj[i] if any(q in rootset for q in adj[j])]
+            assert d[r] == 2 and r == max(cands, key=key)
+
+
+def test_aggregates_on_grid(oracle_mod):
+    A = P.poisson2d(12)
+    Cm = oracle_mod.strength(A, 0.25)
+    count = oracle_mod.col_count(A, Cm)
+    Sptr, Scol = oracle_mod.sym_graph(A, Cm)
+    h = oracle_mod.mis_hash(0, 0, A.n)
+    s, _ = oracle_mod.pmis2(Sptr, Scol, count, h)
+    adj = adjacency(Sptr, Scol)
+    mis_invariants(adj, s)
+    agg, nc = oracle_mod.aggregate(Sptr, Scol, count, h, s)
+    check_aggregates(adj, s, agg, nc, count, h)
+    # in 2D a distance-2 ball has at most 13 nodes, and MIS(2) gives a ratio well above 2
+    sizes = np.bincount(agg)
+    assert sizes.max() <= 13 and A.n / nc > 3
+
+
+# ----------------------------------------------------------------- interpolation
+def test_interp_orthonormal_and_reproduces_B(oracle_mod):
+    rng = np.random.default_rng(0)
+    n, nc = 50, 9
+    agg = np.concatenate([np.arange(nc), rng.integers(0, nc, n - nc)]).astype(np.int32)
+    B = rng.uniform(0.5, 2.0, n)
+    Pw, Bc = oracle_mod.interp(agg, nc, B)
+    Pd = np.zeros((n, nc))
+    Pd[np.arange(n), agg] = Pw
+    assert np.allclose(Pd.T @ Pd, np.eye(nc), atol=4e-16 * 8)  # P^T P = I
+    assert np.allclose(Pd @ Bc, B, rtol=4e-16 * 4, atol=0)  # B_k = P_k B_{k+1}
+    # B_{k+1}(I) is the 2-norm of B over aggregate I
+    for I in range(nc):
+        assert Bc[I] == pytest.approx(np.linalg.norm(B[agg == I]), rel=1e-15)
+
+
+# ----------------------------------------------------------------- Galerkin
+def load_example():
+    agg = None
+    rows = {}
+    coarse = {}
+    for line in open(os.path.join(GOLDEN, "galerkin_example.txt")):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        if line.startswith("agg"):
+            agg = [int(t) - 1 for t in line.split()[1:]]
+        elif line.startswith("row"):
+            head, tail = line.split(":")
+            rows[int(head.split()[1]) - 1] = [int(t) - 1 for t in tail.split()]
+        elif line.startswith("coarse"):
+            head, tail = line.split(":")
+            _, I, J = head.split()
+            coarse[(int(I) - 1, int(J) - 1)] = [tuple(int(u) - 1 for u in t.split(",")) for t in tail.split()]
+    return agg, rows, coarse
+
+
+def test_galerkin_worked_example_exact_order(oracle_mod):
+    agg, rows, coarse = load_example()
+    n = 8
+    assert sum(len(r) for r in rows.values()) == 28
+    rng = np.random.default_rng(7)
+    # magnitudes spread over 16 decades: any change of grouping or summation order
+    # changes the rounded sums
+    vals = {(i, j): float(rng.choice([-1, 1]) * 10.0 ** rng.uniform(-8, 8)) for i in rows for j in rows[i]}
+    A = csr_from_rows(rows, n, vals)
+    Ac = oracle_mod.galerkin(A, np.array(agg, np.int32), 3, None)
+    got = {}
+    for I in range(3):
+        for p in range(Ac.rowptr[I], Ac.rowptr[I + 1]):
+            got[(I, int(Ac.col[p]))] = Ac.val[p]
+    assert set(got) == set(coarse) and Ac.nnz == 7
+    for key, terms in coarse.items():
+        s = vals[terms[0]]
+        for t in terms[1:]:
+            s = s + vals[t]  # left to right, the order of the sorted list
+        assert got[key] == s, key
+
+
+def test_galerkin_equals_dense_triple_product(oracle_mod):
+    for A, alpha in [(P.poisson2d(9), 0.25), (P.varcoef2d(10, 11), 0.25), (P.poisson3d(5), 0.5)]:
+        Cm = oracle_mod.strength(A, alpha)
+        count = oracle_mod.col_count(A, Cm)
+        Sptr, Scol = oracle_mod.sym_graph(A, Cm)
+        h = oracle_mod.mis_hash(3, 0, A.n)
+        s, _ = oracle_mod.pmis2(Sptr, Scol, count, h)
+        agg, nc = oracle_mod.aggregate(Sptr, Scol, count, h, s)
+        B = np.random.default_rng(1).uniform(0.5, 1.5, A.n)
+        Pw, Bc = oracle_mod.interp(agg, nc, B)
+        Pd = np.zeros((A.n, nc))
+        Pd[np.arange(A.n), agg] = Pw
+        dense = Pd.T @ A.to_dense() @ Pd
+        Ac = oracle_mod.galerkin(A, agg, nc, Pw)
+        got = Ac.to_dense()
+        scale = np.abs(dense).max()
+        assert np.abs(got - dense).max() <= 1e-14 * scale
+        # the coarse pattern is exactly symmetric; mirrored values are summed in
+        # different orders, so they agree to rounding only
+        assert np.array_equal(got != 0, got.T != 0)
+        assert np.abs(got - got.T).max() <= 1e-15 * scale
+        # coarse columns ascending within each row
+        for I in range(nc):
+            c = Ac.col[Ac.rowptr[I]:Ac.rowptr[I + 1]]
+            assert (np.diff(c) > 0).all()
+
+
+# ----------------------------------------------------------------- omega
+@pytest.mark.parametrize("kind,m", [("1d", 60), ("2d", 12), ("2d", 30)])
+def test_rho_estimate_against_laplacian_spectrum(oracle_mod, kind, m):
+    A = P.poisson1d(m) if kind == "1d" else P.poisson2d(m)
+    rho_exact = 1.0 + np.cos(np.pi / (m + 1))  # rho(D^-1 A) of the Dirichlet Laplacian
+    rho, H = oracle_mod.rho_estimate(A, seed=0, level=0, m=5)
+    assert rho <= rho_exact * (1 + 1e-12)
+    assert rho >= 0.9 * rho_exact
+    # the oracle's eigen-solver against LAPACK on the same symmetric part
+    T = 0.5 * (H + H.T)
+    assert rho == pytest.approx(np.abs(np.linalg.eigvalsh(T)).max(), rel=1e-13)
+    # Arnoldi on a symmetric operator: H is tridiagonal up to rounding
+    assert np.abs(np.triu(H, 2)).max() <= 1e-12
+
+
+def test_sym_eig_against_lapack(oracle_mod):
+    rng = np.random.default_rng(3)
+    for m in (1, 2, 5, 8):
+        a = rng.normal(size=(m, m))
+        a = a + a.T
+        assert np.allclose(oracle_mod.sym_eig(a), np.linalg.eigvalsh(a), atol=1e-12)
+
+
+def test_cholesky_solve(oracle_mod):
+    rng = np.random.default_rng(4)
+    m = 40
+    a = rng.normal(size=(m, m))
+    a = a @ a.T + m * np.eye(m)
+    L = oracle_mod.cholesky(a)
+    assert np.allclose(L @ L.T, a, rtol=1e-13, atol=1e-12)
+    b = rng.normal(size=m)
+    assert np.allclose(oracle_mod.chol_solve(L, b), np.linalg.solve(a, b), rtol=1e-12)
+    assert oracle_mod.cholesky(-a) is None
+
+
+# ----------------------------------------------------------------- the whole method
+def test_table1_level0_size():
+    vals = dict(l.split() for l in open(os.path.join(GOLDEN, "table1_level0.txt")) if l[0] != "#")
+    A = P.poisson2d(int(vals["m"]))
+    assert A.n == int(vals["n"]) and A.nnz == int(vals["nnz"])
+
+
+@pytest.mark.parametrize("kind", ["1d", "2d", "3d"])
+def test_manufactured_solution(oracle_mod, kind):
+    A, alpha = {"1d": (P.poisson1d(300), 0.25), "2d": (P.poisson2d(40), 0.25), "3d": (P.poisson3d(14), 0.5)}[kind]
+    xs = np.sin(np.arange(A.n) * 0.37) + 0.1
+    b = A.matvec(xs)
+    H = oracle_mod.Hierarchy(A, alpha=alpha, coarse_max=16)
+    assert H.nlevels >= 2
+    tol = 1e-10
+    x, info = H.solve(b, tol=tol, max_iter=300)
+    assert info["status"] == 0 and info["relres"] <= tol
+    kappa = np.linalg.cond(A.to_dense())
+    assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= kappa * tol
+
+
+def test_one_level_converges_in_one_iteration(oracle_mod):
+    A = P.poisson2d(7)  # n = 49 <= coarse_max
+    H = oracle_mod.Hierarchy(A, coarse_max=64)
+    assert H.nlevels == 1
+    x, info = H.solve(P.rhs_uniform(A.n, 0), tol=1e-12)
+    assert info["iters"] == 1 and info["relres"] <= 1e-12
+
+
+def test_fcg_error_decreases_in_A_norm(oracle_mod):
+    A = P.varcoef2d(24, 9)
+    Ad = A.to_dense()
+    b = P.rhs_uniform(A.n, 5)
+    xs = np.linalg.solve(Ad, b)
+    H = oracle_mod.Hierarchy(A, coarse_max=20)
+    errs = []
+    for k in range(1, 12):
+        x, info = H.solve(b, tol=0.0, max_iter=k)
+        e = x - xs
+        errs.append(np.sqrt(e @ Ad @ e))
+    assert all(b_ <= a_ * (1 + 1e-12) for a_, b_ in zip(errs, errs[1:]))
+    assert errs[-1] < 0.1 * errs[0]
+
+
+def test_kcycle_inner_step_is_2x2_galerkin_solve(oracle_mod):
+    A = P.poisson2d(40)
+    H = oracle_mod.Hierarchy(A, coarse_max=16, kcycle_t=0.0)  # always take the second inner step
+    assert H.nlevels >= 3
+    L1 = H.level(1)
+    A1 = P.CSR(L1.n, L1.rowptr, L1.col, L1.val).to_dense()
+    r = P.rhs_uniform(L1.n, 8)
+    x, c, d = H.krylov2_probe(1, r)
+    G = np.array([[c @ A1 @ c, c @ A1 @ d], [d @ A1 @ c, d @ A1 @ d]])
+    ab = np.linalg.solve(G, np.array([c @ r, d @ r]))
+    assert np.allclose(x, ab[0] * c + ab[1] * d, rtol=1e-9, atol=1e-12 * np.abs(x).max())
+    # with t large the first step is accepted: x = (c^T r / c^T A c) c
+    H2 = oracle_mod.Hierarchy(A, coarse_max=16, kcycle_t=10.0)
+    x2, c2, d2 = H2.krylov2_probe(1, r)
+    assert np.allclose(x2, (c2 @ r) / (c2 @ A1 @ c2) * c2, rtol=1e-12)
+    assert not d2.any()
+
+
+def dense_hierarchy(H):
+    levs = [H.level(k) for k in range(H.nlevels)]
+    A = [P.CSR(L.n, L.rowptr, L.col, L.val).to_dense() for L in levs]
+    Pm = []
+    for k in range(len(levs) - 1):
+        Pd = np.zeros((levs[k].n, levs[k + 1].n))
+        Pd[np.arange(levs[k].n), levs[k].agg] = levs[k].P
+        Pm.append(Pd)
+    return levs, A, Pm
+
+
+def test_two_grid_cycle_matches_textbook(oracle_mod):
+    A = P.poisson2d(16)
+    H = oracle_mod.Hierarchy(A, coarse_max=64)
+    assert H.nlevels == 2
+    levs, Ad, Pm = dense_hierarchy(H)
+    w = levs[0].omega / np.diag(Ad[0])
+    b = P.rhs_uniform(A.n, 2)
+    x = w * b
+    x = x + Pm[0] @ np.linalg.solve(Ad[1], Pm[0].T @ (b - Ad[0] @ x))
+    x = x + w * (b - Ad[0] @ x)
+    assert np.allclose(H.precond(b), x, rtol=1e-11, atol=1e-13)
+    # Galerkin coarse operator equals P^T A P
+    assert np.allclose(Ad[1], Pm[0].T @ Ad[0] @ Pm[0], rtol=1e-13, atol=1e-14)
+
+
+def test_vcycle_symmetric_and_matches_recursion(oracle_mod):
+    A = P.poisson2d(30)
+    H = oracle_mod.Hierarchy(A, coarse_max=16, kcycle_levels=0)
+    assert H.nlevels >= 3
+    levs, Ad, Pm = dense_hierarchy(H)
+
+    def vcyc(k, b):
+        if k == len(Ad) - 1:
+            return np.linalg.solve(Ad[k], b)
+        w = levs[k].omega / np.diag(Ad[k])
+        x = w * b
+        xc = vcyc(k + 1, Pm[k].T @ (b - Ad[k] @ x))
+        x = x + Pm[k] @ xc
+        return x + w * (b - Ad[k] @ x)
+
+    b = P.rhs_uniform(A.n, 3)
+    assert np.allclose(H.precond(b), vcyc(0, b), rtol=1e-11, atol=1e-13)
+    u, v = P.rhs_uniform(A.n, 4), P.rhs_uniform(A.n, 5)
+    assert u @ H.precond(v) == pytest.approx(v @ H.precond(u), rel=1e-12)
+
+
+def test_polynomial_smoother_reduces_to_jacobi(oracle_mod):
+    A = P.poisson2d(20)
+    b = P.rhs_uniform(A.n, 6)
+    H = oracle_mod.Hierarchy(A, coarse_max=16)
+    ref = H.precond(b)
+    for k in range(H.nlevels - 1):
+        L = H.level(k)
+        H.set_poly(k, np.tile([L.omega, 0.0, 0.0], (L.n, 1)))
+    assert np.allclose(H.precond(b), ref, rtol=1e-13, atol=1e-15)
+
+
+def test_polynomial_smoother_vcycle_symmetric(oracle_mod):
+    A = P.varcoef2d(20, 3)
+    H = oracle_mod.Hierarchy(A, coarse_max=16, kcycle_levels=0)
+    rng = np.random.default_rng(2)
+    for k in range(H.nlevels - 1):
+        H.set_poly(k, rng.uniform(0.1, 0.6, (H.level(k).n, 3)))
+    u, v = P.rhs_uniform(A.n, 4), P.rhs_uniform(A.n, 5)
+    assert u @ H.precond(v) == pytest.approx(v @ H.precond(u), rel=1e-11)
+
+
+def test_fgmres_manufactured_and_monotone(oracle_mod):
+    A = P.varcoef2d(30, 4)
+    xs = np.cos(np.arange(A.n) * 0.11)
+    b = A.matvec(xs)
+    H = oracle_mod.Hierarchy(A, coarse_max=16, outer=1, restart=5)
+    x, info = H.solve(b, tol=1e-10, max_iter=200)
+    assert info["status"] == 0 and info["relres"] <= 1e-10
+    assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= np.linalg.cond(A.to_dense()) * 1e-10
+    hist = info["hist"]
+    assert all(b_ <= a_ * (1 + 1e-12) for a_, b_ in zip(hist, hist[1:]))
+
+
+def test_setup_rejects_bad_csr(oracle_mod):
+    A = P.poisson1d(5)
+    bad = P.CSR(A.n, A.rowptr, A.col, A.val.copy())
+    bad.val[0] = 0.0  # zero diagonal
+    with pytest.raises(RuntimeError):
+        oracle_mod.Hierarchy(bad)
+    unsorted = P.CSR(A.n, A.rowptr, A.col.copy(), A.val)
+    unsorted.col[1], unsorted.col[2] = unsorted.col[2], unsorted.col[1]
+    with pytest.raises(RuntimeError):
+        oracle_mod.Hierarchy(unsorted)
+
+
+def test_splitmix64_published_vector(oracle_mod):
+    # splitmix64 output sequence from state 0 (Vigna's reference implementation
+    # advances the state by the golden gamma before mixing): first value
+    assert oracle_mod.splitmix64(0) == 0xE220A8397B1DCDAF
+    assert int(P.splitmix64(np.array([0], np.uint64))[0]) == 0xE220A8397B1DCDAF
