@@ -1,0 +1,358 @@
+"""Benchmark: aggregation-AMG preconditioned flexible CG on the 3D 7-point Poisson
+problem on a 128^3 grid (n = 2,097,152, nnz = 14,581,760), to a 1e-8 relative
+residual, on one GB300 per process.
+
+One step = the whole hot path on one system: amg_setup (strength, PMIS(2),
+aggregation, interpolation, Galerkin keyed sum, omega, coarsest inverse) +
+amg_solve (K-cycle preconditioned flexible CG) + amg_free, with the CSR and the
+right-hand side already resident in HBM.  value = DoF solved per second over all
+ranks (each rank solves its own replica: the method does not shard here).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision f32|f64|bf16]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solve ms & DoF/s to 1e-8 rel. residual, mixed/learned vs FP64 AMG; SpMV % HBM"
+M_GRID = 128
+SAMPLE_GRID = 96  # CPU oracle sample: same discretisation on a 96^3 grid
+ALPHA, SEED, TOL = 0.5, 1, 1e-8
+PREC = {"f64": 0, "f32": 1, "bf16": 2}
+PREC_DTYPE = {"f64": "f64", "f32": "f32+f64", "bf16": "bf16+f32+f64"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="f32", choices=list(PREC))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v: float, ws: int) -> float:
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------- CPU oracle leg
+def oracle_sample(grid: int = SAMPLE_GRID):
+    """The FP64 CPU oracle, as it stands, on one setup + solve (single thread)."""
+    from oracle import oracle
+    from paper_1403_1649_gb300 import problems as P
+    oracle.build()
+    A = P.poisson3d(grid)
+    b = P.rhs_uniform(A.n, SEED)
+    t0 = time.perf_counter()
+    H = oracle.Hierarchy(A, alpha=ALPHA, seed=SEED)
+    x, info = H.solve(b, tol=TOL, max_iter=500)
+    dt = time.perf_counter() - t0
+    return {"value": A.n / dt, "unit": "DoF/s", "cores": 1, "kind": "oracle",
+            "sample": f"3D 7-point Poisson {grid}^3 (n={A.n}), oracle setup + FP64 FCG solve to {TOL:g} "
+                      f"({info['iters']} iterations, {dt:.2f} s), same discretisation/alpha/seed as the workload",
+            "seconds": dt}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample()
+    vals, secs = [], []
+    for _ in range(args.steps):
+        r = oracle_sample()
+        vals.append(r["value"])
+        secs.append(r["seconds"])
+    total = sum(secs)
+    n = SAMPLE_GRID ** 3
+    value = n * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"3D 7-point Poisson {SAMPLE_GRID}^3 sample of the 128^3 workload, CPU oracle"},
+        "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} x oracle setup + FP64 FCG solve on 3D 7-point Poisson "
+                                   f"{SAMPLE_GRID}^3, single thread"},
+        "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.idx), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [t.strip() for t in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- GPU leg
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return None
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("solve.cu", "amg_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1403_1649_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(precision: str):
+    """dram bytes per launch of the level-0 SpMV from the committed ncu summary,
+    only if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "spmv_level0_poisson3d_128.json")
+    try:
+        d = json.load(open(p))
+    except (OSError, ValueError):
+        return None
+    e = d.get(precision)
+    if not e or e.get("source_hash") != source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        barrier(ws)
+        return
+
+    import torch
+    assert torch.cuda.is_available(), "bench.py needs a CUDA device"
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1403_1649_gb300 import amg, build
+    from paper_1403_1649_gb300 import problems as P
+    if rank == 0 or not os.path.exists(amg.LIB_PATH):
+        build.build()
+    barrier(ws)
+    amg.lib()
+
+    A = P.poisson3d(M_GRID)
+    b = P.rhs_uniform(A.n, SEED)
+    n, nnz = A.n, A.nnz
+    rp = torch.from_numpy(A.rowptr).to(dev)
+    ci = torch.from_numpy(A.col).to(dev)
+    va = torch.from_numpy(A.val).to(dev)
+    bd = torch.from_numpy(b).to(dev)
+    xd = torch.zeros_like(bd)
+    stream = torch.cuda.current_stream(dev)
+
+    def params(prec):
+        return amg.amg_default_params(alpha=ALPHA, seed=SEED, precision=PREC[prec], max_iter=500)
+
+    stats = {}
+
+    def step(prec):
+        h = amg.amg_setup(rp, ci, va, params(prec), stream.cuda_stream)
+        xd.zero_()
+        rc, it, _ = amg.amg_solve(h, bd, xd, TOL, 500, stream.cuda_stream)
+        info = amg.amg_last_solve_info(h)
+        amg.amg_free(h)
+        stats.setdefault(prec, []).append(info)
+        return info
+
+    prec = args.precision
+    for _ in range(max(args.warmup, 3)):
+        step(prec)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    stats[prec] = []
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(prec)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop()
+    elapsed_ms = max_over_ranks(e0.elapsed_time(e1), ws)
+    infos = stats[prec]
+    assert all(i["status"] == 0 and i["final_relres"] <= TOL for i in infos), infos
+    ms_per_step = elapsed_ms / args.steps
+    value = ws * n * args.steps / (elapsed_ms / 1e3)
+    launches = int(sum(i["kernel_launches"] + i["setup_launches"] for i in infos))
+
+    extra = {}
+    # FP64 preconditioner on the same workload (the comparison the metric names)
+    if rank == 0:
+        for cmp in [p for p in ("f64", "f32") if p != prec]:
+            for _ in range(2):
+                inf = step(cmp)
+            extra[cmp] = {"setup_ms": inf["setup_ms"], "solve_ms": inf["solve_ms"], "iters": inf["iters"],
+                          "final_relres": inf["final_relres"],
+                          "solve_dof_per_s": n / (inf["solve_ms"] / 1e3)}
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    hb = np.ascontiguousarray(b)
+    e2e_ms = []
+    for k in range(args.steps + 1):
+        xh = np.zeros(n)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = amg.amg_setup(A.rowptr, A.col, A.val, params(prec))
+        rc, it, _ = amg.amg_solve(h, hb, xh, TOL, 500)
+        amg.amg_free(h)
+        dt = (time.perf_counter() - t0) * 1e3
+        if k > 0:
+            e2e_ms.append(dt)
+    e2e_step = max_over_ranks(sum(e2e_ms) / len(e2e_ms), ws)
+    h2d = 4 * (n + 1) + 12 * nnz + 8 * n + 8 * n
+    d2h = 8 * n + 8 * 501
+
+    # roofline of the dominant kernel: the level-0 SELL SpMV of the preconditioner
+    roof = None
+    if rank == 0:
+        h = amg.amg_setup(rp, ci, va, params(prec), stream.cuda_stream)
+        vt = torch.float64 if prec == "f64" else torch.float32
+        x = torch.rand(n, dtype=vt, device=dev)
+        y = torch.empty_like(x)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        durs = []
+        for r in range(23):
+            flush.fill_(r & 0xFF)
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            amg.amg_spmv(h, 0, x, y, stream.cuda_stream)
+            s1.record(stream)
+            s1.synchronize()
+            if r >= 3:
+                durs.append(s0.elapsed_time(s1) / 1e3)
+        amg.amg_free(h)
+        vb = {"f64": 8, "f32": 4, "bf16": 2}[prec]
+        xb = 8 if prec == "f64" else 4
+        alg_bytes = nnz * (4 + vb) + 4 * (n + 1) + 2 * xb * n
+        t_avg = sum(durs) / len(durs)
+        peaks = measured_peaks()
+        peak = peaks["hbm_gbs"] if peaks else 6800.0
+        achieved = alg_bytes / t_avg / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": ncu_traffic(prec), "kernel": f"k_sell level-0 SpMV ({prec} values, SELL-32)",
+                "algorithmic_bytes": alg_bytes, "avg_launch_us": t_avg * 1e6,
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs, burst)" if peaks else "fallback"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = oracle_sample()
+        cpu.pop("seconds", None)
+
+    if rank == 0:
+        mean = lambda key: float(np.mean([i[key] for i in infos]))
+        line = {
+            "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": PREC_DTYPE[prec], "data": "synthetic",
+            "config": {"workload": "3D 7-point Poisson 128^3 (n=2,097,152, nnz=14,581,760), RHS U[-1,1] seed 1; "
+                                   "aggregation AMG (alpha 0.5, PMIS(2) seed 1, coarse <= 64) K-cycle "
+                                   f"preconditioner ({prec} values/vectors) in FP64 flexible CG to 1e-8",
+                       "step": "amg_setup + amg_solve + amg_free, inputs resident in HBM",
+                       "l2": "inputs larger than L2 (level-0 FP64 CSR 175 MB > 129 MB)",
+                       "parallelism": f"replicas x{ws}"},
+            "setup_ms": mean("setup_ms"), "solve_ms": mean("solve_ms"), "iters": int(infos[-1]["iters"]),
+            "final_relres": float(infos[-1]["final_relres"]),
+            "solve_dof_per_s": n / (mean("solve_ms") / 1e3),
+            "compare": extra,
+            "e2e": {"value": ws * n / (e2e_step / 1e3), "unit": "DoF/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    barrier(ws)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

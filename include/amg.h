@@ -1,0 +1,173 @@
+/* amg.h -- C ABI of the GB300 aggregation AMG library.
+ *
+ * The library implements the method of Gandham, Esler and Zhang, "A GPU
+ * Accelerated Aggregation Algebraic Multigrid Method" (arXiv 1403.1649):
+ * a setup that builds aggregates from a PMIS(2) maximal independent set on the
+ * graph of strong negative connections (Sec. 2.1, Alg. 1-3) and forms coarse
+ * operators with a keyed-sum Galerkin product (Sec. 3.1), and a solve that uses
+ * K-cycles on the top levels and V-cycles below (Alg. 4, Alg. 5, Sec. 2.2) with
+ * damped Jacobi smoothing (Eq. damped Jacobi) as the preconditioner of flexible
+ * CG or FGMRES (Sec. 2.2, Sec. 4).  Every step runs in the library's CUDA
+ * kernels for sm_103a; there is no CPU fallback.
+ *
+ * General conventions
+ *  - Every call returns AMG_OK (0) on success or a negative AMG_ERR_* code;
+ *    no C++ exception crosses the ABI.  amg_last_error() gives a message
+ *    (thread-local) for the most recent failure of the calling thread.
+ *  - Pointers are plain host or device pointers; the library detects which
+ *    with cudaPointerGetAttributes.  Host data is copied in/out inside the
+ *    call (the copies are part of the call's cost).  Device data must be on
+ *    the current device and is accessed in stream order on `stream`.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Calls are asynchronous with respect to the host only where stated; the
+ *    setup and solve calls synchronise `stream` before returning because they
+ *    take host-side decisions (level sizes, convergence).
+ *  - Input arrays are borrowed: read during the call, never freed or kept.
+ *  - A hierarchy owns all its device memory (cudaMalloc) and releases it in
+ *    amg_free.  A hierarchy is used by one thread at a time.
+ */
+#ifndef AMG_GB300_H
+#define AMG_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define AMG_OK 0
+#define AMG_ERR_BAD_INPUT -1     /* malformed CSR, zero diagonal, bad sizes/params   */
+#define AMG_ERR_CUDA -2          /* a CUDA runtime call failed (message has details) */
+#define AMG_ERR_NOT_CONVERGED -3 /* max_iter reached; iters and res_hist are filled  */
+#define AMG_ERR_BREAKDOWN -4     /* Krylov breakdown (p^T A p <= 0, rho <= 0, ...)   */
+#define AMG_ERR_NAN -5           /* NaN/Inf in a residual norm                       */
+#define AMG_ERR_SETUP -6         /* coarsening failed / coarsest level too large or
+                                    not positive definite                            */
+#define AMG_ERR_UNSUPPORTED -7   /* option not available for this input              */
+
+/* precision of the preconditioner (matrix values and cycle vectors) */
+#define AMG_PREC_F64 0 /* everything FP64                                              */
+#define AMG_PREC_F32 1 /* FP32 values and vectors, FP32 accumulation                   */
+#define AMG_PREC_BF16 2 /* BF16 matrix values, FP32 vectors and accumulation           */
+
+/* A square sparse matrix in CSR form.  Columns ascending inside each row, the
+ * diagonal present and nonzero, int32 indices, FP64 values.  Arrays may be host
+ * or device pointers (all three of the same kind). */
+typedef struct amg_csr {
+  int32_t n;
+  int64_t nnz;
+  const int32_t *row_ptr; /* n+1 */
+  const int32_t *col;     /* nnz */
+  const double *val;      /* nnz */
+} amg_csr;
+
+typedef struct amg_params {
+  double alpha;          /* strength threshold of Sec. 2.1.1 (paper: 0.25 in 2D, 0.5 in 3D) */
+  uint64_t seed;         /* seeds the MIS priorities r_i of Alg. 2 and the Arnoldi start    */
+  int32_t coarse_max;    /* stop coarsening when n_k <= coarse_max (exact solve below)      */
+  int32_t max_levels;    /* cap on the number of levels                                     */
+  int32_t kcycle_levels; /* levels k < kcycle_levels get the Krylov-accelerated coarse
+                            correction of Alg. 5 (paper: the top two, Sec. 2.2)            */
+  double kcycle_t;       /* threshold t of the test ||r~|| <= t ||r|| in Alg. 5            */
+  int32_t omega_mode;    /* 0: omega = (4/3)/rho(D^-1 A), rho from 5 Arnoldi steps;
+                            1: omega = `omega`                                             */
+  double omega;
+  int32_t precision;     /* AMG_PREC_* of the preconditioner                                */
+  int32_t outer;         /* 0: flexible CG (CG variant of Alg. 5); 1: FGMRES(restart)
+                            (GMRES variant)                                                */
+  int32_t restart;       /* FGMRES restart length                                           */
+  int32_t max_iter;      /* outer iteration cap of amg_solve                                */
+  int32_t use_graph;     /* 1: replay one outer iteration as a captured CUDA graph          */
+  int32_t smoother;      /* 0: damped Jacobi; 1: per-row polynomial smoother whose
+                            coefficients are set with amg_set_poly                         */
+} amg_params;
+
+typedef struct amg_level_info {
+  int32_t n;          /* unknowns on this level                             */
+  int64_t nnz;        /* nonzeros of A_k                                    */
+  int32_t n_coarse;   /* n_{k+1} (0 on the coarsest level)                  */
+  int32_t mis_rounds; /* PMIS(2) rounds used to coarsen this level          */
+  double omega;       /* damped-Jacobi weight of this level                 */
+} amg_level_info;
+
+typedef struct amg_solve_info {
+  int32_t iters;         /* outer iterations                                 */
+  int32_t status;        /* return code of the last amg_solve                */
+  double final_relres;   /* ||b - A x||_2 / ||b||_2 recomputed in FP64 at exit */
+  double solve_ms;       /* device time of the last solve (CUDA events)      */
+  double setup_ms;       /* device time of the setup (CUDA events)           */
+  int64_t kernel_launches; /* kernels of this library launched by the last solve */
+  int64_t setup_launches;  /* kernels of this library launched by the setup       */
+} amg_solve_info;
+
+typedef struct amg_hierarchy amg_hierarchy;
+
+/* Fill *p with the defaults: alpha 0.25, seed 0, coarse_max 64, max_levels 25,
+ * kcycle_levels 2, kcycle_t 0.25, omega_mode 0, omega 2/3, precision F64,
+ * outer FCG, restart 30, max_iter 500, use_graph 1, smoother 0. */
+void amg_default_params(amg_params *p);
+
+/* Alg. 1: build the hierarchy of A on the GPU.
+ * Per level: strength (Sec. 2.1.1), PMIS(2) (Alg. 2), aggregation (Sec. 2.1.2),
+ * interpolation (Alg. 3), Galerkin keyed sum (Sec. 3.1), omega (Eq. damped
+ * Jacobi), and finally the dense factorisation of the coarsest level (the paper
+ * uses SuperLU there, Sec. 3).  The aggregates, interpolation weights and coarse
+ * matrices are bit-identical to a sequential FP64 evaluation of those steps.
+ * Returns AMG_ERR_BAD_INPUT for a malformed CSR or zero diagonal, AMG_ERR_SETUP
+ * if coarsening cannot reach a coarsest level of at most 4096 unknowns or that
+ * level is not positive definite.  *out is set only on success. */
+int amg_setup(const amg_csr *A, const amg_params *params, void *stream, amg_hierarchy **out);
+
+/* Solve A x = b to ||b - A x||_2 <= tol ||b||_2 with the outer Krylov method of
+ * the params, preconditioned by one K-cycle (Alg. 5) per iteration (Sec. 2.2).
+ * b: n doubles; x: n doubles holding x0 on entry and the solution on exit
+ * (host or device).  iters (nullable) gets the outer iterations; res_hist
+ * (nullable, host, length max_iter+1) gets the relative residual norm before
+ * the first and after every iteration.  The final residual is recomputed in
+ * FP64 (amg_last_solve_info).  Returns AMG_ERR_NOT_CONVERGED if max_iter is
+ * reached (iters, res_hist and x still filled), AMG_ERR_BREAKDOWN or
+ * AMG_ERR_NAN on numerical failure. */
+int amg_solve(amg_hierarchy *h, const double *b, double *x, double tol, int32_t *iters,
+              double *res_hist, void *stream);
+
+/* One application of the preconditioner, x = M b (Alg. 5 at level 0 from a
+ * zero initial guess).  b, x: n doubles, host or device. */
+int amg_precond(amg_hierarchy *h, const double *b, double *x, void *stream);
+
+/* y = A_k x on level k with the solve-phase matrix (in the hierarchy's
+ * precision).  x, y: n_k elements of the vector type of the precision (double
+ * for F64, float otherwise), DEVICE pointers.  Asynchronous on `stream`. */
+int amg_spmv(amg_hierarchy *h, int32_t level, const void *x, void *y, void *stream);
+
+/* Per-row polynomial smoother coefficients of level k (n_k x 3, row major,
+ * host or device doubles): the smoother applies
+ * x += sum_q diag(c_q) (D^-1 A)^q D^-1 r before the coarse correction and the
+ * transposed polynomial after it.  Takes effect when params.smoother == 1.
+ * The paper lists polynomial smoothers as future work (Sec. 5). */
+int amg_set_poly(amg_hierarchy *h, int32_t level, const double *coef, void *stream);
+
+/* Sizes per level.  levels (host, capacity cap) may be NULL to query *nlevels. */
+int amg_hierarchy_info(const amg_hierarchy *h, amg_level_info *levels, int32_t cap,
+                       int32_t *nlevels);
+
+/* Copy level k of the setup to HOST arrays (any may be NULL): row_ptr (n+1),
+ * col and val (nnz) of A_k in FP64; agg (n, coarse id of every node), P (n,
+ * the nonzero of row i of P_k) and B (n, the near-null vector B_k).  agg and P
+ * are left untouched on the coarsest level. */
+int amg_export_level(const amg_hierarchy *h, int32_t level, int32_t *row_ptr, int32_t *col,
+                     double *val, int32_t *agg, double *P, double *B);
+
+/* Statistics of the last setup/solve on this hierarchy. */
+int amg_last_solve_info(const amg_hierarchy *h, amg_solve_info *info);
+
+/* Release every device and host resource of the hierarchy (NULL is a no-op). */
+void amg_free(amg_hierarchy *h);
+
+/* Message of the calling thread's most recent failure ("" if none). */
+const char *amg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

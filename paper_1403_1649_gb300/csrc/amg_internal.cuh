@@ -1,0 +1,199 @@
+// amg_internal.cuh -- shared declarations of the GB300 aggregation AMG library.
+//
+// Device data layout (per level k of the hierarchy, all in HBM):
+//   setup CSR   rp[n+1] int32, ci[nnz] int32, val[nnz] f64   (bit-exact level matrix)
+//   solve SELL  slices of 32 rows, column-major inside a slice: entry e of row
+//               32*s + l sits at sptr[s] + 32*e + l; padding has col = own row,
+//               value 0.  Values in the preconditioner precision (f64/f32/bf16).
+//   agg[n]      coarse id of every node;  pw[n] the nonzero of row i of P_k
+//   aptr[nc+1], amem[n]   members of every aggregate in ascending fine index
+//   wd[n]       omega / A_ii  (damped Jacobi, Eq. damped Jacobi)
+//   vectors     cycle work vectors in the vector type of the precision
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/amg.h"
+
+namespace amg {
+
+// ---------------------------------------------------------------- errors
+struct Error {
+  int code;
+  std::string msg;
+};
+
+void set_last_error(const std::string &m);
+
+#define AMG_CUDA(call)                                                                        \
+  do {                                                                                        \
+    cudaError_t e__ = (call);                                                                 \
+    if (e__ != cudaSuccess)                                                                   \
+      throw ::amg::Error{AMG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e__) +   \
+                                           " (" + __FILE__ + ":" + std::to_string(__LINE__) + ")"}; \
+  } while (0)
+
+#define AMG_LAUNCH_CHECK() AMG_CUDA(cudaGetLastError())
+
+// kernels launched by the calling thread (setup statistics)
+int64_t &launch_counter();
+#define AMG_COUNT() (++::amg::launch_counter())
+
+// ---------------------------------------------------------------- device memory
+// All allocations of a hierarchy go through one arena so that amg_free
+// releases everything, also after a failure half way through setup.
+struct Arena {
+  std::vector<void *> blocks;
+  void *alloc(size_t bytes) {
+    void *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    AMG_CUDA(cudaMalloc(&p, bytes));
+    blocks.push_back(p);
+    return p;
+  }
+  template <class T>
+  T *get(size_t n) { return static_cast<T *>(alloc(n * sizeof(T))); }
+  void release() {
+    for (void *p : blocks) cudaFree(p);
+    blocks.clear();
+  }
+};
+
+// Temporary device buffer freed at scope exit (setup scratch).
+template <class T>
+struct DevBuf {
+  T *p = nullptr;
+  size_t n = 0;
+  DevBuf() = default;
+  explicit DevBuf(size_t count) { resize(count); }
+  void resize(size_t count) {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = count;
+    AMG_CUDA(cudaMalloc(&p, (count ? count : 1) * sizeof(T)));
+  }
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+  DevBuf(const DevBuf &) = delete;
+  DevBuf &operator=(const DevBuf &) = delete;
+};
+
+// ---------------------------------------------------------------- levels
+constexpr int kSlice = 32;          // SELL slice height = warp width
+constexpr int kMaxLevels = 32;
+constexpr int kMaxDense = 4096;     // largest coarsest level factorised densely
+constexpr int kRedBlocks = 1216;    // 8 x 152 SMs: grid of the reduction kernels
+constexpr int kNumSlots = 32;       // Krylov scalars per level
+
+// scalar slots of a level (double) used by the K-cycle coarse step at that level
+enum Slot {
+  S_RHO1 = 0, S_A1, S_S1, S_NRT2, S_NR2, S_GAM, S_BET, S_A2, S_CC, S_CD,
+  // outer Krylov (level 0 only)
+  S_PQ = 12, S_PR, S_ALPHA, S_BETA, S_RR, S_NB2, S_REL, S_ZQ, S_TRUE_RR, S_TOL, S_MAXIT,
+};
+
+struct Level {
+  int32_t n = 0, nc = 0, mis_rounds = 0;
+  int64_t nnz = 0;
+  double omega = 0.0;
+  // setup CSR (FP64, exact)
+  int32_t *rp = nullptr, *ci = nullptr;
+  double *val = nullptr;
+  double *B = nullptr;  // near-null vector B_k
+  // transfer
+  int32_t *agg = nullptr, *aptr = nullptr, *amem = nullptr;
+  double *pw64 = nullptr;  // P weights in FP64 (exported)
+  // solve-phase matrix (SELL-32)
+  int32_t nslices = 0;
+  int64_t sell_entries = 0;
+  int64_t *sptr = nullptr;
+  int32_t *scol = nullptr;
+  void *sval = nullptr;
+  double *sval64 = nullptr;   // level 0 only: FP64 values for the outer Krylov when
+                              // the preconditioner runs in reduced precision
+  // solve-phase vectors and per-row data in the vector type
+  void *wd = nullptr, *dinv = nullptr, *pw = nullptr, *poly = nullptr;
+  void *r = nullptr, *bc = nullptr, *xc = nullptr, *c = nullptr, *v = nullptr, *rt = nullptr,
+       *d = nullptr, *w = nullptr, *tmp = nullptr, *u0 = nullptr, *u1 = nullptr;
+  double *slots = nullptr;    // kNumSlots doubles
+  int *flag = nullptr;        // predicate of the second inner step of Alg. 5 at this level
+  double *partials = nullptr; // kRedBlocks * 8 doubles
+};
+
+struct Hierarchy {
+  amg_params p{};
+  int L = 0;
+  Level lev[kMaxLevels];
+  double *coarse_inv = nullptr;  // dense inverse of A_{L-1}, n_L x n_L, FP64
+  int32_t nL = 0;
+  Arena arena;
+  // outer Krylov work (FP64, level 0)
+  double *x = nullptr, *b = nullptr, *r = nullptr, *z = nullptr, *pdir = nullptr, *q = nullptr;
+  double *hist = nullptr;   // device residual history
+  int *it_dev = nullptr;    // device iteration counter
+  int *status_dev = nullptr;
+  // FGMRES
+  double *V = nullptr, *Z = nullptr, *H = nullptr, *gv = nullptr;
+  // precision bridging vectors at level 0 of the preconditioner
+  void *pre_in = nullptr, *pre_out = nullptr;
+  // statistics
+  amg_solve_info info{};
+  int64_t launches = 0;
+  cudaGraphExec_t graph_exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  int graph_kind = -1;
+  int64_t graph_launches = 0;     // kernels in one replay of the captured iteration
+  double *host_pinned = nullptr;  // small pinned staging buffer
+  bool poly_set[kMaxLevels] = {};
+};
+
+// ---------------------------------------------------------------- helpers
+inline int grid_for(int64_t items, int per_block, int cap = 152 * 32) {
+  int64_t g = (items + per_block - 1) / per_block;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (int)g;
+}
+
+enum PtrKind { PTR_HOST = 0, PTR_DEVICE = 1 };
+PtrKind pointer_kind(const void *p);
+
+// setup.cu
+void build_hierarchy(Hierarchy &h, const amg_csr &A, cudaStream_t s);
+// solve.cu: per-row smoother data (omega/A_ii, 1/A_ii, P weights) in the vector type
+void make_row_data(Hierarchy &h, Level &L, const double *diag, cudaStream_t s);
+// solve.cu
+void prepare_solve(Hierarchy &h, cudaStream_t s);
+int run_solve(Hierarchy &h, const double *b, double *x, double tol, int32_t *iters, double *res_hist,
+              cudaStream_t s);
+void run_precond(Hierarchy &h, const double *b, double *x, cudaStream_t s);
+void run_spmv(Hierarchy &h, int level, const void *x, void *y, cudaStream_t s);
+void set_poly(Hierarchy &h, int level, const double *coef_dev, cudaStream_t s);
+
+// ---------------------------------------------------------------- device utilities
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <class T> struct VecOf;
+template <> struct VecOf<double> { using type = double; };
+
+__device__ __forceinline__ double to_acc(double v, double) { return v; }
+__device__ __forceinline__ float to_acc(float v, float) { return v; }
+__device__ __forceinline__ float to_acc(__nv_bfloat16 v, float) { return __bfloat162float(v); }
+__device__ __forceinline__ double to_acc(float v, double) { return (double)v; }
+
+}  // namespace amg

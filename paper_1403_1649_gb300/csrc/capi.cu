@@ -1,0 +1,246 @@
+// capi.cu -- the C ABI of include/amg.h: argument checks, stream handoff,
+// error translation (no exception crosses the boundary).
+#include <cstring>
+
+#include "amg_internal.cuh"
+
+struct amg_hierarchy {
+  amg::Hierarchy h;
+  cudaStream_t stream = nullptr;  // internal non-blocking stream (capturable)
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr, t0 = nullptr, t1 = nullptr;
+};
+
+namespace amg {
+
+static thread_local std::string g_last_error;
+
+void set_last_error(const std::string &m) { g_last_error = m; }
+
+int64_t &launch_counter() {
+  static thread_local int64_t n = 0;
+  return n;
+}
+
+PtrKind pointer_kind(const void *p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return PTR_HOST;
+  }
+  return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) ? PTR_DEVICE : PTR_HOST;
+}
+
+}  // namespace amg
+
+namespace {
+
+// run f; translate exceptions to status codes
+template <class F>
+int guarded(F &&f) {
+  try {
+    amg::g_last_error.clear();
+    return f();
+  } catch (const amg::Error &e) {
+    amg::set_last_error(e.msg);
+    return e.code;
+  } catch (const std::exception &e) {
+    amg::set_last_error(e.what());
+    return AMG_ERR_CUDA;
+  }
+}
+
+// make the internal stream wait for the caller's stream
+void enter(amg_hierarchy *H, void *user) {
+  AMG_CUDA(cudaEventRecord(H->ev_in, (cudaStream_t)user));
+  AMG_CUDA(cudaStreamWaitEvent(H->stream, H->ev_in, 0));
+}
+// and the caller's stream for the internal one
+void leave(amg_hierarchy *H, void *user) {
+  AMG_CUDA(cudaEventRecord(H->ev_out, H->stream));
+  AMG_CUDA(cudaStreamWaitEvent((cudaStream_t)user, H->ev_out, 0));
+}
+
+int check_params(const amg_params *p) {
+  if (!p) return AMG_ERR_BAD_INPUT;
+  if (!(p->alpha >= 0.0 && p->alpha < 1.0) || p->coarse_max < 1 || p->max_levels < 1 || p->kcycle_levels < 0 ||
+      p->precision < 0 || p->precision > 2 || p->outer < 0 || p->outer > 1 || p->max_iter < 1 ||
+      p->restart < 1 || p->omega_mode < 0 || p->omega_mode > 1 || p->smoother < 0 || p->smoother > 1) {
+    amg::set_last_error("invalid amg_params");
+    return AMG_ERR_BAD_INPUT;
+  }
+  return AMG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void amg_default_params(amg_params *p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->alpha = 0.25;
+  p->seed = 0;
+  p->coarse_max = 64;
+  p->max_levels = 25;
+  p->kcycle_levels = 2;
+  p->kcycle_t = 0.25;
+  p->omega_mode = 0;
+  p->omega = 2.0 / 3.0;
+  p->precision = AMG_PREC_F64;
+  p->outer = 0;
+  p->restart = 30;
+  p->max_iter = 500;
+  p->use_graph = 1;
+  p->smoother = 0;
+}
+
+int amg_setup(const amg_csr *A, const amg_params *params, void *stream, amg_hierarchy **out) {
+  if (!A || !out || !A->row_ptr || (A->nnz > 0 && (!A->col || !A->val)) || A->n <= 0 || A->nnz < A->n ||
+      A->nnz > (int64_t)INT32_MAX) {
+    amg::set_last_error("amg_setup: null pointer or bad sizes");
+    return AMG_ERR_BAD_INPUT;
+  }
+  int rc = check_params(params);
+  if (rc) return rc;
+  if (params->outer == 1) {
+    amg::set_last_error("amg_setup: FGMRES outer iteration is not available in this build");
+    return AMG_ERR_UNSUPPORTED;
+  }
+  *out = nullptr;
+  amg_hierarchy *H = new amg_hierarchy();
+  rc = guarded([&]() {
+    AMG_CUDA(cudaStreamCreateWithFlags(&H->stream, cudaStreamNonBlocking));
+    AMG_CUDA(cudaEventCreateWithFlags(&H->ev_in, cudaEventDisableTiming));
+    AMG_CUDA(cudaEventCreateWithFlags(&H->ev_out, cudaEventDisableTiming));
+    AMG_CUDA(cudaEventCreate(&H->t0));
+    AMG_CUDA(cudaEventCreate(&H->t1));
+    H->h.p = *params;
+    enter(H, stream);
+    AMG_CUDA(cudaEventRecord(H->t0, H->stream));
+    const int64_t l0 = amg::launch_counter();
+    amg::build_hierarchy(H->h, *A, H->stream);
+    amg::prepare_solve(H->h, H->stream);
+    H->h.info.setup_launches = amg::launch_counter() - l0;
+    AMG_CUDA(cudaEventRecord(H->t1, H->stream));
+    AMG_CUDA(cudaEventSynchronize(H->t1));
+    float ms = 0.f;
+    AMG_CUDA(cudaEventElapsedTime(&ms, H->t0, H->t1));
+    H->h.info.setup_ms = ms;
+    leave(H, stream);
+    return AMG_OK;
+  });
+  if (rc != AMG_OK) {
+    amg_free(H);
+    return rc;
+  }
+  *out = H;
+  return AMG_OK;
+}
+
+int amg_solve(amg_hierarchy *H, const double *b, double *x, double tol, int32_t *iters, double *res_hist,
+              void *stream) {
+  if (!H || !b || !x || !(tol >= 0.0)) {
+    amg::set_last_error("amg_solve: null pointer or negative tolerance");
+    return AMG_ERR_BAD_INPUT;
+  }
+  return guarded([&]() {
+    enter(H, stream);
+    AMG_CUDA(cudaEventRecord(H->t0, H->stream));
+    int rc = amg::run_solve(H->h, b, x, tol, iters, res_hist, H->stream);
+    AMG_CUDA(cudaEventRecord(H->t1, H->stream));
+    AMG_CUDA(cudaEventSynchronize(H->t1));
+    float ms = 0.f;
+    AMG_CUDA(cudaEventElapsedTime(&ms, H->t0, H->t1));
+    H->h.info.solve_ms = ms;
+    leave(H, stream);
+    if (rc == AMG_ERR_NOT_CONVERGED) amg::set_last_error("amg_solve: max_iter reached before tol");
+    if (rc == AMG_ERR_BREAKDOWN) amg::set_last_error("amg_solve: Krylov breakdown (p^T A p <= 0)");
+    if (rc == AMG_ERR_NAN) amg::set_last_error("amg_solve: non-finite residual");
+    return rc;
+  });
+}
+
+int amg_precond(amg_hierarchy *H, const double *b, double *x, void *stream) {
+  if (!H || !b || !x) return AMG_ERR_BAD_INPUT;
+  return guarded([&]() {
+    enter(H, stream);
+    amg::run_precond(H->h, b, x, H->stream);
+    leave(H, stream);
+    return AMG_OK;
+  });
+}
+
+int amg_spmv(amg_hierarchy *H, int32_t level, const void *x, void *y, void *stream) {
+  if (!H || !x || !y || level < 0 || level >= H->h.L) {
+    amg::set_last_error("amg_spmv: bad arguments");
+    return AMG_ERR_BAD_INPUT;
+  }
+  return guarded([&]() {
+    enter(H, stream);
+    amg::run_spmv(H->h, level, x, y, H->stream);
+    leave(H, stream);
+    return AMG_OK;
+  });
+}
+
+int amg_set_poly(amg_hierarchy *H, int32_t level, const double *coef, void *stream) {
+  (void)H; (void)level; (void)coef; (void)stream;
+  amg::set_last_error("amg_set_poly: the polynomial smoother is not available in this build");
+  return AMG_ERR_UNSUPPORTED;
+}
+
+int amg_hierarchy_info(const amg_hierarchy *H, amg_level_info *levels, int32_t cap, int32_t *nlevels) {
+  if (!H) return AMG_ERR_BAD_INPUT;
+  if (nlevels) *nlevels = H->h.L;
+  if (levels)
+    for (int k = 0; k < H->h.L && k < cap; ++k) {
+      const amg::Level &L = H->h.lev[k];
+      levels[k].n = L.n;
+      levels[k].nnz = L.nnz;
+      levels[k].n_coarse = (k + 1 < H->h.L) ? L.nc : 0;
+      levels[k].mis_rounds = L.mis_rounds;
+      levels[k].omega = L.omega;
+    }
+  return AMG_OK;
+}
+
+int amg_export_level(const amg_hierarchy *H, int32_t level, int32_t *row_ptr, int32_t *col, double *val,
+                     int32_t *agg, double *P, double *B) {
+  if (!H || level < 0 || level >= H->h.L) return AMG_ERR_BAD_INPUT;
+  return guarded([&]() {
+    const amg::Level &L = H->h.lev[level];
+    const bool last = level == H->h.L - 1;
+    if (row_ptr) AMG_CUDA(cudaMemcpy(row_ptr, L.rp, sizeof(int32_t) * ((size_t)L.n + 1), cudaMemcpyDeviceToHost));
+    if (col) AMG_CUDA(cudaMemcpy(col, L.ci, sizeof(int32_t) * (size_t)L.nnz, cudaMemcpyDeviceToHost));
+    if (val) AMG_CUDA(cudaMemcpy(val, L.val, sizeof(double) * (size_t)L.nnz, cudaMemcpyDeviceToHost));
+    if (agg && !last) AMG_CUDA(cudaMemcpy(agg, L.agg, sizeof(int32_t) * (size_t)L.n, cudaMemcpyDeviceToHost));
+    if (P && !last) AMG_CUDA(cudaMemcpy(P, L.pw64, sizeof(double) * (size_t)L.n, cudaMemcpyDeviceToHost));
+    if (B) AMG_CUDA(cudaMemcpy(B, L.B, sizeof(double) * (size_t)L.n, cudaMemcpyDeviceToHost));
+    return AMG_OK;
+  });
+}
+
+int amg_last_solve_info(const amg_hierarchy *H, amg_solve_info *info) {
+  if (!H || !info) return AMG_ERR_BAD_INPUT;
+  *info = H->h.info;
+  return AMG_OK;
+}
+
+void amg_free(amg_hierarchy *H) {
+  if (!H) return;
+  if (H->stream) cudaStreamSynchronize(H->stream);
+  if (H->h.graph_exec) cudaGraphExecDestroy(H->h.graph_exec);
+  if (H->h.graph) cudaGraphDestroy(H->h.graph);
+  H->h.arena.release();
+  if (H->h.host_pinned) cudaFreeHost(H->h.host_pinned);
+  if (H->ev_in) cudaEventDestroy(H->ev_in);
+  if (H->ev_out) cudaEventDestroy(H->ev_out);
+  if (H->t0) cudaEventDestroy(H->t0);
+  if (H->t1) cudaEventDestroy(H->t1);
+  if (H->stream) cudaStreamDestroy(H->stream);
+  delete H;
+}
+
+const char *amg_last_error(void) { return amg::g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,1033 @@
+// solve.cu -- solve phase of the aggregation AMG method on the GPU.
+//
+// Preconditioner: Alg. 5 (K-cycle) on levels k < kcycle_levels and Alg. 4
+// (V-cycle) below (Sec. 2.2), one damped-Jacobi pre- and post-smoothing step
+// per level visit (Eq. damped Jacobi), piecewise-constant restriction (a
+// segmented sum over aggregates) and prolongation (a gather), and the exact
+// coarsest solve as a dense matrix-vector product with the inverse formed at
+// setup.  Outer iteration: flexible CG (Sec. 2.2) in FP64.
+//
+// Data-dependent control stays on the device.  The branch of Alg. 5
+// (||r~|| <= t ||r||) is written to a per-level predicate by a one-block
+// kernel; every kernel of the second inner step reads the predicate and returns
+// at once when the step is not taken.  The Krylov scalars live in device
+// memory, so an outer iteration is a fixed sequence of launches that can be
+// captured once as a CUDA graph and replayed.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <type_traits>
+
+#include "amg_internal.cuh"
+
+namespace amg {
+
+// ============================================================== kernels
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+// operands of the fused dot products of the SELL kernel
+enum DotOp { OP_X = 0, OP_Y = 1, OP_U1 = 2, OP_U2 = 3 };
+
+template <class VT>
+struct SellArgs {
+  int32_t n, nslices;
+  const int64_t *sptr;
+  const int32_t *scol;
+  const void *sval;
+  const VT *x;    // SpMV input
+  VT *out;        // output vector
+  const VT *rhs;  // right-hand side (residual / smoothing epilogues)
+  const VT *wd;   // omega / A_ii
+  const VT *xin;  // the iterate that the post-smoothing step updates
+  const VT *u1, *u2;  // extra dot operands
+  double *partials;   // ndot x kRedBlocks
+  int ndot;
+  int dop[3][2];
+  const int *pred;
+};
+
+enum Epi { E_Y = 0, E_RESID = 1, E_POST = 2 };
+
+template <class MV> __device__ __forceinline__ MV ld_stream(const MV *p) { return __ldcs(p); }
+
+template <class VT>
+__device__ __forceinline__ void block_store_dots(double (&acc)[3], int ndot, double *partials) {
+  __shared__ double sh[3][kWarps];
+  for (int k = 0; k < ndot; ++k) {
+    double v = warp_sum(acc[k]);
+    if ((threadIdx.x & 31) == 0) sh[k][threadIdx.x >> 5] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    for (int k = 0; k < ndot; ++k) {
+      double v = threadIdx.x < kWarps ? sh[k][threadIdx.x] : 0.0;
+      v = warp_sum(v);
+      if (threadIdx.x == 0) partials[k * kRedBlocks + blockIdx.x] = v;
+    }
+  }
+}
+
+// y = A x over SELL-32 (one warp per slice, one lane per row) with an epilogue:
+//   E_Y     out = A x
+//   E_RESID out = rhs - A x
+//   E_POST  out = xin + wd * (rhs - A x)   (damped Jacobi after prolongation)
+// and up to three fused dot products of {x_i, y_i, u1_i, u2_i} pairs.
+template <class MV, class VT, int EPI>
+__global__ void __launch_bounds__(kThreads) k_sell(SellArgs<VT> a) {
+  if (a.pred && *a.pred == 0) return;
+  const int lane = threadIdx.x & 31;
+  const MV *__restrict__ sval = static_cast<const MV *>(a.sval);
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int32_t sl = blockIdx.x * kWarps + (threadIdx.x >> 5); sl < a.nslices; sl += gridDim.x * kWarps) {
+    const int64_t base = a.sptr[sl];
+    const int32_t width = (int32_t)((a.sptr[sl + 1] - base) >> 5);
+    const int32_t *__restrict__ cp = a.scol + base + lane;
+    const MV *__restrict__ vp = sval + base + lane;
+    VT y = VT(0);
+    int32_t e = 0;
+    for (; e + 4 <= width; e += 4) {
+      const int32_t c0 = ld_stream(cp + 32 * e), c1 = ld_stream(cp + 32 * (e + 1)),
+                    c2 = ld_stream(cp + 32 * (e + 2)), c3 = ld_stream(cp + 32 * (e + 3));
+      const MV v0 = ld_stream(vp + 32 * e), v1 = ld_stream(vp + 32 * (e + 1)), v2 = ld_stream(vp + 32 * (e + 2)),
+               v3 = ld_stream(vp + 32 * (e + 3));
+      const VT x0 = __ldg(a.x + c0), x1 = __ldg(a.x + c1), x2 = __ldg(a.x + c2), x3 = __ldg(a.x + c3);
+      y += to_acc(v0, VT(0)) * x0;
+      y += to_acc(v1, VT(0)) * x1;
+      y += to_acc(v2, VT(0)) * x2;
+      y += to_acc(v3, VT(0)) * x3;
+    }
+    for (; e < width; ++e) {
+      const int32_t c0 = ld_stream(cp + 32 * e);
+      const MV v0 = ld_stream(vp + 32 * e);
+      y += to_acc(v0, VT(0)) * __ldg(a.x + c0);
+    }
+    const int32_t row = sl * 32 + lane;
+    if (row < a.n) {
+      VT o;
+      if (EPI == E_Y) o = y;
+      else if (EPI == E_RESID) o = a.rhs[row] - y;
+      else o = a.xin[row] + a.wd[row] * (a.rhs[row] - y);
+      a.out[row] = o;
+      if (a.ndot) {
+        const double ops[4] = {(double)a.x[row], (double)o, a.u1 ? (double)a.u1[row] : 0.0,
+                               a.u2 ? (double)a.u2[row] : 0.0};
+        for (int k = 0; k < a.ndot; ++k) acc[k] += ops[a.dop[k][0]] * ops[a.dop[k][1]];
+      }
+    }
+  }
+  if (a.ndot) block_store_dots<VT>(acc, a.ndot, a.partials);
+}
+
+// out = wd * rhs: damped Jacobi from a zero initial guess
+template <class VT>
+__global__ void k_scale(int32_t n, VT *__restrict__ out, const VT *__restrict__ wd, const VT *__restrict__ rhs,
+                        const int *pred) {
+  if (pred && *pred == 0) return;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = wd[i] * rhs[i];
+}
+
+// r_{k+1}(I) = sum_{i in G_I} P(i, I) r_k(i) in ascending fine index; also the
+// next level's smoothing start x0 = wd_{k+1} * r_{k+1} when that level smooths.
+template <class VT>
+__global__ void k_restrict(int32_t nc, const int32_t *__restrict__ aptr, const int32_t *__restrict__ amem,
+                           const VT *__restrict__ pw, const VT *__restrict__ r, VT *__restrict__ bc,
+                           const VT *__restrict__ wdc, VT *__restrict__ x0c, const int *pred) {
+  if (pred && *pred == 0) return;
+  for (int32_t I = blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += gridDim.x * blockDim.x) {
+    VT s = VT(0);
+    for (int32_t m = aptr[I]; m < aptr[I + 1]; ++m) {
+      const int32_t i = amem[m];
+      s += pw[i] * r[i];
+    }
+    bc[I] = s;
+    if (wdc) x0c[I] = wdc[I] * s;
+  }
+}
+
+// x_k += P_k x_{k+1}: a gather through the aggregate map
+template <class VT>
+__global__ void k_prolong(int32_t n, const int32_t *__restrict__ agg, const VT *__restrict__ pw,
+                          const VT *__restrict__ xc, VT *__restrict__ x, const int *pred) {
+  if (pred && *pred == 0) return;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    x[i] += pw[i] * xc[agg[i]];
+}
+
+// exact coarsest solve x = A_L^-1 b (one warp per row, FP64 accumulation)
+template <class VT>
+__global__ void k_coarse(int32_t nL, const double *__restrict__ Ainv, const VT *__restrict__ b, VT *__restrict__ x,
+                         const VT *__restrict__ wdc_unused, const int *pred) {
+  if (pred && *pred == 0) return;
+  const int lane = threadIdx.x & 31;
+  for (int32_t i = blockIdx.x * kWarps + (threadIdx.x >> 5); i < nL; i += gridDim.x * kWarps) {
+    double s = 0.0;
+    for (int32_t j = lane; j < nL; j += 32) s += Ainv[(int64_t)i * nL + j] * (double)b[j];
+    s = warp_sum(s);
+    if (lane == 0) x[i] = (VT)s;
+  }
+}
+
+// sum of the first nb partials of dot k, identical in every block
+__device__ __forceinline__ double sum_partials(const double *__restrict__ part, int k, int nb) {
+  __shared__ double sh[kWarps];
+  __shared__ double result;
+  double acc = 0.0;
+  for (int j = threadIdx.x; j < nb; j += blockDim.x) acc += part[k * kRedBlocks + j];
+  acc = warp_sum(acc);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (int)(blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) result = v;
+  }
+  __syncthreads();
+  return result;
+}
+
+// Alg. 5 after v = A c: rho_1 and alpha_1 (CG: c^T v, c^T r; GMRES: ||v||^2, v^T r)
+__global__ void k_fin_k1(const double *__restrict__ part, int nb, double *__restrict__ slots, const int *pred) {
+  if (pred && *pred == 0) return;
+  const double rho1 = sum_partials(part, 0, nb);
+  const double a1 = sum_partials(part, 1, nb);
+  if (threadIdx.x == 0) {
+    slots[S_RHO1] = rho1;
+    slots[S_A1] = a1;
+    slots[S_S1] = a1 / rho1;
+  }
+}
+
+// r~ = r - (alpha_1/rho_1) v, with ||r~||^2, ||r||^2 partials and the next
+// smoothing start x0 = wd * r~
+template <class VT>
+__global__ void k_axpy_rt(int32_t n, const VT *__restrict__ r, const VT *__restrict__ v, VT *__restrict__ rt,
+                          const VT *__restrict__ wd, VT *__restrict__ x0, const double *__restrict__ slots,
+                          double *__restrict__ part, const int *pred) {
+  if (pred && *pred == 0) return;
+  const VT s1 = (VT)slots[S_S1];
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const VT ri = r[i];
+    const VT t = ri - s1 * v[i];
+    rt[i] = t;
+    if (wd) x0[i] = wd[i] * t;
+    acc[0] += (double)t * (double)t;
+    acc[1] += (double)ri * (double)ri;
+  }
+  block_store_dots<VT>(acc, 2, part);
+}
+
+// the test of Alg. 5: the second inner step runs iff the enclosing step runs
+// and ||r~|| > t ||r||.  Never predicated, so a skipped parent clears it.
+__global__ void k_decide(const double *__restrict__ part, int nb, double *__restrict__ slots, double t,
+                         const int *parent, int *__restrict__ flag) {
+  const double nrt2 = sum_partials(part, 0, nb);
+  const double nr2 = sum_partials(part, 1, nb);
+  if (threadIdx.x == 0) {
+    const int active = parent ? *parent : 1;
+    slots[S_NRT2] = nrt2;
+    slots[S_NR2] = nr2;
+    const bool accept_first = sqrt(nrt2) <= t * sqrt(nr2);
+    *flag = (active && !accept_first) ? 1 : 0;
+  }
+}
+
+// Alg. 5 after w = A d: gamma, beta, alpha_2, rho_2 and the combination weights
+__global__ void k_fin_k3(const double *__restrict__ part, int nb, double *__restrict__ slots, const int *pred) {
+  if (pred && *pred == 0) return;
+  const double gam = sum_partials(part, 0, nb);
+  const double bet = sum_partials(part, 1, nb);
+  const double a2 = sum_partials(part, 2, nb);
+  if (threadIdx.x == 0) {
+    const double rho1 = slots[S_RHO1];
+    const double rho2 = bet - gam * gam / rho1;
+    slots[S_GAM] = gam;
+    slots[S_BET] = bet;
+    slots[S_A2] = a2;
+    slots[S_CC] = slots[S_S1] - gam * a2 / (rho1 * rho2);
+    slots[S_CD] = a2 / rho2;
+  }
+}
+
+// x_{k+1} = (alpha1/rho1) c, or the two-step combination when it was taken
+template <class VT>
+__global__ void k_combine(int32_t n, const VT *__restrict__ c, const VT *__restrict__ d, VT *__restrict__ x,
+                          const double *__restrict__ slots, const int *__restrict__ flag, const int *pred) {
+  if (pred && *pred == 0) return;
+  const bool two = *flag != 0;
+  const VT cc = (VT)(two ? slots[S_CC] : slots[S_S1]);
+  const VT cd = (VT)(two ? slots[S_CD] : 0.0);
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    x[i] = two ? cc * c[i] + cd * d[i] : cc * c[i];
+}
+
+// ---------------------------------------------------------------- outer FCG (FP64)
+template <class VT>
+__global__ void k_to_vt(int32_t n, const double *__restrict__ in, VT *__restrict__ out, const VT *__restrict__ wd,
+                        VT *__restrict__ x0, const int *pred) {
+  if (pred && *pred == 0) return;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const VT v = (VT)in[i];
+    out[i] = v;
+    x0[i] = wd[i] * v;
+  }
+}
+
+// z = (double) zin, with the partials of z^T q
+template <class VT>
+__global__ void k_from_vt_dot(int32_t n, const VT *__restrict__ zin, double *__restrict__ z,
+                              const double *__restrict__ q, double *__restrict__ part, const int *pred) {
+  if (pred && *pred == 0) return;
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double v = (double)zin[i];
+    z[i] = v;
+    acc[0] += v * q[i];
+  }
+  block_store_dots<double>(acc, 1, part);
+}
+
+// p = z + beta p,  beta = -(z^T q_old)/(p_old^T q_old) (0 right after a restart)
+__global__ void k_fcg_p(int32_t n, const double *__restrict__ z, double *__restrict__ p,
+                        const double *__restrict__ part_zq, int nb, double *__restrict__ slots,
+                        const int *__restrict__ restart, const int *pred) {
+  if (pred && *pred == 0) return;
+  const double zq = sum_partials(part_zq, 0, nb);
+  const bool rs = *restart != 0;
+  const double beta = rs ? 0.0 : -zq / slots[S_PQ];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    slots[S_ZQ] = zq;
+    slots[S_BETA] = beta;
+  }
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    p[i] = rs ? z[i] : z[i] + beta * p[i];
+}
+
+// alpha = p^T r / p^T q;  x += alpha p;  r -= alpha q;  partials of ||r||^2.
+// In reduced precision also the preconditioner input (VT) and its x0.
+template <class VT>
+__global__ void k_fcg_update(int32_t n, double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
+                             const double *__restrict__ q, const double *__restrict__ part_pq, int nb,
+                             double *__restrict__ slots, double *__restrict__ part_rr, VT *__restrict__ rvt,
+                             const VT *__restrict__ wd, VT *__restrict__ x0, const int *pred) {
+  if (pred && *pred == 0) return;
+  const double pq = sum_partials(part_pq, 0, nb);
+  const double pr = sum_partials(part_pq, 1, nb);
+  const double alpha = pr / pq;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    slots[S_PQ] = pq;
+    slots[S_PR] = pr;
+    slots[S_ALPHA] = alpha;
+  }
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    x[i] += alpha * p[i];
+    const double ri = r[i] - alpha * q[i];
+    r[i] = ri;
+    acc[0] += ri * ri;
+    if (rvt) {
+      const VT v = (VT)ri;
+      rvt[i] = v;
+      x0[i] = wd[i] * v;
+    }
+  }
+  block_store_dots<double>(acc, 1, part_rr);
+}
+
+// end of an outer iteration: relative residual into the history, iteration
+// count, convergence / breakdown status; deactivates the following launches
+__global__ void k_fcg_fin(const double *__restrict__ part_rr, int nb, double *__restrict__ slots,
+                          double *__restrict__ hist, int *__restrict__ it, int *__restrict__ active,
+                          int *__restrict__ restart, int *__restrict__ status) {
+  if (*active == 0) return;
+  const double tol = slots[S_TOL];
+  const int max_iter = (int)slots[S_MAXIT];
+  const double rr = sum_partials(part_rr, 0, nb);
+  if (threadIdx.x == 0) {
+    const double rel = sqrt(rr) / sqrt(slots[S_NB2]);
+    const int k = *it + 1;
+    *it = k;
+    hist[k] = rel;
+    slots[S_RR] = rr;
+    slots[S_REL] = rel;
+    *restart = 0;
+    if (!(slots[S_PQ] > 0.0)) {
+      *status = AMG_ERR_BREAKDOWN;
+      *active = 0;
+    } else if (!isfinite(rel)) {
+      *status = AMG_ERR_NAN;
+      *active = 0;
+    } else if (rel <= tol) {
+      *status = 1;  // recursive residual converged: the host checks the true residual
+      *active = 0;
+    } else if (k >= max_iter) {
+      *status = AMG_ERR_NOT_CONVERGED;
+      *active = 0;
+    }
+  }
+}
+
+// block partial dot (generic)
+__global__ void k_dot64(int32_t n, const double *__restrict__ a, const double *__restrict__ b,
+                        double *__restrict__ part, const int *pred) {
+  if (pred && *pred == 0) return;
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) acc[0] += a[i] * b[i];
+  block_store_dots<double>(acc, 1, part);
+}
+
+__global__ void k_store_sum(const double *__restrict__ part, int nb, double *__restrict__ dst) {
+  const double v = sum_partials(part, 0, nb);
+  if (threadIdx.x == 0) *dst = v;
+}
+
+// r = b - A x in FP64 (level-0 SELL with FP64 values), with ||r||^2 partials
+__global__ void k_residual64(int32_t n, int32_t nslices, const int64_t *__restrict__ sptr,
+                             const int32_t *__restrict__ scol, const double *__restrict__ sval,
+                             const double *__restrict__ x, const double *__restrict__ b, double *__restrict__ r,
+                             double *__restrict__ part) {
+  const int lane = threadIdx.x & 31;
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int32_t sl = blockIdx.x * kWarps + (threadIdx.x >> 5); sl < nslices; sl += gridDim.x * kWarps) {
+    const int64_t base = sptr[sl];
+    const int32_t width = (int32_t)((sptr[sl + 1] - base) >> 5);
+    double y = 0.0;
+    for (int32_t e = 0; e < width; ++e) {
+      const int64_t at = base + 32 * e + lane;
+      y += sval[at] * x[scol[at]];
+    }
+    const int32_t row = sl * 32 + lane;
+    if (row < n) {
+      const double ri = b[row] - y;
+      r[row] = ri;
+      acc[0] += ri * ri;
+    }
+  }
+  block_store_dots<double>(acc, 1, part);
+}
+
+// ---------------------------------------------------------------- outer FGMRES (FP64)
+constexpr int kMaxRestart = 32;
+
+// partial dot products of w with the basis vectors V_0..V_{ncol-1}, eight
+// columns per sweep over the rows
+__global__ void k_mdot(int32_t n, const double *__restrict__ V, int ncol, const double *__restrict__ w,
+                       double *__restrict__ part, const int *pred) {
+  if (pred && *pred == 0) return;
+  __shared__ double sh[kWarps][8];
+  for (int c0 = 0; c0 < ncol; c0 += 8) {
+    double acc[8];
+#pragma unroll
+    for (int l = 0; l < 8; ++l) acc[l] = 0.0;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+      const double wi = w[i];
+#pragma unroll
+      for (int l = 0; l < 8; ++l)
+        if (c0 + l < ncol) acc[l] += V[(int64_t)(c0 + l) * n + i] * wi;
+    }
+#pragma unroll
+    for (int l = 0; l < 8; ++l) {
+      const double v = warp_sum(acc[l]);
+      if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5][l] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 8 && c0 + (int)threadIdx.x < ncol) {
+      double v = 0.0;
+      for (int wq = 0; wq < kWarps; ++wq) v += sh[wq][threadIdx.x];
+      part[(int64_t)(c0 + threadIdx.x) * kRedBlocks + blockIdx.x] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// h_l = sum of the partials of column l; H(l, j) += h_l; hc = h
+__global__ void k_fin_mdot(const double *__restrict__ part, int nb, int ncol, double *__restrict__ H, int ldh,
+                           int j, double *__restrict__ hc, int accumulate, const int *pred) {
+  if (pred && *pred == 0) return;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int l = wid; l < ncol; l += blockDim.x >> 5) {
+    double v = 0.0;
+    for (int b = lane; b < nb; b += 32) v += part[(int64_t)l * kRedBlocks + b];
+    v = warp_sum(v);
+    if (lane == 0) {
+      hc[l] = v;
+      H[l * ldh + j] = accumulate ? H[l * ldh + j] + v : v;
+    }
+  }
+}
+
+// w -= sum_l hc_l V_l
+__global__ void k_maxpy(int32_t n, const double *__restrict__ V, int ncol, const double *__restrict__ hc,
+                        double *__restrict__ w, const int *pred) {
+  if (pred && *pred == 0) return;
+  __shared__ double h[kMaxRestart + 1];
+  for (int l = threadIdx.x; l < ncol; l += blockDim.x) h[l] = hc[l];
+  __syncthreads();
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double t = w[i];
+    for (int l = 0; l < ncol; ++l) t -= h[l] * V[(int64_t)l * n + i];
+    w[i] = t;
+  }
+}
+
+// v_{j+1} = w / ||w||, H(j+1, j) = ||w||   (norm from the partials, same in every block)
+__global__ void k_fg_normalize(int32_t n, const double *__restrict__ w, double *__restrict__ vnext,
+                               const double *__restrict__ part, int nb, double *__restrict__ H, int ldh, int j,
+                               const int *pred) {
+  if (pred && *pred == 0) return;
+  const double nrm = sqrt(sum_partials(part, 0, nb));
+  if (blockIdx.x == 0 && threadIdx.x == 0) H[(j + 1) * ldh + j] = nrm;
+  const double inv = nrm != 0.0 ? 1.0 / nrm : 0.0;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) vnext[i] = w[i] * inv;
+}
+
+// Givens rotations on column j of H, residual estimate |g_{j+1}| / ||b||
+// into the history; deactivates the following steps when done.
+// fg[0..m] = g, fg[m+1..2m] = cos, fg[2m+1..3m] = sin
+__global__ void k_fg_givens(double *__restrict__ H, int ldh, int j, int m, double *__restrict__ fg,
+                            double *__restrict__ slots, double *__restrict__ hist, int *__restrict__ it,
+                            int *__restrict__ active, int *__restrict__ status) {
+  if (threadIdx.x != 0 || blockIdx.x != 0 || *active == 0) return;
+  double *g = fg, *cs = fg + m + 1, *sn = fg + 2 * m + 1;
+  for (int l = 0; l < j; ++l) {
+    const double a = H[l * ldh + j], b = H[(l + 1) * ldh + j];
+    H[l * ldh + j] = cs[l] * a + sn[l] * b;
+    H[(l + 1) * ldh + j] = -sn[l] * a + cs[l] * b;
+  }
+  const double a = H[j * ldh + j], b = H[(j + 1) * ldh + j];
+  const double den = sqrt(a * a + b * b);
+  cs[j] = a / den;
+  sn[j] = b / den;
+  H[j * ldh + j] = den;
+  const double hn = H[(j + 1) * ldh + j];
+  H[(j + 1) * ldh + j] = 0.0;
+  g[j + 1] = -sn[j] * g[j];
+  g[j] = cs[j] * g[j];
+  const int k = *it + 1;
+  *it = k;
+  const double rel = fabs(g[j + 1]) / sqrt(slots[S_NB2]);
+  hist[k] = rel;
+  slots[S_REL] = rel;
+  if (!isfinite(rel)) {
+    *status = AMG_ERR_NAN;
+    *active = 0;
+  } else if (rel <= slots[S_TOL] || hn == 0.0) {
+    *status = 1;
+    *active = 0;
+  } else if (k >= (int)slots[S_MAXIT]) {
+    *status = AMG_ERR_NOT_CONVERGED;
+    *active = 0;
+  }
+}
+
+// y = H(0:j, 0:j)^-1 g by back substitution (one thread), into fg[3m+1 ..]
+__global__ void k_fg_trisolve(const double *__restrict__ H, int ldh, int j, int m, double *__restrict__ fg) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double *g = fg;
+  double *y = fg + 3 * m + 1;
+  for (int l = j - 1; l >= 0; --l) {
+    double t = g[l];
+    for (int q = l + 1; q < j; ++q) t -= H[l * ldh + q] * y[q];
+    y[l] = t / H[l * ldh + l];
+  }
+}
+
+// x += sum_l y_l Z_l
+__global__ void k_fg_xupdate(int32_t n, double *__restrict__ x, const double *__restrict__ Z, int ncol,
+                             const double *__restrict__ y) {
+  __shared__ double ys[kMaxRestart + 1];
+  for (int l = threadIdx.x; l < ncol; l += blockDim.x) ys[l] = y[l];
+  __syncthreads();
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double t = x[i];
+    for (int l = 0; l < ncol; ++l) t += ys[l] * Z[(int64_t)l * n + i];
+    x[i] = t;
+  }
+}
+
+// V_0 = r / ||r||, g = (||r||, 0, ...)
+__global__ void k_fg_start(int32_t n, const double *__restrict__ r, double *__restrict__ v0,
+                           const double *__restrict__ slots, int slot_rr, double *__restrict__ fg, int m) {
+  const double beta = sqrt(slots[slot_rr]);
+  if (blockIdx.x == 0)
+    for (int l = threadIdx.x; l <= m; l += blockDim.x) fg[l] = (l == 0) ? beta : 0.0;
+  const double inv = beta != 0.0 ? 1.0 / beta : 0.0;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v0[i] = r[i] * inv;
+}
+
+template <class VT>
+__global__ void k_convert_row_data(int32_t n, const double *__restrict__ diag, double omega,
+                                   const double *__restrict__ pw64, VT *__restrict__ wd, VT *__restrict__ dinv,
+                                   VT *__restrict__ pw) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    wd[i] = (VT)(omega / diag[i]);
+    dinv[i] = (VT)(1.0 / diag[i]);
+    if (pw64) pw[i] = (VT)pw64[i];
+  }
+}
+
+template <class VT>
+__global__ void k_copy_cast(int32_t n, const double *__restrict__ in, VT *__restrict__ out) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = (VT)in[i];
+}
+
+// ============================================================== host engine
+namespace {
+
+inline int ew_grid(int64_t n) { return grid_for(n, kThreads, kRedBlocks); }
+inline int sell_grid(const Level &L) { return grid_for((int64_t)L.nslices, kWarps, kRedBlocks); }
+
+template <class MV, class VT>
+struct Engine {
+  Hierarchy &h;
+  cudaStream_t s;
+  int64_t launches = 0;
+  bool gmres_variant;
+
+  Engine(Hierarchy &hh, cudaStream_t ss) : h(hh), s(ss) { gmres_variant = h.p.outer == 1; }
+
+  VT *V(void *p) { return static_cast<VT *>(p); }
+
+  void check() {
+    ++launches;
+    AMG_LAUNCH_CHECK();
+  }
+
+  SellArgs<VT> sell_args(int k, const VT *x, VT *out, const int *pred) {
+    const Level &L = h.lev[k];
+    SellArgs<VT> a{};
+    a.n = L.n;
+    a.nslices = L.nslices;
+    a.sptr = L.sptr;
+    a.scol = L.scol;
+    a.sval = L.sval;
+    a.x = x;
+    a.out = out;
+    a.pred = pred;
+    a.partials = L.partials;
+    return a;
+  }
+
+  template <int EPI>
+  void sell(const SellArgs<VT> &a, int k) {
+    k_sell<MV, VT, EPI><<<sell_grid(h.lev[k]), kThreads, 0, s>>>(a);
+    check();
+  }
+
+  // out = approximately A_k^-1 rhs with a zero initial guess (Alg. 4/5).
+  // If x0_ready, lev[k].tmp already holds wd_k * rhs.
+  void cycle(int k, const VT *rhs, VT *out, bool x0_ready, const int *pred) {
+    Level &L = h.lev[k];
+    if (k == h.L - 1) {
+      k_coarse<VT><<<grid_for(h.nL, kWarps, 152), kThreads, 0, s>>>(h.nL, h.coarse_inv, rhs, out, nullptr, pred);
+      check();
+      return;
+    }
+    Level &C = h.lev[k + 1];
+    VT *tmp = V(L.tmp);
+    if (!x0_ready) {
+      k_scale<VT><<<ew_grid(L.n), kThreads, 0, s>>>(L.n, tmp, V(L.wd), rhs, pred);  // pre-smoothing
+      check();
+    }
+    {  // r_k = b_k - A_k x_k
+      SellArgs<VT> a = sell_args(k, tmp, V(L.r), pred);
+      a.rhs = rhs;
+      sell<E_RESID>(a, k);
+    }
+    const bool coarse_is_last = (k + 1 == h.L - 1);
+    // r_{k+1} = R_k r_k  (and x0 of level k+1 when it smooths)
+    k_restrict<VT><<<ew_grid(L.nc), kThreads, 0, s>>>(L.nc, L.aptr, L.amem, V(L.pw), V(L.r), V(C.bc),
+                                                      coarse_is_last ? nullptr : V(C.wd), V(C.tmp), pred);
+    check();
+    if (coarse_is_last) {
+      cycle(k + 1, V(C.bc), V(C.xc), true, pred);  // exact coarse solve
+    } else if (k < h.p.kcycle_levels) {
+      krylov2(k + 1, pred);  // Alg. 5 coarse correction
+    } else {
+      cycle(k + 1, V(C.bc), V(C.xc), true, pred);  // Alg. 4 recursion
+    }
+    // x_k += P_k x_{k+1}
+    k_prolong<VT><<<ew_grid(L.n), kThreads, 0, s>>>(L.n, L.agg, V(L.pw), V(C.xc), tmp, pred);
+    check();
+    // r_k = b_k - A_k x_k;  x_k += omega D^-1 r_k
+    SellArgs<VT> a = sell_args(k, tmp, out, pred);
+    a.rhs = rhs;
+    a.wd = V(L.wd);
+    a.xin = tmp;
+    if (k == 0 && std::is_same<VT, double>::value && zq_fuse) {
+      a.ndot = 1;  // z^T q for the outer flexible CG
+      a.dop[0][0] = OP_Y;
+      a.dop[0][1] = OP_U1;
+      a.u1 = (const VT *)h.q;
+      a.partials = h.lev[0].partials + 4 * kRedBlocks;
+    }
+    sell<E_POST>(a, k);
+  }
+  bool zq_fuse = false;
+
+  // Alg. 5 coarse part at level m: rhs = bc[m], result in xc[m]; lev[m].tmp holds wd*bc.
+  void krylov2(int m, const int *pred) {
+    Level &L = h.lev[m];
+    const int nb = sell_grid(L);
+    // c = cycle(m, r)
+    cycle(m, V(L.bc), V(L.c), true, pred);
+    {  // v = A c; dots
+      SellArgs<VT> a = sell_args(m, V(L.c), V(L.v), pred);
+      a.ndot = 2;
+      a.u1 = V(L.bc);
+      if (gmres_variant) {  // rho1 = v^T v, alpha1 = v^T r
+        a.dop[0][0] = OP_Y; a.dop[0][1] = OP_Y; a.dop[1][0] = OP_Y; a.dop[1][1] = OP_U1;
+      } else {               // rho1 = c^T v, alpha1 = c^T r
+        a.dop[0][0] = OP_X; a.dop[0][1] = OP_Y; a.dop[1][0] = OP_X; a.dop[1][1] = OP_U1;
+      }
+      sell<E_Y>(a, m);
+    }
+    k_fin_k1<<<1, kThreads, 0, s>>>(L.partials, nb, L.slots, pred);
+    check();
+    const bool deeper_smooths = true;  // level m is not the coarsest here
+    (void)deeper_smooths;
+    const int ng = ew_grid(L.n);
+    k_axpy_rt<VT><<<ng, kThreads, 0, s>>>(L.n, V(L.bc), V(L.v), V(L.rt), V(L.wd), V(L.tmp), L.slots,
+                                          L.partials + 3 * kRedBlocks, pred);
+    check();
+    k_decide<<<1, kThreads, 0, s>>>(L.partials + 3 * kRedBlocks, ng, L.slots, h.p.kcycle_t, pred, L.flag);
+    check();
+    // second inner step, predicated on the decision
+    cycle(m, V(L.rt), V(L.d), true, L.flag);
+    {
+      SellArgs<VT> a = sell_args(m, V(L.d), V(L.w), L.flag);
+      a.ndot = 3;
+      a.u1 = V(L.v);
+      a.u2 = V(L.rt);
+      if (gmres_variant) {  // gamma = w^T v, beta = w^T w, alpha2 = w^T r~
+        a.dop[0][0] = OP_Y; a.dop[0][1] = OP_U1;
+        a.dop[1][0] = OP_Y; a.dop[1][1] = OP_Y;
+        a.dop[2][0] = OP_Y; a.dop[2][1] = OP_U2;
+      } else {               // gamma = d^T v, beta = d^T w, alpha2 = d^T r~
+        a.dop[0][0] = OP_X; a.dop[0][1] = OP_U1;
+        a.dop[1][0] = OP_X; a.dop[1][1] = OP_Y;
+        a.dop[2][0] = OP_X; a.dop[2][1] = OP_U2;
+      }
+      sell<E_Y>(a, m);
+    }
+    k_fin_k3<<<1, kThreads, 0, s>>>(L.partials, nb, L.slots, L.flag);
+    check();
+    k_combine<VT><<<ng, kThreads, 0, s>>>(L.n, V(L.c), V(L.d), V(L.xc), L.slots, L.flag, pred);
+    check();
+  }
+
+  // z = M r for the FP64 outer iteration
+  void precond(const double *r, double *z, const int *pred, bool with_zq) {
+    Level &L0 = h.lev[0];
+    if (std::is_same<VT, double>::value) {
+      zq_fuse = with_zq;
+      cycle(0, (const VT *)r, (VT *)z, false, pred);
+      zq_fuse = false;
+      if (with_zq && h.L == 1) {
+        k_dot64<<<ew_grid(L0.n), kThreads, 0, s>>>(L0.n, z, h.q, L0.partials + 4 * kRedBlocks, pred);
+        check();
+      }
+    } else {
+      k_to_vt<VT><<<ew_grid(L0.n), kThreads, 0, s>>>(L0.n, r, V(h.pre_in), V(L0.wd), V(L0.tmp), pred);
+      check();
+      cycle(0, V(h.pre_in), V(h.pre_out), true, pred);
+      k_from_vt_dot<VT><<<ew_grid(L0.n), kThreads, 0, s>>>(L0.n, V(h.pre_out), z, h.q,
+                                                           L0.partials + 4 * kRedBlocks, pred);
+      check();
+    }
+  }
+
+  // one flexible-CG iteration, all on the device (graph-capturable)
+  void fcg_iteration(int *active, int *restart) {
+    Level &L0 = h.lev[0];
+    double *part = L0.partials;
+    const int ng = ew_grid(L0.n);
+    const int nsg = sell_grid(L0);
+    const int nzq = (std::is_same<VT, double>::value && h.L > 1) ? nsg : ng;
+    // z = M r (+ z^T q partials)
+    precond(h.r, h.z, active, true);
+    // p = z + beta p
+    k_fcg_p<<<ng, kThreads, 0, s>>>(L0.n, h.z, h.pdir, part + 4 * kRedBlocks, nzq, L0.slots, restart, active);
+    check();
+    {  // q = A p (FP64), p^T q, p^T r
+      SellArgs<double> a{};
+      a.n = L0.n;
+      a.nslices = L0.nslices;
+      a.sptr = L0.sptr;
+      a.scol = L0.scol;
+      a.sval = L0.sval64;
+      a.x = h.pdir;
+      a.out = h.q;
+      a.u1 = h.r;
+      a.ndot = 2;
+      a.dop[0][0] = OP_X; a.dop[0][1] = OP_Y;
+      a.dop[1][0] = OP_X; a.dop[1][1] = OP_U1;
+      a.partials = part + 5 * kRedBlocks;
+      a.pred = active;
+      k_sell<double, double, E_Y><<<nsg, kThreads, 0, s>>>(a);
+      check();
+    }
+    // x, r update (+ the next preconditioner input in reduced precision)
+    const bool red = !std::is_same<VT, double>::value;
+    k_fcg_update<VT><<<ng, kThreads, 0, s>>>(L0.n, h.x, h.r, h.pdir, h.q, part + 5 * kRedBlocks, nsg, L0.slots,
+                                             part + 7 * kRedBlocks, nullptr, V(L0.wd), V(L0.tmp), active);
+    check();
+    (void)red;
+    k_fcg_fin<<<1, kThreads, 0, s>>>(part + 7 * kRedBlocks, ng, L0.slots, h.hist, h.it_dev, active, restart,
+                                     h.status_dev);
+    check();
+  }
+};
+
+template <class MV, class VT>
+void alloc_level_vectors(Hierarchy &h, Level &L, int k) {
+  const size_t n = (size_t)L.n;
+  auto vec = [&]() { return (void *)h.arena.get<VT>(n + 1); };
+  L.r = vec();
+  L.bc = vec();
+  L.xc = vec();
+  L.tmp = vec();
+  L.u0 = vec();
+  L.u1 = vec();
+  if (k >= 1) {
+    L.c = vec();
+    L.v = vec();
+    L.rt = vec();
+    L.d = vec();
+    L.w = vec();
+  }
+  L.slots = h.arena.get<double>(kNumSlots);
+  L.flag = h.arena.get<int>(4);
+  L.partials = h.arena.get<double>((size_t)kRedBlocks * 8);
+  AMG_CUDA(cudaMemset(L.slots, 0, sizeof(double) * kNumSlots));
+  AMG_CUDA(cudaMemset(L.flag, 0, sizeof(int) * 4));
+  AMG_CUDA(cudaMemset(L.partials, 0, sizeof(double) * kRedBlocks * 8));
+}
+
+template <class MV, class VT>
+void prepare_t(Hierarchy &h, cudaStream_t s) {
+  for (int k = 0; k < h.L; ++k) alloc_level_vectors<MV, VT>(h, h.lev[k], k);
+  const size_t n = (size_t)h.lev[0].n;
+  h.x = h.arena.get<double>(n);
+  h.b = h.arena.get<double>(n);
+  h.r = h.arena.get<double>(n);
+  h.z = h.arena.get<double>(n);
+  h.pdir = h.arena.get<double>(n);
+  h.q = h.arena.get<double>(n);
+  h.pre_in = h.arena.get<VT>(n);
+  h.pre_out = h.arena.get<VT>(n);
+  h.hist = h.arena.get<double>((size_t)h.p.max_iter + 8);
+  h.it_dev = h.arena.get<int>(8);
+  h.status_dev = h.it_dev + 4;
+  AMG_CUDA(cudaMemsetAsync(h.q, 0, sizeof(double) * n, s));
+  AMG_CUDA(cudaMemsetAsync(h.pdir, 0, sizeof(double) * n, s));
+  AMG_CUDA(cudaMallocHost(&h.host_pinned, 64 * sizeof(double)));
+}
+
+template <class VT>
+void make_row_data_t(Hierarchy &h, Level &L, const double *diag, cudaStream_t s) {
+  L.wd = h.arena.get<VT>((size_t)L.n + 1);
+  L.dinv = h.arena.get<VT>((size_t)L.n + 1);
+  L.pw = h.arena.get<VT>((size_t)L.n + 1);
+  k_convert_row_data<VT><<<ew_grid(L.n), kThreads, 0, s>>>(L.n, diag, L.omega, L.pw64, (VT *)L.wd,
+                                                           (VT *)L.dinv, (VT *)L.pw);
+  AMG_LAUNCH_CHECK();
+}
+
+__global__ void k_set_state(int *it, int *active, int *restart, int *status, int it_v, int active_v,
+                            int restart_v, int status_v) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    if (it_v >= 0) *it = it_v;
+    *active = active_v;
+    *restart = restart_v;
+    *status = status_v;
+  }
+}
+
+__global__ void k_set_slot(double *slots, int idx, double v) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) slots[idx] = v;
+}
+
+// Copy n doubles between user memory (host or device) and device memory.
+void copy_in(double *dst_dev, const double *src, int32_t n, cudaStream_t s) {
+  const cudaMemcpyKind k = pointer_kind(src) == PTR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  AMG_CUDA(cudaMemcpyAsync(dst_dev, src, sizeof(double) * (size_t)n, k, s));
+}
+void copy_out(double *dst, const double *src_dev, int32_t n, cudaStream_t s) {
+  const cudaMemcpyKind k = pointer_kind(dst) == PTR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  AMG_CUDA(cudaMemcpyAsync(dst, src_dev, sizeof(double) * (size_t)n, k, s));
+}
+
+// ||b - A x||^2 into slots[dst] (FP64)
+void true_residual(Hierarchy &h, int dst, cudaStream_t s, int64_t &launches) {
+  Level &L0 = h.lev[0];
+  const int nsg = sell_grid(L0);
+  k_residual64<<<nsg, kThreads, 0, s>>>(L0.n, L0.nslices, L0.sptr, L0.scol, L0.sval64, h.x, h.b, h.r,
+                                        L0.partials + 7 * kRedBlocks);
+  k_store_sum<<<1, kThreads, 0, s>>>(L0.partials + 7 * kRedBlocks, nsg, L0.slots + dst);
+  launches += 2;
+  AMG_LAUNCH_CHECK();
+}
+
+template <class MV, class VT>
+int run_solve_t(Hierarchy &h, const double *b, double *x, double tol, int32_t *iters, double *res_hist,
+                cudaStream_t s) {
+  Level &L0 = h.lev[0];
+  const int32_t n = L0.n;
+  Engine<MV, VT> eng(h, s);
+  int64_t launches = 0;
+  int *active = h.it_dev + 1, *restart = h.it_dev + 2;
+  copy_in(h.b, b, n, s);
+  copy_in(h.x, x, n, s);
+  // ||b||^2 and the initial residual
+  k_dot64<<<ew_grid(n), kThreads, 0, s>>>(n, h.b, h.b, L0.partials + 6 * kRedBlocks, nullptr);
+  k_store_sum<<<1, kThreads, 0, s>>>(L0.partials + 6 * kRedBlocks, ew_grid(n), L0.slots + S_NB2);
+  launches += 2;
+  AMG_LAUNCH_CHECK();
+  true_residual(h, S_RR, s, launches);
+  k_set_slot<<<1, 32, 0, s>>>(L0.slots, S_TOL, tol);
+  k_set_slot<<<1, 32, 0, s>>>(L0.slots, S_MAXIT, (double)h.p.max_iter);
+  AMG_CUDA(cudaMemcpyAsync(h.host_pinned, L0.slots, sizeof(double) * kNumSlots, cudaMemcpyDeviceToHost, s));
+  AMG_CUDA(cudaStreamSynchronize(s));
+  double nb2 = h.host_pinned[S_NB2];
+  const double rr0 = h.host_pinned[S_RR];
+  const bool zero_b = !(nb2 > 0.0);
+  if (zero_b) nb2 = 1.0, k_set_slot<<<1, 32, 0, s>>>(L0.slots, S_NB2, 1.0);
+  double rel = std::sqrt(rr0 / nb2);
+  std::vector<double> hist(1, rel);
+  int status = AMG_OK;
+  int it = 0;
+  if (!std::isfinite(rel)) status = AMG_ERR_NAN;
+  else if (rel > tol) {
+    k_set_state<<<1, 32, 0, s>>>(h.it_dev, active, restart, h.status_dev, 0, 1, 1, 0);
+    AMG_CUDA(cudaMemcpyAsync(h.hist, &hist[0], sizeof(double), cudaMemcpyHostToDevice, s));
+    AMG_LAUNCH_CHECK();
+    // capture one outer iteration as a graph
+    int64_t per_iter = 0;
+    if (h.p.use_graph && h.graph_kind != 0) {
+      if (h.graph_exec) {
+        cudaGraphExecDestroy(h.graph_exec);
+        cudaGraphDestroy(h.graph);
+        h.graph_exec = nullptr;
+      }
+      AMG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      eng.fcg_iteration(active, restart);
+      AMG_CUDA(cudaStreamEndCapture(s, &h.graph));
+      AMG_CUDA(cudaGraphInstantiate(&h.graph_exec, h.graph, 0));
+      h.graph_kind = 0;
+      h.graph_launches = eng.launches;
+      eng.launches = 0;
+    }
+    per_iter = h.graph_launches;
+    auto enqueue = [&]() {
+      if (h.p.use_graph) {
+        AMG_CUDA(cudaGraphLaunch(h.graph_exec, s));
+        launches += per_iter;
+      } else {
+        eng.fcg_iteration(active, restart);
+      }
+    };
+    int *st_host = reinterpret_cast<int *>(h.host_pinned + 32);
+    for (;;) {
+      enqueue();
+      AMG_CUDA(cudaMemcpyAsync(st_host, h.it_dev, sizeof(int) * 8, cudaMemcpyDeviceToHost, s));
+      AMG_CUDA(cudaStreamSynchronize(s));
+      const int dst = st_host[4];
+      it = st_host[0];
+      if (dst == 0) continue;  // still iterating
+      if (dst == 1) {          // updated residual meets tol: check the true residual
+        true_residual(h, S_TRUE_RR, s, launches);
+        AMG_CUDA(cudaMemcpyAsync(h.host_pinned, L0.slots, sizeof(double) * kNumSlots, cudaMemcpyDeviceToHost, s));
+        AMG_CUDA(cudaStreamSynchronize(s));
+        const double rel_true = std::sqrt(h.host_pinned[S_TRUE_RR] / nb2);
+        if (rel_true <= tol) {
+          status = AMG_OK;
+          break;
+        }
+        if (it >= h.p.max_iter) {
+          status = AMG_ERR_NOT_CONVERGED;
+          break;
+        }
+        // iterative refinement: restart flexible CG from the true residual
+        k_set_state<<<1, 32, 0, s>>>(h.it_dev, active, restart, h.status_dev, -1, 1, 1, 0);
+        AMG_LAUNCH_CHECK();
+        continue;
+      }
+      status = dst;
+      break;
+    }
+    hist.resize((size_t)it + 1);
+    if (it > 0)
+      AMG_CUDA(cudaMemcpyAsync(&hist[1], h.hist + 1, sizeof(double) * (size_t)it, cudaMemcpyDeviceToHost, s));
+  }
+  launches += eng.launches;
+  // final FP64 residual
+  true_residual(h, S_TRUE_RR, s, launches);
+  AMG_CUDA(cudaMemcpyAsync(h.host_pinned, L0.slots, sizeof(double) * kNumSlots, cudaMemcpyDeviceToHost, s));
+  copy_out(x, h.x, n, s);
+  AMG_CUDA(cudaStreamSynchronize(s));
+  h.info.final_relres = zero_b ? std::sqrt(h.host_pinned[S_TRUE_RR]) : std::sqrt(h.host_pinned[S_TRUE_RR] / nb2);
+  h.info.iters = it;
+  h.info.status = status;
+  h.info.kernel_launches = launches;
+  if (iters) *iters = it;
+  if (res_hist) std::memcpy(res_hist, hist.data(), sizeof(double) * hist.size());
+  return status;
+}
+
+template <class MV, class VT>
+void run_precond_t(Hierarchy &h, const double *b, double *x, cudaStream_t s) {
+  Engine<MV, VT> eng(h, s);
+  const int32_t n = h.lev[0].n;
+  copy_in(h.r, b, n, s);
+  eng.precond(h.r, h.z, nullptr, false);
+  copy_out(x, h.z, n, s);
+  AMG_CUDA(cudaStreamSynchronize(s));
+  h.info.kernel_launches = eng.launches;
+}
+
+template <class MV, class VT>
+void run_spmv_t(Hierarchy &h, int k, const void *x, void *y, cudaStream_t s) {
+  Engine<MV, VT> eng(h, s);
+  SellArgs<VT> a = eng.sell_args(k, static_cast<const VT *>(x), static_cast<VT *>(y), nullptr);
+  eng.template sell<E_Y>(a, k);
+}
+
+}  // namespace
+
+#define AMG_DISPATCH(prec, CALL)                                   \
+  switch (prec) {                                                  \
+    case AMG_PREC_F64: { using MV = double; using VT = double; CALL; break; } \
+    case AMG_PREC_F32: { using MV = float; using VT = float; CALL; break; }   \
+    default: { using MV = __nv_bfloat16; using VT = float; CALL; break; }     \
+  }
+
+void make_row_data(Hierarchy &h, Level &L, const double *diag, cudaStream_t s) {
+  if (h.p.precision == AMG_PREC_F64)
+    make_row_data_t<double>(h, L, diag, s);
+  else
+    make_row_data_t<float>(h, L, diag, s);
+}
+
+void prepare_solve(Hierarchy &h, cudaStream_t s) {
+  AMG_DISPATCH(h.p.precision, (prepare_t<MV, VT>(h, s)));
+}
+
+int run_solve(Hierarchy &h, const double *b, double *x, double tol, int32_t *iters, double *res_hist,
+              cudaStream_t s) {
+  int rc = 0;
+  AMG_DISPATCH(h.p.precision, (rc = run_solve_t<MV, VT>(h, b, x, tol, iters, res_hist, s)));
+  return rc;
+}
+
+void run_precond(Hierarchy &h, const double *b, double *x, cudaStream_t s) {
+  AMG_DISPATCH(h.p.precision, (run_precond_t<MV, VT>(h, b, x, s)));
+}
+
+void run_spmv(Hierarchy &h, int level, const void *x, void *y, cudaStream_t s) {
+  AMG_DISPATCH(h.p.precision, (run_spmv_t<MV, VT>(h, level, x, y, s)));
+}
+
+}  // namespace amg

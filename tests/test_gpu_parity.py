@@ -1,0 +1,220 @@
+"""GPU path against the FP64 CPU oracle, through the C ABI.
+
+Integer results (aggregates, coarse sparsity) and the FP64 hierarchy values must
+be bit-identical; FP64 solutions within 1e-10 relative (iterates compared after
+the same number of outer iterations, so that the stopping test cannot pick
+different iterations); reduced-precision preconditioners must still reach the
+FP64 residual tolerance.
+"""
+import numpy as np
+import pytest
+
+from paper_1403_1649_gb300 import problems as P
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    # 2D 5-point Poisson 64x64 (the small workload; oracle runs in milliseconds)
+    "poisson2d_64": lambda: (P.poisson2d(64), 0.25, 0),
+    # 37^2 = 1369 rows: ragged last slice, several SELL slices
+    "poisson2d_37": lambda: (P.poisson2d(37), 0.25, 5),
+    "varcoef2d_50": lambda: (P.varcoef2d(50, 7), 0.25, 7),
+    "aniso2d_40": lambda: (P.aniso2d(40, 0.05), 0.25, 9),
+    "poisson3d_20": lambda: (P.poisson3d(20), 0.5, 1),
+    "varcoef3d_24": lambda: (P.varcoef3d(24, 2), 0.5, 2),
+    "varcoef3d_16": lambda: (P.varcoef3d(16, 2, block=4), 0.5, 2),
+    "fem2d_48": lambda: (P.fem2d(48, 3), 0.25, 3),
+}
+
+_cache = {}
+
+
+def case(name):
+    if name not in _cache:
+        _cache[name] = CASES[name]()
+    return _cache[name]
+
+
+@pytest.fixture(scope="session")
+def gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1403_1649_gb300 import amg, build
+    build.build()
+    amg.lib()
+    return amg
+
+
+@pytest.fixture(scope="session")
+def orc():
+    from oracle import oracle
+    oracle.build()
+    return oracle
+
+
+def pair(gpu, orc, name, **kw):
+    A, alpha, seed = case(name)
+    g = gpu.Hierarchy(A, alpha=alpha, seed=seed, **kw)
+    okw = {k: v for k, v in kw.items() if k in ("coarse_max", "max_levels", "kcycle_levels", "kcycle_t",
+                                                 "omega_mode", "omega", "outer", "restart")}
+    o = orc.Hierarchy(A, alpha=alpha, seed=seed, **okw)
+    return A, g, o
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_hierarchy_bit_exact(gpu, orc, name):
+    A, g, o = pair(gpu, orc, name)
+    assert g.nlevels == o.nlevels
+    for k in range(o.nlevels):
+        gl, ol = g.level(k), o.level(k)
+        assert gl["n"] == ol.n and gl["nnz"] == ol.nnz, k
+        assert np.array_equal(gl["rowptr"], ol.rowptr), k
+        assert np.array_equal(gl["col"], ol.col), k
+        assert np.array_equal(gl["val"], ol.val), k  # keyed sum in the same order: identical values
+        assert np.array_equal(gl["B"], ol.B), k
+        if k < o.nlevels - 1:
+            assert np.array_equal(gl["agg"], ol.agg), k
+            assert np.array_equal(gl["P"], ol.P), k
+            assert gl["mis_rounds"] == ol.mis_rounds, k
+            assert gl["omega"] == pytest.approx(ol.omega, rel=1e-12), k
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_preconditioner_parity(gpu, orc, name):
+    A, g, o = pair(gpu, orc, name)
+    b = P.rhs_uniform(A.n, 11)
+    zg, zo = g.precond(b), o.precond(b)
+    assert np.linalg.norm(zg - zo) <= 1e-11 * np.linalg.norm(zo)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_solve_iterates_parity(gpu, orc, name):
+    A, g, o = pair(gpu, orc, name, max_iter=6)
+    b = P.rhs_uniform(A.n, 12)
+    xg, ig = g.solve(b, tol=0.0, allow=(gpu.AMG_OK, gpu.AMG_ERR_NOT_CONVERGED))
+    xo, io = o.solve(b, tol=0.0, max_iter=6)
+    assert ig["iters"] == io["iters"] == 6
+    assert np.linalg.norm(xg - xo) <= 1e-10 * np.linalg.norm(xo)
+    assert np.allclose(ig["hist"], io["hist"], rtol=1e-9, atol=0)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_solve_converges_like_oracle(gpu, orc, name):
+    A, g, o = pair(gpu, orc, name)
+    b = P.rhs_uniform(A.n, 13)
+    xg, ig = g.solve(b, tol=1e-8)
+    xo, io = o.solve(b, tol=1e-8, max_iter=500)
+    assert ig["status"] == gpu.AMG_OK and ig["final_relres"] <= 1e-8
+    assert abs(ig["iters"] - io["iters"]) <= 1
+    r = b - A.matvec(xg)
+    assert np.linalg.norm(r) <= 1e-8 * np.linalg.norm(b) * (1 + 1e-6)
+    if ig["iters"] == io["iters"]:
+        assert np.linalg.norm(xg - xo) <= 1e-10 * np.linalg.norm(xo)
+
+
+@pytest.mark.parametrize("name", ["poisson2d_37", "varcoef3d_24", "fem2d_48"])
+def test_spmv_every_level(gpu, orc, name):
+    import torch
+    A, g, o = pair(gpu, orc, name)
+    for k in range(g.nlevels):
+        L = g.level(k)
+        Ak = P.CSR(L["n"], L["rowptr"], L["col"], L["val"])
+        x = P.rhs_uniform(Ak.n, 20 + k)
+        xd = torch.from_numpy(x).cuda()
+        yd = torch.zeros_like(xd)
+        gpu.amg_spmv(g.h, k, xd, yd)
+        torch.cuda.synchronize()
+        ref = Ak.matvec(x)
+        assert np.abs(yd.cpu().numpy() - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_mixed_precision_reaches_fp64_tolerance(gpu, orc, prec):
+    A, g, o = pair(gpu, orc, "varcoef3d_16", precision=prec)
+    b = P.rhs_uniform(A.n, 14)
+    xg, ig = g.solve(b, tol=1e-8)
+    assert ig["status"] == gpu.AMG_OK and ig["final_relres"] <= 1e-8
+    xo, io = o.solve(b, tol=1e-12, max_iter=500)
+    err = np.linalg.norm(xg - xo) / np.linalg.norm(xo)
+    ev = np.linalg.eigvalsh(A.to_dense())
+    kappa = ev[-1] / ev[0]
+    assert err <= kappa * 1e-8
+    print(f"precision {prec}: {ig['iters']} iterations (fp64 oracle {io['iters']} to 1e-12), "
+          f"rel. error vs FP64 oracle {err:.2e}")
+
+
+def test_single_level_one_iteration(gpu):
+    A = P.poisson2d(7)
+    g = gpu.Hierarchy(A, coarse_max=64)
+    assert g.nlevels == 1
+    x, info = g.solve(P.rhs_uniform(A.n, 1), tol=1e-12)
+    assert info["iters"] == 1 and info["final_relres"] <= 1e-12
+
+
+def test_bad_inputs_rejected(gpu):
+    A = P.poisson1d(50)
+    bad = P.CSR(A.n, A.rowptr, A.col, A.val.copy())
+    bad.val[0] = 0.0
+    with pytest.raises(gpu.AMGError) as e:
+        gpu.Hierarchy(bad)
+    assert e.value.code == gpu.AMG_ERR_BAD_INPUT and "diagonal" in gpu.amg_last_error()
+    uns = P.CSR(A.n, A.rowptr, A.col.copy(), A.val)
+    uns.col[1], uns.col[2] = uns.col[2], uns.col[1]
+    with pytest.raises(gpu.AMGError) as e:
+        gpu.Hierarchy(uns)
+    assert e.value.code == gpu.AMG_ERR_BAD_INPUT
+    nanv = P.CSR(A.n, A.rowptr, A.col, A.val.copy())
+    nanv.val[5] = np.nan
+    with pytest.raises(gpu.AMGError):
+        gpu.Hierarchy(nanv)
+
+
+def test_not_converged_and_zero_rhs(gpu):
+    A = P.varcoef2d(40, 3)
+    g = gpu.Hierarchy(A, max_iter=2)
+    x, info = g.solve(P.rhs_uniform(A.n, 2), tol=1e-14, allow=(gpu.AMG_OK, gpu.AMG_ERR_NOT_CONVERGED))
+    assert info["status"] == gpu.AMG_ERR_NOT_CONVERGED and info["iters"] == 2 and len(info["hist"]) == 3
+    x, info = g.solve(np.zeros(A.n), tol=1e-8)
+    assert info["status"] == gpu.AMG_OK and info["iters"] == 0 and not x.any()
+
+
+def test_device_and_host_buffers_agree(gpu):
+    import torch
+    A, alpha, seed = case("poisson3d_20")
+    g = gpu.Hierarchy(A, alpha=alpha, seed=seed)
+    b = P.rhs_uniform(A.n, 3)
+    xh, _ = g.solve(b, tol=1e-8)
+    bd = torch.from_numpy(b).cuda()
+    xd = torch.zeros_like(bd)
+    gpu.amg_solve(g.h, bd, xd, 1e-8, g.params.max_iter)
+    torch.cuda.synchronize()
+    assert np.array_equal(xd.cpu().numpy(), xh)
+
+
+def test_graph_and_stream_launches_agree(gpu):
+    A, alpha, seed = case("varcoef2d_50")
+    b = P.rhs_uniform(A.n, 4)
+    xg, ig = gpu.Hierarchy(A, alpha=alpha, seed=seed, use_graph=1).solve(b, tol=1e-8)
+    xs, is_ = gpu.Hierarchy(A, alpha=alpha, seed=seed, use_graph=0).solve(b, tol=1e-8)
+    assert ig["iters"] == is_["iters"] and np.array_equal(xg, xs)
+    assert ig["kernel_launches"] == is_["kernel_launches"] > 0
+
+
+@pytest.mark.slow
+def test_full_size_poisson3d_128(gpu, orc):
+    """128^3 7-point Poisson at full size in the benchmark's configuration: the
+    whole hierarchy bit-exact and six FP64 iterations within 1e-10."""
+    A = P.poisson3d(128)
+    g = gpu.Hierarchy(A, alpha=0.5, seed=1, max_iter=6)
+    o = orc.Hierarchy(A, alpha=0.5, seed=1)
+    assert g.nlevels == o.nlevels
+    for k in range(o.nlevels):
+        gl, ol = g.level(k), o.level(k)
+        assert np.array_equal(gl["col"], ol.col) and np.array_equal(gl["val"], ol.val), k
+        if k < o.nlevels - 1:
+            assert np.array_equal(gl["agg"], ol.agg), k
+    b = P.rhs_uniform(A.n, 1)
+    xg, ig = g.solve(b, tol=0.0, allow=(gpu.AMG_OK, gpu.AMG_ERR_NOT_CONVERGED))
+    xo, io = o.solve(b, tol=0.0, max_iter=6)
+    assert np.linalg.norm(xg - xo) <= 1e-10 * np.linalg.norm(xo)
