@@ -973,3 +973,197 @@ int32_t or_krylov2_probe(or_hier *h, int32_t m, const double *r, double *x, doub
   memcpy(d, L->d, sizeof(double) * (size_t)L->n);
   return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Learned per-row polynomial smoother.  The paper lists polynomial smoothers */
+/* as future work (Sec. 5); the coefficients here come from a small MLP on    */
+/* per-row features, trained to minimise the two-grid error reduction.        */
+/* ------------------------------------------------------------------------- */
+
+/* Features of row i (d = |A_ii|, t_j = -A_ij/d for j != i), all scale-free:
+ *  0: 1                      1: (#off-diagonals)/8
+ *  2..9: the eight largest |A_ij|/d, descending, zero-padded
+ *  10: fraction of off-diagonals with the sign of A_ii
+ *  11: (sum_j A_ij)/A_ii      12: level/4
+ *  13: min_j t_j              14: max_j t_j
+ *  15: sum_{j != i} |A_ij|/d  (sums in CSR order) */
+void or_features(int32_t n, const int32_t *rp, const int32_t *ci, const double *val, int32_t level,
+                 float *feat) {
+  for (int32_t i = 0; i < n; ++i) {
+    double aii = 0.0;
+    for (int32_t p = rp[i]; p < rp[i + 1]; ++p)
+      if (ci[p] == i) aii = val[p];
+    double d = fabs(aii), top[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double rowsum = 0.0, abssum = 0.0, tmin = 0.0, tmax = 0.0;
+    int32_t noff = 0, nsame = 0;
+    for (int32_t p = rp[i]; p < rp[i + 1]; ++p) {
+      rowsum = rowsum + val[p];
+      if (ci[p] == i) continue;
+      double a = fabs(val[p]) / d, t = -val[p] / d;
+      abssum = abssum + a;
+      if (noff == 0 || t < tmin) tmin = t;
+      if (noff == 0 || t > tmax) tmax = t;
+      if ((val[p] > 0.0 && aii > 0.0) || (val[p] < 0.0 && aii < 0.0)) nsame++;
+      noff++;
+      for (int k = 0; k < 8; ++k) /* insert into the descending top-8 list */
+        if (a > top[k]) {
+          for (int q = 7; q > k; --q) top[q] = top[q - 1];
+          top[k] = a;
+          break;
+        }
+    }
+    float *f = feat + (size_t)i * OR_NFEAT;
+    f[0] = 1.0f;
+    f[1] = (float)((double)noff / 8.0);
+    for (int k = 0; k < 8; ++k) f[2 + k] = (float)top[k];
+    f[10] = noff ? (float)((double)nsame / (double)noff) : 0.0f;
+    f[11] = (float)(rowsum / aii);
+    f[12] = (float)((double)level / 4.0);
+    f[13] = (float)tmin;
+    f[14] = (float)tmax;
+    f[15] = (float)abssum;
+  }
+}
+
+/* IEEE binary16 -> binary32 from the bit pattern (every half is exact in float) */
+static float half_to_float(uint16_t h) {
+  uint32_t sign = (uint32_t)(h >> 15) << 31, ex = (h >> 10) & 0x1F, man = h & 0x3FF, bits;
+  if (ex == 0) {
+    if (man == 0) {
+      bits = sign;
+    } else { /* subnormal: normalise */
+      int e = -1;
+      do {
+        e++;
+        man <<= 1;
+      } while (!(man & 0x400));
+      bits = sign | ((uint32_t)(127 - 15 - e) << 23) | ((man & 0x3FF) << 13);
+    }
+  } else if (ex == 31) {
+    bits = sign | 0x7F800000u | (man << 13);
+  } else {
+    bits = sign | ((ex - 15 + 127) << 23) | (man << 13);
+  }
+  float f;
+  memcpy(&f, &bits, sizeof(f));
+  return f;
+}
+
+#define W1_OFF 0
+#define B1_OFF (OR_HID * OR_NFEAT)
+#define W2_OFF (B1_OFF + OR_HID)
+#define B2_OFF (W2_OFF + OR_HID * OR_HID)
+#define W3_OFF (B2_OFF + OR_HID)
+#define B3_OFF (W3_OFF + OR_NOUT * OR_HID)
+
+void or_mlp_forward(int32_t n, const uint16_t *w16, const float *feat, float *out) {
+  float w[OR_NPARAM];
+  for (int k = 0; k < OR_NPARAM; ++k) w[k] = half_to_float(w16[k]);
+  for (int32_t i = 0; i < n; ++i) {
+    const float *f = feat + (size_t)i * OR_NFEAT;
+    float h1[OR_HID], h2[OR_HID];
+    for (int u = 0; u < OR_HID; ++u) {
+      float z = w[B1_OFF + u];
+      for (int k = 0; k < OR_NFEAT; ++k) z += w[W1_OFF + u * OR_NFEAT + k] * f[k];
+      h1[u] = tanhf(z);
+    }
+    for (int v = 0; v < OR_HID; ++v) {
+      float z = w[B2_OFF + v];
+      for (int u = 0; u < OR_HID; ++u) z += w[W2_OFF + v * OR_HID + u] * h1[u];
+      h2[v] = tanhf(z);
+    }
+    for (int q = 0; q < OR_NOUT; ++q) {
+      float z = w[B3_OFF + q];
+      for (int v = 0; v < OR_HID; ++v) z += w[W3_OFF + q * OR_HID + v] * h2[v];
+      out[(size_t)i * OR_NOUT + q] = z;
+    }
+  }
+}
+
+void or_mlp_backward(int32_t n, const double *w, const float *feat, const double *dout, double *dparam,
+                     double *out) {
+  for (int k = 0; k < OR_NPARAM; ++k) dparam[k] = 0.0;
+  for (int32_t i = 0; i < n; ++i) {
+    const float *f = feat + (size_t)i * OR_NFEAT;
+    double h1[OR_HID], h2[OR_HID], dz2[OR_HID];
+    for (int u = 0; u < OR_HID; ++u) {
+      double z = w[B1_OFF + u];
+      for (int k = 0; k < OR_NFEAT; ++k) z += w[W1_OFF + u * OR_NFEAT + k] * (double)f[k];
+      h1[u] = tanh(z);
+    }
+    for (int v = 0; v < OR_HID; ++v) {
+      double z = w[B2_OFF + v];
+      for (int u = 0; u < OR_HID; ++u) z += w[W2_OFF + v * OR_HID + u] * h1[u];
+      h2[v] = tanh(z);
+    }
+    const double *g = dout + (size_t)i * OR_NOUT;
+    for (int q = 0; q < OR_NOUT; ++q) {
+      double z = w[B3_OFF + q];
+      for (int v = 0; v < OR_HID; ++v) z += w[W3_OFF + q * OR_HID + v] * h2[v];
+      if (out) out[(size_t)i * OR_NOUT + q] = z;
+      dparam[B3_OFF + q] += g[q];
+      for (int v = 0; v < OR_HID; ++v) dparam[W3_OFF + q * OR_HID + v] += g[q] * h2[v];
+    }
+    for (int v = 0; v < OR_HID; ++v) {
+      double dh = 0.0;
+      for (int q = 0; q < OR_NOUT; ++q) dh += w[W3_OFF + q * OR_HID + v] * g[q];
+      dz2[v] = dh * (1.0 - h2[v] * h2[v]);
+      dparam[B2_OFF + v] += dz2[v];
+      for (int u = 0; u < OR_HID; ++u) dparam[W2_OFF + v * OR_HID + u] += dz2[v] * h1[u];
+    }
+    for (int u = 0; u < OR_HID; ++u) {
+      double dh = 0.0;
+      for (int v = 0; v < OR_HID; ++v) dh += w[W2_OFF + v * OR_HID + u] * dz2[v];
+      const double dz1 = dh * (1.0 - h1[u] * h1[u]);
+      dparam[B1_OFF + u] += dz1;
+      for (int k = 0; k < OR_NFEAT; ++k) dparam[W1_OFF + u * OR_NFEAT + k] += dz1 * (double)f[k];
+    }
+  }
+}
+
+/* random error vector v of the two-grid measurement: uniform in [-1, 1) */
+static double twogrid_error(uint64_t seed, int32_t v, int32_t i) {
+  uint64_t z = or_splitmix64(seed ^ ((uint64_t)(uint32_t)(v + 1) << 44) ^ (uint64_t)(uint32_t)i);
+  return 2.0 * ((double)(z >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
+}
+
+double or_twogrid_loss(or_hier *h, const double *coef, int32_t nvec, uint64_t seed, double *dcoef) {
+  if (h->L < 2) return -1.0;
+  or_level *L = &h->lev[0];
+  or_level *Cl = &h->lev[1];
+  const int32_t n = L->n, nc = Cl->n;
+  double *e0 = dalloc((size_t)n), *Ae = dalloc((size_t)n), *u0 = dalloc((size_t)n), *u1 = dalloc((size_t)n),
+         *u2 = dalloc((size_t)n), *e1 = dalloc((size_t)n), *rc = dalloc((size_t)nc);
+  double loss = 0.0;
+  if (dcoef)
+    for (int32_t i = 0; i < 3 * n; ++i) dcoef[i] = 0.0;
+  for (int32_t v = 0; v < nvec; ++v) {
+    for (int32_t i = 0; i < n; ++i) e0[i] = twogrid_error(seed, v, i);
+    spmv(L, e0, Ae);
+    const double nrm0 = dot(n, e0, Ae);
+    for (int32_t i = 0; i < n; ++i) u0[i] = L->dinv[i] * Ae[i];   /* D^-1 A e0 */
+    spmv(L, u0, u1);
+    for (int32_t i = 0; i < n; ++i) u1[i] = L->dinv[i] * u1[i];   /* (D^-1 A) D^-1 A e0 */
+    spmv(L, u1, u2);
+    for (int32_t i = 0; i < n; ++i) u2[i] = L->dinv[i] * u2[i];
+    for (int32_t i = 0; i < n; ++i) /* e1 = (I - G A) e0 */
+      e1[i] = e0[i] - (coef[3 * i] * u0[i] + coef[3 * i + 1] * u1[i] + coef[3 * i + 2] * u2[i]);
+    spmv(L, e1, Ae);                                               /* coarse correction */
+    for (int32_t I = 0; I < nc; ++I) rc[I] = 0.0;
+    for (int32_t i = 0; i < n; ++i) rc[L->agg[i]] = rc[L->agg[i]] + L->P[i] * Ae[i];
+    or_chol_solve(nc, h->chol, rc);
+    for (int32_t i = 0; i < n; ++i) e1[i] = e1[i] - L->P[i] * rc[L->agg[i]];
+    spmv(L, e1, Ae);
+    const double num = dot(n, e1, Ae);
+    loss += num / nrm0 / nvec;
+    if (dcoef) /* dL/de1 = 2 A e2 / nrm0 (A e2 is A-orthogonal to range(P)); e1 = e0 - sum c u */
+      for (int32_t i = 0; i < n; ++i) {
+        const double g = 2.0 * Ae[i] / nrm0 / nvec;
+        dcoef[3 * i] -= g * u0[i];
+        dcoef[3 * i + 1] -= g * u1[i];
+        dcoef[3 * i + 2] -= g * u2[i];
+      }
+  }
+  free(e0); free(Ae); free(u0); free(u1); free(u2); free(e1); free(rc);
+  return loss;
+}

@@ -103,6 +103,30 @@ void or_free(or_hier *h);
 /* test hook: Alg. 5 coarse part at level m, exposing the inner iterates c, d */
 int32_t or_krylov2_probe(or_hier *h, int32_t m, const double *r, double *x, double *c, double *d);
 
+/* ---- learned per-row polynomial smoother (the paper names polynomial
+ *      smoothers as future work, Sec. 5; this part is the library's own) ---- */
+#define OR_NFEAT 16
+#define OR_HID 64
+#define OR_NOUT 3
+/* parameter layout (float): W1[64][16] b1[64] W2[64][64] b2[64] W3[3][64] b3[3] */
+#define OR_NPARAM (OR_HID * OR_NFEAT + OR_HID + OR_HID * OR_HID + OR_HID + OR_NOUT * OR_HID + OR_NOUT)
+/* 16 scale-free features of every row (see the definition in amg_oracle.c) */
+void or_features(int32_t n, const int32_t *rp, const int32_t *ci, const double *val, int32_t level,
+                 float *feat);
+/* MLP 16 -> 64 -> 64 -> 3 with tanh, FP16 weights (IEEE binary16 bit patterns),
+ * FP32 arithmetic; out is n x 3 */
+void or_mlp_forward(int32_t n, const uint16_t *w16, const float *feat, float *out);
+/* FP64 forward + backward: given dL/dout (n x 3), accumulate dL/dparam (double,
+ * OR_NPARAM) for weights w (double) */
+void or_mlp_backward(int32_t n, const double *w, const float *feat, const double *dout, double *dparam,
+                     double *out);
+/* Two-grid error reduction of the pre-smoother x += sum_q diag(c_q)(D^-1 A)^q D^-1 r
+ * with exact coarse solve, on nvec seeded random errors e0:
+ *   L = mean_v ||T (I - G A) e0||_A^2 / ||e0||_A^2,  T = I - P A_c^-1 P^T A.
+ * Uses levels 0 and 1 of a two-level hierarchy.  coef: n x 3.  dcoef (nullable)
+ * gets dL/dcoef.  Returns L. */
+double or_twogrid_loss(or_hier *h, const double *coef, int32_t nvec, uint64_t seed, double *dcoef);
+
 #ifdef __cplusplus
 }
 #endif

@@ -103,6 +103,13 @@ def lib():
         L.or_free.argtypes = [C.c_void_p]
         L.or_krylov2_probe.argtypes = [C.c_void_p, C.c_int32, _f64p, _f64p, _f64p, _f64p]
         L.or_krylov2_probe.restype = C.c_int32
+        _f32p = np.ctypeslib.ndpointer(dtype=np.float32, flags="C_CONTIGUOUS")
+        _u16p = np.ctypeslib.ndpointer(dtype=np.uint16, flags="C_CONTIGUOUS")
+        L.or_features.argtypes = [C.c_int32, _i32p, _i32p, _f64p, C.c_int32, _f32p]
+        L.or_mlp_forward.argtypes = [C.c_int32, _u16p, _f32p, _f32p]
+        L.or_mlp_backward.argtypes = [C.c_int32, _f64p, _f32p, _f64p, _f64p, C.c_void_p]
+        L.or_twogrid_loss.argtypes = [C.c_void_p, _f64p, C.c_int32, C.c_uint64, C.c_void_p]
+        L.or_twogrid_loss.restype = C.c_double
         _lib = L
     return _lib
 
@@ -214,6 +221,37 @@ def chol_solve(L: np.ndarray, b: np.ndarray) -> np.ndarray:
     return x
 
 
+# ------------------------------------------------------------ learned smoother
+NFEAT, HID, NOUT = 16, 64, 3
+NPARAM = HID * NFEAT + HID + HID * HID + HID + NOUT * HID + NOUT
+
+
+def features(A, level: int = 0) -> np.ndarray:
+    n, rp, ci, v = _csr_args(A)
+    f = np.zeros((n, NFEAT), np.float32)
+    lib().or_features(n, rp, ci, v, level, f.reshape(-1))
+    return f
+
+
+def mlp_forward(w16: np.ndarray, feat: np.ndarray) -> np.ndarray:
+    """FP32 MLP with FP16 weights; w16 holds binary16 bit patterns (uint16)."""
+    w16 = np.ascontiguousarray(w16, np.uint16)
+    feat = np.ascontiguousarray(feat, np.float32)
+    out = np.zeros((feat.shape[0], NOUT), np.float32)
+    lib().or_mlp_forward(feat.shape[0], w16, feat.reshape(-1), out.reshape(-1))
+    return out
+
+
+def mlp_backward(w: np.ndarray, feat: np.ndarray, dout: np.ndarray):
+    """FP64 forward + backward: returns (dL/dparam, out) for L with dL/dout = dout."""
+    feat = np.ascontiguousarray(feat, np.float32)
+    dparam = np.zeros(NPARAM)
+    out = np.zeros((feat.shape[0], NOUT))
+    lib().or_mlp_backward(feat.shape[0], np.ascontiguousarray(w, np.float64), feat.reshape(-1),
+                          np.ascontiguousarray(dout, np.float64).reshape(-1), dparam, out.ctypes.data)
+    return dparam, out
+
+
 # ------------------------------------------------------------ whole method
 @dataclass
 class Level:
@@ -289,6 +327,13 @@ class Hierarchy:
         if lib().or_krylov2_probe(self.h, m, np.ascontiguousarray(r, np.float64), x, c, d) != 0:
             raise ValueError("level has no K-cycle coarse part")
         return x, c, d
+
+    def twogrid_loss(self, coef: np.ndarray, nvec: int = 4, seed: int = 0, grad: bool = True):
+        """Two-grid error reduction of the polynomial pre-smoother (levels 0, 1)."""
+        coef = np.ascontiguousarray(coef, np.float64).reshape(-1)
+        d = np.zeros_like(coef) if grad else None
+        L = lib().or_twogrid_loss(self.h, coef, nvec, seed, None if d is None else d.ctypes.data)
+        return L, (None if d is None else d.reshape(-1, 3))
 
     def solve(self, b: np.ndarray, x0: np.ndarray | None = None, tol: float = 1e-8, max_iter: int = 200):
         x = np.zeros(self.n) if x0 is None else np.ascontiguousarray(x0, np.float64).copy()
