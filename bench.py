@@ -43,7 +43,34 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="f32", choices=list(PREC))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-spmv", action="store_true",
+                    help="set up the workload and run two level-0 SpMV launches per precision (ncu target)")
     return ap.parse_args()
+
+
+def profile_spmv():
+    """Two level-0 SpMV launches (amg_spmv) for each preconditioner precision on the
+    128^3 workload, nothing else on the GPU after setup: the target of the ncu
+    captures summarised under profiles/."""
+    import torch
+    from paper_1403_1649_gb300 import amg, build
+    from paper_1403_1649_gb300 import problems as P
+    build.build()
+    A = P.poisson3d(M_GRID)
+    dev = torch.device("cuda", 0)
+    rp, ci, va = (torch.from_numpy(a).to(dev) for a in (A.rowptr, A.col, A.val))
+    for prec in ("f32", "f64"):
+        h = amg.amg_setup(rp, ci, va, amg.amg_default_params(alpha=ALPHA, seed=SEED, precision=PREC[prec]))
+        vt = torch.float64 if prec == "f64" else torch.float32
+        x = torch.rand(A.n, dtype=vt, device=dev)
+        y = torch.empty_like(x)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        for r in range(2):
+            flush.fill_(r)
+            amg.amg_spmv(h, 0, x, y)
+        torch.cuda.synchronize()
+        amg.amg_free(h)
+    print("profile-spmv done")
 
 
 def dist_init():
@@ -196,6 +223,9 @@ def ncu_traffic(precision: str):
 
 def main():
     args = parse()
+    if args.profile_spmv:
+        profile_spmv()
+        return
     ws, rank, local = dist_init()
     if args.impl == "reference":
         run_reference(args, ws, rank)

@@ -81,6 +81,8 @@ typedef struct amg_params {
   int32_t use_graph;     /* 1: replay one outer iteration as a captured CUDA graph          */
   int32_t smoother;      /* 0: damped Jacobi; 1: per-row polynomial smoother whose
                             coefficients are set with amg_set_poly                         */
+  int32_t tail;          /* 1: run the coarse levels (at most 65536 rows, below the
+                            K-cycle levels) in one thread-block-cluster launch per visit   */
 } amg_params;
 
 typedef struct amg_level_info {
@@ -105,7 +107,7 @@ typedef struct amg_hierarchy amg_hierarchy;
 
 /* Fill *p with the defaults: alpha 0.25, seed 0, coarse_max 64, max_levels 25,
  * kcycle_levels 2, kcycle_t 0.25, omega_mode 0, omega 2/3, precision F64,
- * outer FCG, restart 30, max_iter 500, use_graph 1, smoother 0. */
+ * outer FCG, restart 30, max_iter 500, use_graph 1, smoother 0, tail 1. */
 void amg_default_params(amg_params *p);
 
 /* Alg. 1: build the hierarchy of A on the GPU.

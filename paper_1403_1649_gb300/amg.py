@@ -40,7 +40,7 @@ class amg_params(C.Structure):
                 ("max_levels", C.c_int32), ("kcycle_levels", C.c_int32), ("kcycle_t", C.c_double),
                 ("omega_mode", C.c_int32), ("omega", C.c_double), ("precision", C.c_int32),
                 ("outer", C.c_int32), ("restart", C.c_int32), ("max_iter", C.c_int32),
-                ("use_graph", C.c_int32), ("smoother", C.c_int32)]
+                ("use_graph", C.c_int32), ("smoother", C.c_int32), ("tail", C.c_int32)]
 
 
 class amg_level_info(C.Structure):

@@ -45,26 +45,41 @@ int64_t &launch_counter();
 #define AMG_COUNT() (++::amg::launch_counter())
 
 // ---------------------------------------------------------------- device memory
+// Device memory comes from one stream-ordered pool per device that keeps freed
+// blocks (release threshold = unlimited), so repeated setups do not pay for
+// cudaMalloc/cudaFree and never synchronise the device to free scratch.
+cudaMemPool_t device_pool();
+// stream of the API call in progress on this thread (allocation order)
+cudaStream_t &current_stream();
+
+inline void *pool_alloc(size_t bytes) {
+  void *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  AMG_CUDA(cudaMallocFromPoolAsync(&p, bytes, device_pool(), current_stream()));
+  return p;
+}
+inline void pool_free(void *p) {
+  if (p) cudaFreeAsync(p, current_stream());
+}
+
 // All allocations of a hierarchy go through one arena so that amg_free
 // releases everything, also after a failure half way through setup.
 struct Arena {
   std::vector<void *> blocks;
   void *alloc(size_t bytes) {
-    void *p = nullptr;
-    if (bytes == 0) bytes = 16;
-    AMG_CUDA(cudaMalloc(&p, bytes));
+    void *p = pool_alloc(bytes);
     blocks.push_back(p);
     return p;
   }
   template <class T>
   T *get(size_t n) { return static_cast<T *>(alloc(n * sizeof(T))); }
   void release() {
-    for (void *p : blocks) cudaFree(p);
+    for (void *p : blocks) pool_free(p);
     blocks.clear();
   }
 };
 
-// Temporary device buffer freed at scope exit (setup scratch).
+// Temporary device buffer returned to the pool at scope exit (setup scratch).
 template <class T>
 struct DevBuf {
   T *p = nullptr;
@@ -72,14 +87,11 @@ struct DevBuf {
   DevBuf() = default;
   explicit DevBuf(size_t count) { resize(count); }
   void resize(size_t count) {
-    if (p) cudaFree(p);
-    p = nullptr;
+    pool_free(p);
     n = count;
-    AMG_CUDA(cudaMalloc(&p, (count ? count : 1) * sizeof(T)));
+    p = static_cast<T *>(pool_alloc((count ? count : 1) * sizeof(T)));
   }
-  ~DevBuf() {
-    if (p) cudaFree(p);
-  }
+  ~DevBuf() { pool_free(p); }
   DevBuf(const DevBuf &) = delete;
   DevBuf &operator=(const DevBuf &) = delete;
 };
@@ -126,9 +138,31 @@ struct Level {
   double *partials = nullptr; // kRedBlocks * 8 doubles
 };
 
+// Per-level view used by the cluster kernel that runs the coarse tail of the
+// cycle (levels t..L-1) in one launch.
+struct TailLevel {
+  int32_t n, nslices, nc;
+  const int64_t *sptr;
+  const int32_t *scol;
+  const void *sval;
+  const void *wd, *pw;
+  const int32_t *agg, *aptr, *amem;
+  void *bc, *xc, *r, *c, *v, *rt, *d, *w;
+};
+
+struct TailArgs {
+  int t, L, mode, nL, gmres;  // mode 0: V-cycle at t; 1: Alg. 5 coarse part at t
+  double kt;                  // K-cycle threshold
+  const double *Ainv;         // coarsest inverse
+  const TailLevel *lev;       // device array indexed by level
+  const int *pred;
+};
+
 struct Hierarchy {
   amg_params p{};
   int L = 0;
+  int tail_t = -1;                 // first level of the cluster tail (-1: none)
+  TailLevel *tail_dev = nullptr;   // device copy of the per-level views
   Level lev[kMaxLevels];
   double *coarse_inv = nullptr;  // dense inverse of A_{L-1}, n_L x n_L, FP64
   int32_t nL = 0;
@@ -139,7 +173,7 @@ struct Hierarchy {
   int *it_dev = nullptr;    // device iteration counter
   int *status_dev = nullptr;
   // FGMRES
-  double *V = nullptr, *Z = nullptr, *H = nullptr, *gv = nullptr;
+  double *V = nullptr, *Z = nullptr, *H = nullptr, *fg = nullptr, *hc = nullptr, *gpart = nullptr;
   // precision bridging vectors at level 0 of the preconditioner
   void *pre_in = nullptr, *pre_out = nullptr;
   // statistics
@@ -175,6 +209,11 @@ int run_solve(Hierarchy &h, const double *b, double *x, double tol, int32_t *ite
 void run_precond(Hierarchy &h, const double *b, double *x, cudaStream_t s);
 void run_spmv(Hierarchy &h, int level, const void *x, void *y, cudaStream_t s);
 void set_poly(Hierarchy &h, int level, const double *coef_dev, cudaStream_t s);
+
+// tail.cu
+template <class MV, class VT>
+void tail_launch(const TailArgs &a, cudaStream_t s);
+constexpr int kTailMaxRows = 65536;  // largest first tail level
 
 // ---------------------------------------------------------------- device utilities
 __device__ __forceinline__ double warp_sum(double v) {

@@ -21,6 +21,30 @@ int64_t &launch_counter() {
   return n;
 }
 
+cudaStream_t &current_stream() {
+  static thread_local cudaStream_t s = nullptr;
+  return s;
+}
+
+cudaMemPool_t device_pool() {
+  static cudaMemPool_t pools[64] = {};
+  int dev = 0;
+  AMG_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) throw Error{AMG_ERR_CUDA, "device index out of range"};
+  if (!pools[dev]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    AMG_CUDA(cudaMemPoolCreate(&p, &props));
+    uint64_t keep = UINT64_MAX;
+    AMG_CUDA(cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep));
+    pools[dev] = p;
+  }
+  return pools[dev];
+}
+
 PtrKind pointer_kind(const void *p) {
   cudaPointerAttributes at{};
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
@@ -51,6 +75,7 @@ int guarded(F &&f) {
 
 // make the internal stream wait for the caller's stream
 void enter(amg_hierarchy *H, void *user) {
+  amg::current_stream() = H->stream;
   AMG_CUDA(cudaEventRecord(H->ev_in, (cudaStream_t)user));
   AMG_CUDA(cudaStreamWaitEvent(H->stream, H->ev_in, 0));
 }
@@ -92,6 +117,7 @@ void amg_default_params(amg_params *p) {
   p->max_iter = 500;
   p->use_graph = 1;
   p->smoother = 0;
+  p->tail = 1;
 }
 
 int amg_setup(const amg_csr *A, const amg_params *params, void *stream, amg_hierarchy **out) {
@@ -102,9 +128,9 @@ int amg_setup(const amg_csr *A, const amg_params *params, void *stream, amg_hier
   }
   int rc = check_params(params);
   if (rc) return rc;
-  if (params->outer == 1) {
-    amg::set_last_error("amg_setup: FGMRES outer iteration is not available in this build");
-    return AMG_ERR_UNSUPPORTED;
+  if (params->outer == 1 && params->restart > 32) {
+    amg::set_last_error("amg_setup: FGMRES restart length is limited to 32");
+    return AMG_ERR_BAD_INPUT;
   }
   *out = nullptr;
   amg_hierarchy *H = new amg_hierarchy();
@@ -184,9 +210,16 @@ int amg_spmv(amg_hierarchy *H, int32_t level, const void *x, void *y, void *stre
 }
 
 int amg_set_poly(amg_hierarchy *H, int32_t level, const double *coef, void *stream) {
-  (void)H; (void)level; (void)coef; (void)stream;
-  amg::set_last_error("amg_set_poly: the polynomial smoother is not available in this build");
-  return AMG_ERR_UNSUPPORTED;
+  if (!H || !coef || level < 0 || level >= H->h.L - 1) {
+    amg::set_last_error("amg_set_poly: bad level (the coarsest level has no smoother) or null pointer");
+    return AMG_ERR_BAD_INPUT;
+  }
+  return guarded([&]() {
+    enter(H, stream);
+    amg::set_poly(H->h, level, coef, H->stream);
+    leave(H, stream);
+    return AMG_OK;
+  });
 }
 
 int amg_hierarchy_info(const amg_hierarchy *H, amg_level_info *levels, int32_t cap, int32_t *nlevels) {
@@ -231,7 +264,9 @@ void amg_free(amg_hierarchy *H) {
   if (H->stream) cudaStreamSynchronize(H->stream);
   if (H->h.graph_exec) cudaGraphExecDestroy(H->h.graph_exec);
   if (H->h.graph) cudaGraphDestroy(H->h.graph);
+  amg::current_stream() = H->stream;
   H->h.arena.release();
+  if (H->stream) cudaStreamSynchronize(H->stream);
   if (H->h.host_pinned) cudaFreeHost(H->h.host_pinned);
   if (H->ev_in) cudaEventDestroy(H->ev_in);
   if (H->ev_out) cudaEventDestroy(H->ev_out);

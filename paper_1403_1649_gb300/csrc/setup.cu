@@ -420,7 +420,7 @@ template <> __device__ __forceinline__ __nv_bfloat16 conv_val<__nv_bfloat16>(dou
 }
 
 template <class MV>
-__global__ void k_sell_fill(int32_t n, int32_t nslices, const int32_t *__restrict__ rp,
+__global__ void k_build_sell(int32_t n, int32_t nslices, const int32_t *__restrict__ rp,
                             const int32_t *__restrict__ ci, const double *__restrict__ val,
                             const int64_t *__restrict__ sptr, int32_t *__restrict__ scol, MV *__restrict__ sval) {
   const int lane = threadIdx.x & 31;
@@ -531,10 +531,13 @@ __device__ int count_below(const double *T, int m, double sigma) {
 
 // H: (m+1) x 8 Hessenberg from the Arnoldi loop, wn[j] = ||M q_j||.  Applies
 // the breakdown rule (h_{j+1,j} <= 1e-12 ||M q_j|| ends the process after j+1
-// steps), symmetrises the leading block and sets omega = (4/3)/rho.
+// steps), symmetrises the leading block and sets omega = (4/3)/rho.  One warp:
+// multisection, every lane tests one of 32 points of the current interval, so
+// each round narrows it 33-fold (12 rounds reach double precision).
 __global__ void k_omega_from_H(const double *__restrict__ H, const double *__restrict__ wn, int m,
                                double *__restrict__ omega_out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
   int mm = m;
   for (int j = 0; j < m; ++j)
     if (H[(j + 1) * 8 + j] <= 1e-12 * wn[j] || j + 1 == m) {
@@ -552,25 +555,29 @@ __global__ void k_omega_from_H(const double *__restrict__ H, const double *__res
     g = fmax(g, rs);
   }
   g = g * (1.0 + 1e-12) + 1e-300;
-  // largest eigenvalue: sup{sigma : count_below(sigma) < mm}
-  double lo = -g, hi = g;
-  for (int it = 0; it < 200; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (mid == lo || mid == hi) break;
-    if (count_below(T, mm, mid) < mm) lo = mid; else hi = mid;
+  double ext[2];
+  for (int side = 0; side < 2; ++side) {
+    // side 0: largest eigenvalue = sup{sigma : count_below(sigma) < mm}
+    // side 1: smallest eigenvalue = sup{sigma : count_below(sigma) == 0}
+    double lo = -g, hi = g;
+    for (int it = 0; it < 40; ++it) {
+      const double sig = lo + (hi - lo) * (double)(lane + 1) / 33.0;
+      const int c = count_below(T, mm, sig);
+      const bool below = side == 0 ? (c < mm) : (c == 0);
+      // predicate is monotone in sigma: lanes 0..k-1 true, the rest false
+      const unsigned bal = __ballot_sync(0xffffffffu, below);
+      const int k = __popc(bal);
+      const double nlo = k > 0 ? __shfl_sync(0xffffffffu, sig, k - 1) : lo;
+      const double nhi = k < 32 ? __shfl_sync(0xffffffffu, sig, k < 32 ? k : 31) : hi;
+      if (nlo == lo && nhi == hi) break;
+      lo = nlo;
+      hi = nhi;
+      if (hi - lo <= 1e-16 * fmax(fabs(lo), fabs(hi))) break;
+    }
+    ext[side] = 0.5 * (lo + hi);
   }
-  const double lmax = 0.5 * (lo + hi);
-  // smallest eigenvalue: sup{sigma : count_below(sigma) == 0}
-  lo = -g;
-  hi = g;
-  for (int it = 0; it < 200; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (mid == lo || mid == hi) break;
-    if (count_below(T, mm, mid) == 0) lo = mid; else hi = mid;
-  }
-  const double lmin = 0.5 * (lo + hi);
-  const double rho = fmax(fabs(lmax), fabs(lmin));
-  *omega_out = (4.0 / 3.0) / rho;
+  const double rho = fmax(fabs(ext[0]), fabs(ext[1]));
+  if (lane == 0) *omega_out = (4.0 / 3.0) / rho;
 }
 
 // ============================================================== coarsest level
@@ -722,21 +729,21 @@ void build_solve_matrix(Hierarchy &h, Level &L, cudaStream_t s) {
   switch (h.p.precision) {
     case AMG_PREC_F64:
       L.sval = h.arena.get<double>(entries);
-      AMG_COUNT(), k_sell_fill<double><<<g, 256, 0, s>>>(n, L.nslices, L.rp, L.ci, L.val, L.sptr, L.scol, (double *)L.sval);
+      AMG_COUNT(), k_build_sell<double><<<g, 256, 0, s>>>(n, L.nslices, L.rp, L.ci, L.val, L.sptr, L.scol, (double *)L.sval);
       break;
     case AMG_PREC_F32:
       L.sval = h.arena.get<float>(entries);
-      AMG_COUNT(), k_sell_fill<float><<<g, 256, 0, s>>>(n, L.nslices, L.rp, L.ci, L.val, L.sptr, L.scol, (float *)L.sval);
+      AMG_COUNT(), k_build_sell<float><<<g, 256, 0, s>>>(n, L.nslices, L.rp, L.ci, L.val, L.sptr, L.scol, (float *)L.sval);
       break;
     default:
       L.sval = h.arena.get<__nv_bfloat16>(entries);
-      AMG_COUNT(), k_sell_fill<__nv_bfloat16><<<g, 256, 0, s>>>(n, L.nslices, L.rp, L.ci, L.val, L.sptr, L.scol,
+      AMG_COUNT(), k_build_sell<__nv_bfloat16><<<g, 256, 0, s>>>(n, L.nslices, L.rp, L.ci, L.val, L.sptr, L.scol,
                                                    (__nv_bfloat16 *)L.sval);
   }
   AMG_LAUNCH_CHECK();
   if (&L == &h.lev[0] && h.p.precision != AMG_PREC_F64) {
     L.sval64 = h.arena.get<double>(entries);
-    AMG_COUNT(), k_sell_fill<double><<<g, 256, 0, s>>>(n, L.nslices, L.rp, L.ci, L.val, L.sptr, L.scol, L.sval64);
+    AMG_COUNT(), k_build_sell<double><<<g, 256, 0, s>>>(n, L.nslices, L.rp, L.ci, L.val, L.sptr, L.scol, L.sval64);
     AMG_LAUNCH_CHECK();
   } else if (&L == &h.lev[0]) {
     L.sval64 = (double *)L.sval;

@@ -45,27 +45,55 @@ struct SellArgs {
   int ndot;
   int dop[3][2];
   const int *pred;
+  // polynomial smoother operands
+  const VT *dinv;     // 1 / A_ii
+  const VT *coef;     // n x 3 per-row coefficients c_0, c_1, c_2
+  const VT *p0, *p1;  // earlier polynomial terms
+  const VT *res;      // residual the Horner steps add back
+  VT *out2;           // second output
 };
 
-enum Epi { E_Y = 0, E_RESID = 1, E_POST = 2 };
+// epilogues of the SELL kernel (y = A x):
+//   E_Y            out = y
+//   E_RESID        out = rhs - y
+//   E_POST         out = xin + wd (rhs - y)                  damped Jacobi after prolongation
+//   E_DSCALE       out = D^-1 y                               polynomial pre-smoother, term 1
+//   E_POLYPRE      out = c0 p0 + c1 p1 + c2 D^-1 y            polynomial pre-smoother, sum
+//   E_RESID_POLY   out = rhs - y, out2 = D^-1 (c2 out)        post-smoother: residual, Horner start
+//   E_HORNER       out = D^-1 y + D^-1 (c1 res)               Horner middle step
+//   E_HORNER_LAST  out = xin + D^-1 y + D^-1 (c0 res)         Horner last step, update
+enum Epi { E_Y = 0, E_RESID = 1, E_POST = 2, E_DSCALE = 3, E_POLYPRE = 4, E_RESID_POLY = 5, E_HORNER = 6,
+           E_HORNER_LAST = 7 };
 
 template <class MV> __device__ __forceinline__ MV ld_stream(const MV *p) { return __ldcs(p); }
 
-template <class VT>
-__device__ __forceinline__ void block_store_dots(double (&acc)[3], int ndot, double *partials) {
+// per-block partial sums of up to three dot products -> partials[k*kRedBlocks + block]
+__device__ __forceinline__ void block_store_dots3(double a0, double a1, double a2, int ndot, double *partials) {
   __shared__ double sh[3][kWarps];
-  for (int k = 0; k < ndot; ++k) {
-    double v = warp_sum(acc[k]);
-    if ((threadIdx.x & 31) == 0) sh[k][threadIdx.x >> 5] = v;
+  const double in[3] = {a0, a1, a2};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    if (k < ndot) {
+      const double v = warp_sum(in[k]);
+      if ((threadIdx.x & 31) == 0) sh[k][threadIdx.x >> 5] = v;
+    }
   }
   __syncthreads();
   if (threadIdx.x < 32) {
-    for (int k = 0; k < ndot; ++k) {
-      double v = threadIdx.x < kWarps ? sh[k][threadIdx.x] : 0.0;
-      v = warp_sum(v);
-      if (threadIdx.x == 0) partials[k * kRedBlocks + blockIdx.x] = v;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      if (k < ndot) {
+        double v = threadIdx.x < kWarps ? sh[k][threadIdx.x] : 0.0;
+        v = warp_sum(v);
+        if (threadIdx.x == 0) partials[k * kRedBlocks + blockIdx.x] = v;
+      }
     }
   }
+}
+
+template <class VT>
+__device__ __forceinline__ void block_store_dots(const double (&acc)[3], int ndot, double *partials) {
+  block_store_dots3(acc[0], acc[1], acc[2], ndot, partials);
 }
 
 // y = A x over SELL-32 (one warp per slice, one lane per row) with an epilogue:
@@ -73,50 +101,68 @@ __device__ __forceinline__ void block_store_dots(double (&acc)[3], int ndot, dou
 //   E_RESID out = rhs - A x
 //   E_POST  out = xin + wd * (rhs - A x)   (damped Jacobi after prolongation)
 // and up to three fused dot products of {x_i, y_i, u1_i, u2_i} pairs.
+__device__ __forceinline__ double dot_operand(int op, double x, double y, double u1, double u2) {
+  return op == OP_X ? x : (op == OP_Y ? y : (op == OP_U1 ? u1 : u2));
+}
+
 template <class MV, class VT, int EPI>
-__global__ void __launch_bounds__(kThreads) k_sell(SellArgs<VT> a) {
+__global__ void __launch_bounds__(kThreads, 4) k_sell(SellArgs<VT> a) {
   if (a.pred && *a.pred == 0) return;
   const int lane = threadIdx.x & 31;
   const MV *__restrict__ sval = static_cast<const MV *>(a.sval);
-  double acc[3] = {0.0, 0.0, 0.0};
+  double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
   for (int32_t sl = blockIdx.x * kWarps + (threadIdx.x >> 5); sl < a.nslices; sl += gridDim.x * kWarps) {
     const int64_t base = a.sptr[sl];
     const int32_t width = (int32_t)((a.sptr[sl + 1] - base) >> 5);
     const int32_t *__restrict__ cp = a.scol + base + lane;
     const MV *__restrict__ vp = sval + base + lane;
     VT y = VT(0);
-    int32_t e = 0;
-    for (; e + 4 <= width; e += 4) {
-      const int32_t c0 = ld_stream(cp + 32 * e), c1 = ld_stream(cp + 32 * (e + 1)),
-                    c2 = ld_stream(cp + 32 * (e + 2)), c3 = ld_stream(cp + 32 * (e + 3));
-      const MV v0 = ld_stream(vp + 32 * e), v1 = ld_stream(vp + 32 * (e + 1)), v2 = ld_stream(vp + 32 * (e + 2)),
-               v3 = ld_stream(vp + 32 * (e + 3));
-      const VT x0 = __ldg(a.x + c0), x1 = __ldg(a.x + c1), x2 = __ldg(a.x + c2), x3 = __ldg(a.x + c3);
-      y += to_acc(v0, VT(0)) * x0;
-      y += to_acc(v1, VT(0)) * x1;
-      y += to_acc(v2, VT(0)) * x2;
-      y += to_acc(v3, VT(0)) * x3;
-    }
-    for (; e < width; ++e) {
-      const int32_t c0 = ld_stream(cp + 32 * e);
-      const MV v0 = ld_stream(vp + 32 * e);
-      y += to_acc(v0, VT(0)) * __ldg(a.x + c0);
+    // eight entries per step, all loads issued before the gathers
+    for (int32_t e = 0; e < width; e += 8) {
+      int32_t c[8];
+      MV v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if (e + q < width) {
+          c[q] = ld_stream(cp + 32 * (e + q));
+          v[q] = ld_stream(vp + 32 * (e + q));
+        }
+      }
+      VT xv[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (e + q < width) xv[q] = __ldg(a.x + c[q]);
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (e + q < width) y += to_acc(v[q], VT(0)) * xv[q];
     }
     const int32_t row = sl * 32 + lane;
     if (row < a.n) {
       VT o;
       if (EPI == E_Y) o = y;
       else if (EPI == E_RESID) o = a.rhs[row] - y;
-      else o = a.xin[row] + a.wd[row] * (a.rhs[row] - y);
+      else if (EPI == E_POST) o = a.xin[row] + a.wd[row] * (a.rhs[row] - y);
+      else if (EPI == E_DSCALE) o = a.dinv[row] * y;
+      else if (EPI == E_POLYPRE)
+        o = a.coef[3 * row] * a.p0[row] + a.coef[3 * row + 1] * a.p1[row] + a.coef[3 * row + 2] * (a.dinv[row] * y);
+      else if (EPI == E_RESID_POLY) {
+        o = a.rhs[row] - y;
+        a.out2[row] = a.dinv[row] * (a.coef[3 * row + 2] * o);
+      } else if (EPI == E_HORNER)
+        o = a.dinv[row] * y + a.dinv[row] * (a.coef[3 * row + 1] * a.res[row]);
+      else
+        o = a.xin[row] + (a.dinv[row] * y + a.dinv[row] * (a.coef[3 * row] * a.res[row]));
       a.out[row] = o;
       if (a.ndot) {
-        const double ops[4] = {(double)a.x[row], (double)o, a.u1 ? (double)a.u1[row] : 0.0,
-                               a.u2 ? (double)a.u2[row] : 0.0};
-        for (int k = 0; k < a.ndot; ++k) acc[k] += ops[a.dop[k][0]] * ops[a.dop[k][1]];
+        const double ox = (double)a.x[row], oy = (double)o, o1 = a.u1 ? (double)a.u1[row] : 0.0,
+                     o2 = a.u2 ? (double)a.u2[row] : 0.0;
+        acc0 += dot_operand(a.dop[0][0], ox, oy, o1, o2) * dot_operand(a.dop[0][1], ox, oy, o1, o2);
+        if (a.ndot > 1) acc1 += dot_operand(a.dop[1][0], ox, oy, o1, o2) * dot_operand(a.dop[1][1], ox, oy, o1, o2);
+        if (a.ndot > 2) acc2 += dot_operand(a.dop[2][0], ox, oy, o1, o2) * dot_operand(a.dop[2][1], ox, oy, o1, o2);
       }
     }
   }
-  if (a.ndot) block_store_dots<VT>(acc, a.ndot, a.partials);
+  if (a.ndot) block_store_dots3(acc0, acc1, acc2, a.ndot, a.partials);
 }
 
 // out = wd * rhs: damped Jacobi from a zero initial guess
@@ -577,7 +623,8 @@ __global__ void k_copy_cast(int32_t n, const double *__restrict__ in, VT *__rest
 namespace {
 
 inline int ew_grid(int64_t n) { return grid_for(n, kThreads, kRedBlocks); }
-inline int sell_grid(const Level &L) { return grid_for((int64_t)L.nslices, kWarps, kRedBlocks); }
+// k_sell keeps 4 blocks of 256 threads resident per SM (64 registers): one wave
+inline int sell_grid(const Level &L) { return grid_for((int64_t)L.nslices, kWarps, 4 * 152); }
 
 template <class MV, class VT>
 struct Engine {
@@ -627,7 +674,20 @@ struct Engine {
     }
     Level &C = h.lev[k + 1];
     VT *tmp = V(L.tmp);
-    if (!x0_ready) {
+    const bool poly = h.p.smoother == 1 && L.poly != nullptr;
+    if (poly) {  // x = sum_q diag(c_q) (D^-1 A)^q D^-1 b
+      k_scale<VT><<<ew_grid(L.n), kThreads, 0, s>>>(L.n, V(L.u0), V(L.dinv), rhs, pred);
+      check();
+      SellArgs<VT> a = sell_args(k, V(L.u0), V(L.u1), pred);
+      a.dinv = V(L.dinv);
+      sell<E_DSCALE>(a, k);
+      a = sell_args(k, V(L.u1), tmp, pred);
+      a.dinv = V(L.dinv);
+      a.coef = V(L.poly);
+      a.p0 = V(L.u0);
+      a.p1 = V(L.u1);
+      sell<E_POLYPRE>(a, k);
+    } else if (!x0_ready) {
       k_scale<VT><<<ew_grid(L.n), kThreads, 0, s>>>(L.n, tmp, V(L.wd), rhs, pred);  // pre-smoothing
       check();
     }
@@ -637,11 +697,25 @@ struct Engine {
       sell<E_RESID>(a, k);
     }
     const bool coarse_is_last = (k + 1 == h.L - 1);
+    const bool tail = (k + 1 == h.tail_t);
     // r_{k+1} = R_k r_k  (and x0 of level k+1 when it smooths)
     k_restrict<VT><<<ew_grid(L.nc), kThreads, 0, s>>>(L.nc, L.aptr, L.amem, V(L.pw), V(L.r), V(C.bc),
-                                                      coarse_is_last ? nullptr : V(C.wd), V(C.tmp), pred);
+                                                      (coarse_is_last || tail) ? nullptr : V(C.wd), V(C.tmp), pred);
     check();
-    if (coarse_is_last) {
+    if (tail) {  // levels k+1..L-1 in one cluster launch
+      TailArgs ta{};
+      ta.t = k + 1;
+      ta.L = h.L;
+      ta.mode = k < h.p.kcycle_levels ? 1 : 0;
+      ta.nL = h.nL;
+      ta.gmres = gmres_variant ? 1 : 0;
+      ta.kt = h.p.kcycle_t;
+      ta.Ainv = h.coarse_inv;
+      ta.lev = h.tail_dev;
+      ta.pred = pred;
+      tail_launch<MV, VT>(ta, s);
+      ++launches;
+    } else if (coarse_is_last) {
       cycle(k + 1, V(C.bc), V(C.xc), true, pred);  // exact coarse solve
     } else if (k < h.p.kcycle_levels) {
       krylov2(k + 1, pred);  // Alg. 5 coarse correction
@@ -651,11 +725,28 @@ struct Engine {
     // x_k += P_k x_{k+1}
     k_prolong<VT><<<ew_grid(L.n), kThreads, 0, s>>>(L.n, L.agg, V(L.pw), V(C.xc), tmp, pred);
     check();
-    // r_k = b_k - A_k x_k;  x_k += omega D^-1 r_k
+    // r_k = b_k - A_k x_k;  x_k += omega D^-1 r_k  (or the transposed polynomial)
     SellArgs<VT> a = sell_args(k, tmp, out, pred);
     a.rhs = rhs;
     a.wd = V(L.wd);
     a.xin = tmp;
+    if (poly) {
+      SellArgs<VT> b = sell_args(k, tmp, V(L.r), pred);
+      b.rhs = rhs;
+      b.dinv = V(L.dinv);
+      b.coef = V(L.poly);
+      b.out2 = V(L.u0);
+      sell<E_RESID_POLY>(b, k);
+      b = sell_args(k, V(L.u0), V(L.u1), pred);
+      b.dinv = V(L.dinv);
+      b.coef = V(L.poly);
+      b.res = V(L.r);
+      sell<E_HORNER>(b, k);
+      a.x = V(L.u1);
+      a.dinv = V(L.dinv);
+      a.coef = V(L.poly);
+      a.res = V(L.r);
+    }
     if (k == 0 && std::is_same<VT, double>::value && zq_fuse) {
       a.ndot = 1;  // z^T q for the outer flexible CG
       a.dop[0][0] = OP_Y;
@@ -663,7 +754,10 @@ struct Engine {
       a.u1 = (const VT *)h.q;
       a.partials = h.lev[0].partials + 4 * kRedBlocks;
     }
-    sell<E_POST>(a, k);
+    if (poly)
+      sell<E_HORNER_LAST>(a, k);
+    else
+      sell<E_POST>(a, k);
   }
   bool zq_fuse = false;
 
@@ -801,9 +895,55 @@ void alloc_level_vectors(Hierarchy &h, Level &L, int k) {
   L.slots = h.arena.get<double>(kNumSlots);
   L.flag = h.arena.get<int>(4);
   L.partials = h.arena.get<double>((size_t)kRedBlocks * 8);
-  AMG_CUDA(cudaMemset(L.slots, 0, sizeof(double) * kNumSlots));
-  AMG_CUDA(cudaMemset(L.flag, 0, sizeof(int) * 4));
-  AMG_CUDA(cudaMemset(L.partials, 0, sizeof(double) * kRedBlocks * 8));
+  AMG_CUDA(cudaMemsetAsync(L.slots, 0, sizeof(double) * kNumSlots, current_stream()));
+  AMG_CUDA(cudaMemsetAsync(L.flag, 0, sizeof(int) * 4, current_stream()));
+  AMG_CUDA(cudaMemsetAsync(L.partials, 0, sizeof(double) * kRedBlocks * 8, current_stream()));
+}
+
+// First level t of the cluster tail: at most kTailMaxRows rows, not the
+// coarsest, every level in t..L-3 below the K-cycle levels (the tail runs
+// V-cycles only), and no polynomial smoother on those levels.
+void configure_tail(Hierarchy &h, cudaStream_t s) {
+  h.tail_t = -1;
+  if (!h.p.tail) return;
+  for (int t = 1; t <= h.L - 2; ++t) {
+    if (h.lev[t].n > kTailMaxRows) continue;
+    bool ok = true;
+    for (int k = t; k <= h.L - 3; ++k) ok = ok && k >= h.p.kcycle_levels;
+    for (int k = t; k < h.L - 1; ++k) ok = ok && !(h.p.smoother == 1 && h.lev[k].poly);
+    if (ok) {
+      h.tail_t = t;
+      break;
+    }
+  }
+  if (h.tail_t < 0) return;
+  std::vector<TailLevel> tl(h.L);
+  for (int k = 0; k < h.L; ++k) {
+    const Level &L = h.lev[k];
+    TailLevel &T = tl[k];
+    T.n = L.n;
+    T.nslices = L.nslices;
+    T.nc = L.nc;
+    T.sptr = L.sptr;
+    T.scol = L.scol;
+    T.sval = L.sval;
+    T.wd = L.wd;
+    T.pw = L.pw;
+    T.agg = L.agg;
+    T.aptr = L.aptr;
+    T.amem = L.amem;
+    T.bc = L.bc;
+    T.xc = L.xc;
+    T.r = L.r;
+    T.c = L.c;
+    T.v = L.v;
+    T.rt = L.rt;
+    T.d = L.d;
+    T.w = L.w;
+  }
+  if (!h.tail_dev) h.tail_dev = h.arena.get<TailLevel>(kMaxLevels);
+  AMG_CUDA(cudaMemcpyAsync(h.tail_dev, tl.data(), sizeof(TailLevel) * h.L, cudaMemcpyHostToDevice, s));
+  AMG_CUDA(cudaStreamSynchronize(s));
 }
 
 template <class MV, class VT>
@@ -823,7 +963,18 @@ void prepare_t(Hierarchy &h, cudaStream_t s) {
   h.status_dev = h.it_dev + 4;
   AMG_CUDA(cudaMemsetAsync(h.q, 0, sizeof(double) * n, s));
   AMG_CUDA(cudaMemsetAsync(h.pdir, 0, sizeof(double) * n, s));
+  if (h.p.outer == 1) {
+    const int m = h.p.restart;
+    h.V = h.arena.get<double>(n * (size_t)(m + 1));
+    h.Z = h.arena.get<double>(n * (size_t)m);
+    h.H = h.arena.get<double>((size_t)(m + 1) * m);
+    h.fg = h.arena.get<double>(4 * (size_t)m + 2);
+    h.hc = h.arena.get<double>(kMaxRestart + 2);
+    h.gpart = h.arena.get<double>((size_t)(kMaxRestart + 1) * kRedBlocks);
+    AMG_CUDA(cudaMemsetAsync(h.H, 0, sizeof(double) * (m + 1) * m, s));
+  }
   AMG_CUDA(cudaMallocHost(&h.host_pinned, 64 * sizeof(double)));
+  configure_tail(h, s);
 }
 
 template <class VT>
@@ -977,6 +1128,118 @@ int run_solve_t(Hierarchy &h, const double *b, double *x, double tol, int32_t *i
   return status;
 }
 
+// Flexible GMRES(m) (Sec. 2.2, Sec. 4): the Arnoldi basis is orthogonalised by
+// classical Gram-Schmidt with one reorthogonalisation (two multi-dot passes), in
+// FP64; the K-cycle uses the GMRES variant of Alg. 5.  Every restart starts from
+// the true FP64 residual.
+template <class MV, class VT>
+int run_fgmres_t(Hierarchy &h, const double *b, double *x, double tol, int32_t *iters, double *res_hist,
+                 cudaStream_t s) {
+  Level &L0 = h.lev[0];
+  const int32_t n = L0.n;
+  const int m = h.p.restart;
+  Engine<MV, VT> eng(h, s);
+  int64_t launches = 0;
+  int *active = h.it_dev + 1;
+  copy_in(h.b, b, n, s);
+  copy_in(h.x, x, n, s);
+  const int ng = ew_grid(n);
+  k_dot64<<<ng, kThreads, 0, s>>>(n, h.b, h.b, L0.partials + 6 * kRedBlocks, nullptr);
+  k_store_sum<<<1, kThreads, 0, s>>>(L0.partials + 6 * kRedBlocks, ng, L0.slots + S_NB2);
+  k_set_slot<<<1, 32, 0, s>>>(L0.slots, S_TOL, tol);
+  k_set_slot<<<1, 32, 0, s>>>(L0.slots, S_MAXIT, (double)h.p.max_iter);
+  k_set_state<<<1, 32, 0, s>>>(h.it_dev, active, h.it_dev + 2, h.status_dev, 0, 1, 0, 0);
+  launches += 5;
+  AMG_LAUNCH_CHECK();
+  double *w = h.q;
+  int it = 0, status = AMG_ERR_NOT_CONVERGED;
+  std::vector<double> hist;
+  double nb2 = 1.0;
+  bool first = true;
+  int *st_host = reinterpret_cast<int *>(h.host_pinned + 32);
+  for (;;) {
+    true_residual(h, S_RR, s, launches);
+    AMG_CUDA(cudaMemcpyAsync(h.host_pinned, L0.slots, sizeof(double) * kNumSlots, cudaMemcpyDeviceToHost, s));
+    AMG_CUDA(cudaStreamSynchronize(s));
+    if (first) {
+      nb2 = h.host_pinned[S_NB2];
+      if (!(nb2 > 0.0)) {
+        nb2 = 1.0;
+        k_set_slot<<<1, 32, 0, s>>>(L0.slots, S_NB2, 1.0);
+        ++launches;
+      }
+      hist.push_back(std::sqrt(h.host_pinned[S_RR] / nb2));
+      first = false;
+    }
+    const double rel = std::sqrt(h.host_pinned[S_RR] / nb2);
+    if (!std::isfinite(rel)) { status = AMG_ERR_NAN; break; }
+    if (rel <= tol) { status = AMG_OK; break; }
+    if (it >= h.p.max_iter) { status = AMG_ERR_NOT_CONVERGED; break; }
+    k_fg_start<<<ng, kThreads, 0, s>>>(n, h.r, h.V, L0.slots, S_RR, h.fg, m);
+    k_set_state<<<1, 32, 0, s>>>(h.it_dev, active, h.it_dev + 2, h.status_dev, -1, 1, 0, 0);
+    launches += 2;
+    AMG_LAUNCH_CHECK();
+    int jused = 0, dst = 0;
+    for (int j = 0; j < m; ++j) {
+      double *vj = h.V + (size_t)j * n, *zj = h.Z + (size_t)j * n;
+      const int64_t before = eng.launches;
+      eng.precond(vj, zj, active, false);
+      {  // w = A z_j in FP64
+        SellArgs<double> a{};
+        a.n = n;
+        a.nslices = L0.nslices;
+        a.sptr = L0.sptr;
+        a.scol = L0.scol;
+        a.sval = L0.sval64;
+        a.x = zj;
+        a.out = w;
+        a.pred = active;
+        k_sell<double, double, E_Y><<<sell_grid(L0), kThreads, 0, s>>>(a);
+        eng.check();
+      }
+      for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
+        k_mdot<<<ng, kThreads, 0, s>>>(n, h.V, j + 1, w, h.gpart, active);
+        k_fin_mdot<<<1, 1024, 0, s>>>(h.gpart, ng, j + 1, h.H, m, j, h.hc, pass, active);
+        k_maxpy<<<ng, kThreads, 0, s>>>(n, h.V, j + 1, h.hc, w, active);
+        eng.launches += 3;
+        AMG_LAUNCH_CHECK();
+      }
+      k_dot64<<<ng, kThreads, 0, s>>>(n, w, w, L0.partials + 6 * kRedBlocks, active);
+      k_fg_normalize<<<ng, kThreads, 0, s>>>(n, w, h.V + (size_t)(j + 1) * n, L0.partials + 6 * kRedBlocks, ng,
+                                             h.H, m, j, active);
+      k_fg_givens<<<1, 32, 0, s>>>(h.H, m, j, m, h.fg, L0.slots, h.hist, h.it_dev, active, h.status_dev);
+      eng.launches += 3;
+      AMG_LAUNCH_CHECK();
+      (void)before;
+      AMG_CUDA(cudaMemcpyAsync(st_host, h.it_dev, sizeof(int) * 8, cudaMemcpyDeviceToHost, s));
+      AMG_CUDA(cudaStreamSynchronize(s));
+      it = st_host[0];
+      dst = st_host[4];
+      jused = j + 1;
+      if (dst != 0) break;
+    }
+    k_fg_trisolve<<<1, 32, 0, s>>>(h.H, m, jused, m, h.fg);
+    k_fg_xupdate<<<ng, kThreads, 0, s>>>(n, h.x, h.Z, jused, h.fg + 3 * m + 1);
+    launches += 2;
+    AMG_LAUNCH_CHECK();
+    if (dst == AMG_ERR_NAN) { status = AMG_ERR_NAN; break; }
+  }
+  hist.resize((size_t)it + 1);
+  if (it > 0)
+    AMG_CUDA(cudaMemcpyAsync(&hist[1], h.hist + 1, sizeof(double) * (size_t)it, cudaMemcpyDeviceToHost, s));
+  launches += eng.launches;
+  AMG_CUDA(cudaMemcpyAsync(h.host_pinned, L0.slots, sizeof(double) * kNumSlots, cudaMemcpyDeviceToHost, s));
+  copy_out(x, h.x, n, s);
+  AMG_CUDA(cudaStreamSynchronize(s));
+  h.info.final_relres = std::sqrt(h.host_pinned[S_RR] / nb2);
+  h.info.iters = it;
+  h.info.status = status;
+  h.info.kernel_launches = launches;
+  if (iters) *iters = it;
+  if (res_hist) std::memcpy(res_hist, hist.data(), sizeof(double) * hist.size());
+  return status;
+}
+
 template <class MV, class VT>
 void run_precond_t(Hierarchy &h, const double *b, double *x, cudaStream_t s) {
   Engine<MV, VT> eng(h, s);
@@ -1004,6 +1267,25 @@ void run_spmv_t(Hierarchy &h, int k, const void *x, void *y, cudaStream_t s) {
     default: { using MV = __nv_bfloat16; using VT = float; CALL; break; }     \
   }
 
+void set_poly(Hierarchy &h, int level, const double *coef, cudaStream_t s) {
+  Level &L = h.lev[level];
+  const size_t cnt = (size_t)L.n * 3;
+  DevBuf<double> tmp(cnt);
+  const cudaMemcpyKind kind = pointer_kind(coef) == PTR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  AMG_CUDA(cudaMemcpyAsync(tmp.p, coef, sizeof(double) * cnt, kind, s));
+  if (h.p.precision == AMG_PREC_F64) {
+    if (!L.poly) L.poly = h.arena.get<double>(cnt);
+    AMG_CUDA(cudaMemcpyAsync(L.poly, tmp.p, sizeof(double) * cnt, cudaMemcpyDeviceToDevice, s));
+  } else {
+    if (!L.poly) L.poly = h.arena.get<float>(cnt);
+    k_copy_cast<float><<<ew_grid((int64_t)cnt), kThreads, 0, s>>>((int32_t)cnt, tmp.p, (float *)L.poly);
+    AMG_LAUNCH_CHECK();
+  }
+  AMG_CUDA(cudaStreamSynchronize(s));
+  configure_tail(h, s);
+  h.graph_kind = -1;  // the captured iteration no longer matches: capture again
+}
+
 void make_row_data(Hierarchy &h, Level &L, const double *diag, cudaStream_t s) {
   if (h.p.precision == AMG_PREC_F64)
     make_row_data_t<double>(h, L, diag, s);
@@ -1018,7 +1300,11 @@ void prepare_solve(Hierarchy &h, cudaStream_t s) {
 int run_solve(Hierarchy &h, const double *b, double *x, double tol, int32_t *iters, double *res_hist,
               cudaStream_t s) {
   int rc = 0;
-  AMG_DISPATCH(h.p.precision, (rc = run_solve_t<MV, VT>(h, b, x, tol, iters, res_hist, s)));
+  if (h.p.outer == 1) {
+    AMG_DISPATCH(h.p.precision, (rc = run_fgmres_t<MV, VT>(h, b, x, tol, iters, res_hist, s)));
+  } else {
+    AMG_DISPATCH(h.p.precision, (rc = run_solve_t<MV, VT>(h, b, x, tol, iters, res_hist, s)));
+  }
   return rc;
 }
 

@@ -144,6 +144,57 @@ def test_mixed_precision_reaches_fp64_tolerance(gpu, orc, prec):
           f"rel. error vs FP64 oracle {err:.2e}")
 
 
+@pytest.mark.parametrize("name", ["varcoef3d_16", "varcoef2d_50"])
+def test_fgmres_iterates_parity_across_restart(gpu, orc, name):
+    A, g, o = pair(gpu, orc, name, outer=1, restart=5, max_iter=8)
+    b = P.rhs_uniform(A.n, 15)
+    xg, ig = g.solve(b, tol=0.0, allow=(gpu.AMG_OK, gpu.AMG_ERR_NOT_CONVERGED))
+    xo, io = o.solve(b, tol=0.0, max_iter=8)
+    assert ig["iters"] == io["iters"] == 8
+    assert np.linalg.norm(xg - xo) <= 1e-10 * np.linalg.norm(xo)
+    assert np.allclose(ig["hist"], io["hist"], rtol=1e-8, atol=0)
+
+
+def test_fgmres_converges(gpu, orc):
+    A, g, o = pair(gpu, orc, "varcoef3d_24", outer=1, restart=30)
+    b = P.rhs_uniform(A.n, 16)
+    xg, ig = g.solve(b, tol=1e-8)
+    xo, io = o.solve(b, tol=1e-8, max_iter=500)
+    assert ig["status"] == gpu.AMG_OK and ig["final_relres"] <= 1e-8
+    assert abs(ig["iters"] - io["iters"]) <= 1
+    hist = ig["hist"]
+    assert all(b_ <= a_ * (1 + 1e-9) for a_, b_ in zip(hist[:30], hist[1:30]))  # monotone within a cycle
+
+
+@pytest.mark.parametrize("name", ["fem2d_48", "varcoef3d_16"])
+def test_polynomial_smoother_parity(gpu, orc, name):
+    """Per-row polynomial smoother (pre: sum_q diag(c_q)(D^-1A)^q D^-1, post: its
+    transpose) against the oracle with the same coefficients on every level."""
+    A, g, o = pair(gpu, orc, name, smoother=1, max_iter=5)
+    rng = np.random.default_rng(9)
+    for k in range(g.nlevels - 1):
+        n = g.level(k)["n"]
+        coef = np.column_stack([rng.uniform(0.3, 0.7, n), rng.uniform(-0.2, 0.2, n), rng.uniform(-0.1, 0.1, n)])
+        gpu.amg_set_poly(g.h, k, coef)
+        o.set_poly(k, coef)
+    b = P.rhs_uniform(A.n, 17)
+    zg, zo = g.precond(b), o.precond(b)
+    assert np.linalg.norm(zg - zo) <= 1e-11 * np.linalg.norm(zo)
+    xg, ig = g.solve(b, tol=0.0, allow=(gpu.AMG_OK, gpu.AMG_ERR_NOT_CONVERGED))
+    xo, io = o.solve(b, tol=0.0, max_iter=g.params.max_iter)
+    assert np.linalg.norm(xg - xo) <= 1e-9 * np.linalg.norm(xo)
+
+
+def test_polynomial_smoother_reduces_to_jacobi(gpu, orc):
+    A, g, _ = pair(gpu, orc, "varcoef2d_50", smoother=1)
+    b = P.rhs_uniform(A.n, 18)
+    z_j = g.precond(b)  # no coefficients set yet: damped Jacobi on every level
+    for k in range(g.nlevels - 1):
+        L = g.level(k)
+        gpu.amg_set_poly(g.h, k, np.tile([L["omega"], 0.0, 0.0], (L["n"], 1)))
+    assert np.allclose(g.precond(b), z_j, rtol=1e-12, atol=1e-14 * np.abs(z_j).max())
+
+
 def test_single_level_one_iteration(gpu):
     A = P.poisson2d(7)
     g = gpu.Hierarchy(A, coarse_max=64)
