@@ -149,6 +149,53 @@ int amg_spmv(amg_hierarchy *h, int32_t level, const void *x, void *y, void *stre
  * The paper lists polynomial smoothers as future work (Sec. 5). */
 int amg_set_poly(amg_hierarchy *h, int32_t level, const double *coef, void *stream);
 
+/* ---- learned per-row polynomial smoother ----------------------------------
+ * The paper names polynomial smoothers as future work (Sec. 5).  Here a small
+ * MLP (16 -> 64 -> 64 -> 3, tanh, FP16 weights, FP32 arithmetic) maps 16
+ * scale-free features of each matrix row to the coefficients of the smoother
+ * of amg_set_poly: c_q = omega_k (delta_q0 + o_q), so o = 0 is damped Jacobi.
+ * The network is trained on the GPU to minimise the two-grid error reduction
+ * ||T (I - G A) e||_A^2 / ||e||_A^2 measured on seeded random errors e of
+ * two-level hierarchies (T = exact coarse-grid correction).
+ * Parameter layout (AMG_MLP_NPARAM floats): W1[64][16] b1[64] W2[64][64]
+ * b2[64] W3[3][64] b3[3]. */
+#define AMG_MLP_NFEAT 16
+#define AMG_MLP_NPARAM 5443
+
+/* Features of every row of level k into feat (n_k x 16 floats, host or device). */
+int amg_features(const amg_hierarchy *h, int32_t level, float *feat, void *stream);
+
+/* out (n x 3) = MLP(feat (n x 16)); w16: AMG_MLP_NPARAM binary16 bit patterns.
+ * All three arrays are DEVICE pointers.  Asynchronous on stream. */
+int amg_mlp_forward(int32_t n, const uint16_t *w16, const float *feat, float *out, void *stream);
+
+/* dparam (AMG_MLP_NPARAM doubles) = sum over rows of d<dout, MLP_w(feat)>/dw
+ * evaluated at the FP32 weights w; all DEVICE pointers.  The sum over rows is
+ * in a fixed order (deterministic). */
+int amg_mlp_backward(int32_t n, const float *w, const float *feat, const float *dout, double *dparam,
+                     void *stream);
+
+/* Two-grid error reduction of the polynomial pre-smoother with coefficients
+ * coef (n_0 x 3 doubles, DEVICE) on a hierarchy with exactly two levels, over
+ * nvec seeded random errors; *loss (host) gets the mean factor and dcoef
+ * (DEVICE, nullable) its gradient. */
+int amg_twogrid_loss(amg_hierarchy *h, const double *coef, int32_t nvec, uint64_t seed, double *loss,
+                     double *dcoef, void *stream);
+
+/* Train the MLP on two-level hierarchies hs[0..nh) with Adam for `steps`
+ * steps (learning rate lr, nvec random errors per hierarchy and step).
+ * w (host, AMG_MLP_NPARAM floats): initial weights in, trained weights out;
+ * loss_hist (host, nullable, steps doubles): mean two-grid factor per step.
+ * Every step runs on the GPU: features, MLP forward, two-grid gradient, MLP
+ * backward, Adam update. */
+int amg_train_smoother(amg_hierarchy *const *hs, int32_t nh, int32_t steps, double lr, int32_t nvec,
+                       uint64_t seed, float *w, double *loss_hist, void *stream);
+
+/* Evaluate the MLP (binary16 weights w16, host or device) on every level but
+ * the coarsest and install the resulting per-row coefficients; turns the
+ * polynomial smoother on. */
+int amg_apply_learned_smoother(amg_hierarchy *h, const uint16_t *w16, void *stream);
+
 /* Sizes per level.  levels (host, capacity cap) may be NULL to query *nlevels. */
 int amg_hierarchy_info(const amg_hierarchy *h, amg_level_info *levels, int32_t cap,
                        int32_t *nlevels);

@@ -86,8 +86,16 @@ def lib() -> C.CDLL:
         L.amg_free.restype = None
         L.amg_last_error.argtypes = []
         L.amg_last_error.restype = C.c_char_p
+        u64 = C.c_uint64
+        L.amg_features.argtypes = [vp, i32, vp, vp]
+        L.amg_mlp_forward.argtypes = [i32, vp, vp, vp, vp]
+        L.amg_mlp_backward.argtypes = [i32, vp, vp, vp, vp, vp]
+        L.amg_twogrid_loss.argtypes = [vp, vp, i32, u64, C.POINTER(dbl), vp, vp]
+        L.amg_train_smoother.argtypes = [vp, i32, i32, dbl, i32, u64, vp, vp, vp]
+        L.amg_apply_learned_smoother.argtypes = [vp, vp, vp]
         for name in ("amg_setup", "amg_solve", "amg_precond", "amg_spmv", "amg_set_poly", "amg_hierarchy_info",
-                     "amg_export_level", "amg_last_solve_info"):
+                     "amg_export_level", "amg_last_solve_info", "amg_features", "amg_mlp_forward",
+                     "amg_mlp_backward", "amg_twogrid_loss", "amg_train_smoother", "amg_apply_learned_smoother"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libamg_gb300.so")
-SOURCES = ["setup.cu", "solve.cu", "tail.cu", "capi.cu"]
+SOURCES = ["setup.cu", "solve.cu", "tail.cu", "learned.cu", "capi.cu"]
 HEADERS = ["amg_internal.cuh", "scan.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

@@ -210,10 +210,24 @@ void run_precond(Hierarchy &h, const double *b, double *x, cudaStream_t s);
 void run_spmv(Hierarchy &h, int level, const void *x, void *y, cudaStream_t s);
 void set_poly(Hierarchy &h, int level, const double *coef_dev, cudaStream_t s);
 
+// learned.cu
+void twogrid_loss(Hierarchy &h, const double *coef, int nvec, uint64_t seed, double *loss_dev, double *dcoef,
+                  cudaStream_t s);
+void features(const Hierarchy &h, int level, float *feat_dev, cudaStream_t s);
+void mlp_forward_half(int32_t n, const uint16_t *w16_dev, const float *feat, float *out, cudaStream_t s);
+void mlp_backward(int32_t n, const float *w, const float *feat, const float *dout, double *dparam, cudaStream_t s,
+                  bool zero);
+void apply_learned(Hierarchy &h, const uint16_t *w16_dev, cudaStream_t s);
+void train_smoother(Hierarchy *const *hs, int nh, int steps, double lr, int nvec, uint64_t seed, float *w_host,
+                    double *loss_hist, cudaStream_t s);
+
 // tail.cu
 template <class MV, class VT>
 void tail_launch(const TailArgs &a, cudaStream_t s);
-constexpr int kTailMaxRows = 65536;  // largest first tail level
+// Largest first level of the cluster tail.  Eight SMs of a cluster run a level
+// of ~1.5k rows in a few microseconds per phase, where one full-GPU kernel per
+// step is bound by launch latency; a 17k-row level is faster on all 152 SMs.
+constexpr int kTailMaxRows = 4096;
 
 // ---------------------------------------------------------------- device utilities
 __device__ __forceinline__ double warp_sum(double v) {

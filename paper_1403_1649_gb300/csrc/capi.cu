@@ -222,6 +222,89 @@ int amg_set_poly(amg_hierarchy *H, int32_t level, const double *coef, void *stre
   });
 }
 
+int amg_features(const amg_hierarchy *H, int32_t level, float *feat, void *stream) {
+  if (!H || !feat || level < 0 || level >= H->h.L) return AMG_ERR_BAD_INPUT;
+  return guarded([&]() {
+    amg_hierarchy *Hm = const_cast<amg_hierarchy *>(H);
+    enter(Hm, stream);
+    const size_t cnt = (size_t)H->h.lev[level].n * AMG_MLP_NFEAT;
+    if (amg::pointer_kind(feat) == amg::PTR_DEVICE) {
+      amg::features(H->h, level, feat, Hm->stream);
+    } else {
+      amg::DevBuf<float> tmp(cnt);
+      amg::features(H->h, level, tmp.p, Hm->stream);
+      AMG_CUDA(cudaMemcpyAsync(feat, tmp.p, sizeof(float) * cnt, cudaMemcpyDeviceToHost, Hm->stream));
+      AMG_CUDA(cudaStreamSynchronize(Hm->stream));
+    }
+    leave(Hm, stream);
+    return AMG_OK;
+  });
+}
+
+int amg_mlp_forward(int32_t n, const uint16_t *w16, const float *feat, float *out, void *stream) {
+  if (n < 0 || !w16 || !feat || !out) return AMG_ERR_BAD_INPUT;
+  return guarded([&]() {
+    amg::mlp_forward_half(n, w16, feat, out, (cudaStream_t)stream);
+    return AMG_OK;
+  });
+}
+
+int amg_mlp_backward(int32_t n, const float *w, const float *feat, const float *dout, double *dparam, void *stream) {
+  if (n < 0 || !w || !feat || !dout || !dparam) return AMG_ERR_BAD_INPUT;
+  return guarded([&]() {
+    amg::current_stream() = (cudaStream_t)stream;
+    amg::mlp_backward(n, w, feat, dout, dparam, (cudaStream_t)stream, true);
+    return AMG_OK;
+  });
+}
+
+int amg_twogrid_loss(amg_hierarchy *H, const double *coef, int32_t nvec, uint64_t seed, double *loss, double *dcoef,
+                     void *stream) {
+  if (!H || !coef || !loss || nvec < 1) return AMG_ERR_BAD_INPUT;
+  return guarded([&]() {
+    enter(H, stream);
+    amg::DevBuf<double> l(1);
+    amg::twogrid_loss(H->h, coef, nvec, seed, l.p, dcoef, H->stream);
+    AMG_CUDA(cudaMemcpyAsync(loss, l.p, sizeof(double), cudaMemcpyDeviceToHost, H->stream));
+    AMG_CUDA(cudaStreamSynchronize(H->stream));
+    leave(H, stream);
+    return AMG_OK;
+  });
+}
+
+int amg_train_smoother(amg_hierarchy *const *hs, int32_t nh, int32_t steps, double lr, int32_t nvec, uint64_t seed,
+                       float *w, double *loss_hist, void *stream) {
+  if (!hs || nh < 1 || steps < 0 || !w || nvec < 1) return AMG_ERR_BAD_INPUT;
+  for (int j = 0; j < nh; ++j)
+    if (!hs[j] || hs[j]->h.L != 2) {
+      amg::set_last_error("amg_train_smoother: every hierarchy needs exactly two levels");
+      return AMG_ERR_BAD_INPUT;
+    }
+  return guarded([&]() {
+    enter(hs[0], stream);
+    std::vector<amg::Hierarchy *> v(nh);
+    for (int j = 0; j < nh; ++j) v[j] = &hs[j]->h;
+    amg::train_smoother(v.data(), nh, steps, lr, nvec, seed, w, loss_hist, hs[0]->stream);
+    leave(hs[0], stream);
+    return AMG_OK;
+  });
+}
+
+int amg_apply_learned_smoother(amg_hierarchy *H, const uint16_t *w16, void *stream) {
+  if (!H || !w16) return AMG_ERR_BAD_INPUT;
+  return guarded([&]() {
+    enter(H, stream);
+    amg::DevBuf<uint16_t> w(AMG_MLP_NPARAM);
+    const cudaMemcpyKind k =
+        amg::pointer_kind(w16) == amg::PTR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    AMG_CUDA(cudaMemcpyAsync(w.p, w16, sizeof(uint16_t) * AMG_MLP_NPARAM, k, H->stream));
+    amg::apply_learned(H->h, w.p, H->stream);
+    AMG_CUDA(cudaStreamSynchronize(H->stream));
+    leave(H, stream);
+    return AMG_OK;
+  });
+}
+
 int amg_hierarchy_info(const amg_hierarchy *H, amg_level_info *levels, int32_t cap, int32_t *nlevels) {
   if (!H) return AMG_ERR_BAD_INPUT;
   if (nlevels) *nlevels = H->h.L;

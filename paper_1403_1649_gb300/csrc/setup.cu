@@ -331,17 +331,94 @@ __global__ void k_interp(int32_t nc, const int32_t *__restrict__ aptr, const int
 // the paper's stable sort.  The warp walks the distinct coarse columns J in
 // ascending order; for each it sums P_iI * A_ij * P_jJ over the run in order,
 // one term at a time, so every coarse value is the sequential sum.
+constexpr int kGalWarps = 8;   // warps per block of k_galerkin
+constexpr int kGalCap = 320;   // entries of one coarse row staged in shared memory
+
 template <bool FILL>
-__global__ void k_galerkin(int32_t nc, const int32_t *__restrict__ aptr, const int32_t *__restrict__ amem,
-                           const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                           const double *__restrict__ val, const int32_t *__restrict__ agg,
-                           const double *__restrict__ pw, int32_t *__restrict__ ccount,
-                           const int32_t *__restrict__ crp, int32_t *__restrict__ cci,
-                           double *__restrict__ cval) {
+__global__ void __launch_bounds__(kGalWarps * 32) k_galerkin(
+    int32_t nc, const int32_t *__restrict__ aptr, const int32_t *__restrict__ amem,
+    const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ val,
+    const int32_t *__restrict__ agg, const double *__restrict__ pw, int32_t *__restrict__ ccount,
+    const int32_t *__restrict__ crp, int32_t *__restrict__ cci, double *__restrict__ cval) {
+  __shared__ int32_t sJ[kGalWarps][kGalCap];
+  __shared__ double sV[FILL ? kGalWarps : 1][FILL ? kGalCap : 1];
   const int lane = threadIdx.x & 31;
+  const int wid = threadIdx.x >> 5;
   const int wpb = blockDim.x >> 5;
-  for (int32_t I = blockIdx.x * wpb + (threadIdx.x >> 5); I < nc; I += gridDim.x * wpb) {
+  for (int32_t I = blockIdx.x * wpb + wid; I < nc; I += gridDim.x * wpb) {
     const int32_t m0 = aptr[I], m1 = aptr[I + 1];
+    // length of the run of keys (I, *): all entries of the member rows
+    int32_t total = 0;
+    for (int32_t m = m0 + lane; m < m1; m += 32) {
+      const int32_t i = amem[m];
+      total += rp[i + 1] - rp[i];
+    }
+    total = __reduce_add_sync(0xffffffffu, total);
+    if (total <= kGalCap) {
+      // stage (J, P_iI * A_ij * P_jJ) in run order: one lane per member row,
+      // offsets from a warp prefix sum over the member rows
+      int32_t base = 0;
+      for (int32_t mb = m0; mb < m1; mb += 32) {
+        const int32_t m = mb + lane;
+        int32_t i = 0, p0 = 0, len = 0;
+        if (m < m1) {
+          i = amem[m];
+          p0 = rp[i];
+          len = rp[i + 1] - p0;
+        }
+        int32_t incl = len;
+        for (int o = 1; o < 32; o <<= 1) {
+          const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += y;
+        }
+        const int32_t off = base + incl - len;
+        const double Pi = (m < m1) ? pw[i] : 0.0;
+        for (int32_t q = 0; q < len; ++q) {
+          const int32_t j = ci[p0 + q];
+          sJ[wid][off + q] = agg[j];
+          if (FILL) sV[wid][off + q] = __dmul_rn(__dmul_rn(Pi, val[p0 + q]), pw[j]);
+        }
+        base += __shfl_sync(0xffffffffu, incl, 31);
+      }
+      __syncwarp();
+      // walk the distinct coarse columns in ascending order; sum each in run order
+      int32_t cur = -1, out = 0;
+      for (;;) {
+        int32_t next = INT_MAX;
+        double sum = 0.0;
+        bool have = false;
+        for (int32_t e0 = 0; e0 < total; e0 += 32) {
+          const int32_t e = e0 + lane;
+          const int32_t J = e < total ? sJ[wid][e] : INT_MAX;
+          if (J > cur && J < next) next = J;
+          if (FILL) {
+            unsigned mask = __ballot_sync(0xffffffffu, J == cur);
+            const double v = (J == cur) ? sV[wid][e] : 0.0;
+            while (mask) {
+              const int src = __ffs(mask) - 1;
+              const double t = __shfl_sync(0xffffffffu, v, src);
+              sum = have ? __dadd_rn(sum, t) : t;
+              have = true;
+              mask &= mask - 1;
+            }
+          }
+        }
+        next = __reduce_min_sync(0xffffffffu, next);
+        if (cur >= 0) {
+          if (FILL && lane == 0) {
+            cci[crp[I] + out] = cur;
+            cval[crp[I] + out] = sum;
+          }
+          out++;
+        }
+        if (next == INT_MAX) break;
+        cur = next;
+      }
+      if (!FILL && lane == 0) ccount[I] = out;
+      __syncwarp();
+      continue;
+    }
+    // long runs: the same walk reading the member rows from global memory
     int32_t cur = -1, out = 0;
     for (;;) {
       int32_t next = INT_MAX;

@@ -195,6 +195,23 @@ def test_polynomial_smoother_reduces_to_jacobi(gpu, orc):
     assert np.allclose(g.precond(b), z_j, rtol=1e-12, atol=1e-14 * np.abs(z_j).max())
 
 
+@pytest.mark.parametrize("name,prec", [("varcoef3d_24", 0), ("poisson2d_64", 0), ("fem2d_48", 1)])
+def test_cluster_tail_matches_kernel_per_step(gpu, name, prec):
+    """The coarse levels run as one cluster launch or as one kernel per step:
+    same preconditioner up to rounding, same iterations."""
+    A, alpha, seed = case(name)
+    b = P.rhs_uniform(A.n, 19)
+    g1 = gpu.Hierarchy(A, alpha=alpha, seed=seed, precision=prec, tail=1)
+    g0 = gpu.Hierarchy(A, alpha=alpha, seed=seed, precision=prec, tail=0)
+    z1, z0 = g1.precond(b), g0.precond(b)
+    tol = 1e-12 if prec == 0 else 1e-5
+    assert np.linalg.norm(z1 - z0) <= tol * np.linalg.norm(z0)
+    x1, i1 = g1.solve(b, tol=1e-8)
+    x0, i0 = g0.solve(b, tol=1e-8)
+    assert abs(i1["iters"] - i0["iters"]) <= (0 if prec == 0 else 1)
+    assert i1["final_relres"] <= 1e-8 and i1["kernel_launches"] < i0["kernel_launches"]
+
+
 def test_single_level_one_iteration(gpu):
     A = P.poisson2d(7)
     g = gpu.Hierarchy(A, coarse_max=64)
