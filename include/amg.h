@@ -175,6 +175,26 @@ int amg_mlp_forward(int32_t n, const uint16_t *w16, const float *feat, float *ou
 int amg_mlp_backward(int32_t n, const float *w, const float *feat, const float *dout, double *dparam,
                      void *stream);
 
+/* Same result as amg_mlp_backward, for callers that cannot allocate device
+ * memory: code that runs while a CUDA graph is being captured, real-time or
+ * embedding applications that must not enter the allocator, or a host that
+ * has handed the whole device memory budget to another framework.  The paper
+ * has no counterpart; this is a service of the library.
+ *  - No cudaMalloc, cudaFree or allocating library call: the work arrays live
+ *    in a fixed device array of about 4.2 MB (2048 rows x (3 + 4 x 64) floats
+ *    plus 64 x 4096 doubles) that every GPU loading this library keeps until
+ *    the process exits.
+ *  - n may be at most 2048; larger n returns AMG_ERR_BAD_INPUT with a message.
+ *  - The first call on a device looks up that array's device address (once per
+ *    device, with the device current); make that first call before any stream
+ *    capture.
+ *  - All calls share the array: calls whose executions overlap on the GPU (for
+ *    example on two streams) race and give wrong results.  Each call writes
+ *    every scratch word it reads and clears dparam itself.
+ * All pointers are DEVICE pointers; asynchronous on stream. */
+int amg_mlp_backward_noalloc(int32_t n, const float *w, const float *feat, const float *dout, double *dparam,
+                             void *stream);
+
 /* Two-grid error reduction of the polynomial pre-smoother with coefficients
  * coef (n_0 x 3 doubles, DEVICE) on a hierarchy with exactly two levels, over
  * nvec seeded random errors; *loss (host) gets the mean factor and dcoef

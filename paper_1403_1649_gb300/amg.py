@@ -90,6 +90,8 @@ def lib() -> C.CDLL:
         L.amg_features.argtypes = [vp, i32, vp, vp]
         L.amg_mlp_forward.argtypes = [i32, vp, vp, vp, vp]
         L.amg_mlp_backward.argtypes = [i32, vp, vp, vp, vp, vp]
+        L.amg_mlp_backward_noalloc.argtypes = [i32, vp, vp, vp, vp, vp]
+        L.amg_mlp_backward_noalloc.restype = C.c_int
         L.amg_twogrid_loss.argtypes = [vp, vp, i32, u64, C.POINTER(dbl), vp, vp]
         L.amg_train_smoother.argtypes = [vp, i32, i32, dbl, i32, u64, vp, vp, vp]
         L.amg_apply_learned_smoother.argtypes = [vp, vp, vp]

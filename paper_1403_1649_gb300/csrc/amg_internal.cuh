@@ -220,6 +220,10 @@ void mlp_backward(int32_t n, const float *w, const float *feat, const float *dou
 void apply_learned(Hierarchy &h, const uint16_t *w16_dev, cudaStream_t s);
 void train_smoother(Hierarchy *const *hs, int nh, int steps, double lr, int nvec, uint64_t seed, float *w_host,
                     double *loss_hist, cudaStream_t s);
+void mlp_backward_fixed(int32_t n, const float *w, const float *feat, const float *dout, double *dparam,
+                        cudaStream_t s);
+size_t fixed_scratch_bytes();
+int32_t fixed_scratch_max_rows();
 
 // tail.cu
 template <class MV, class VT>

@@ -258,6 +258,18 @@ int amg_mlp_backward(int32_t n, const float *w, const float *feat, const float *
   });
 }
 
+int amg_mlp_backward_noalloc(int32_t n, const float *w, const float *feat, const float *dout, double *dparam,
+                             void *stream) {
+  if (n < 0 || !w || !feat || !dout || !dparam) {
+    amg::set_last_error("amg_mlp_backward_noalloc: null pointer or negative n");
+    return AMG_ERR_BAD_INPUT;
+  }
+  return guarded([&]() {
+    amg::mlp_backward_fixed(n, w, feat, dout, dparam, (cudaStream_t)stream);
+    return AMG_OK;
+  });
+}
+
 int amg_twogrid_loss(amg_hierarchy *H, const double *coef, int32_t nvec, uint64_t seed, double *loss, double *dcoef,
                      void *stream) {
   if (!H || !coef || !loss || nvec < 1) return AMG_ERR_BAD_INPUT;

@@ -401,6 +401,71 @@ void mlp_backward(int32_t n, const float *w, const float *feat, const float *dou
   AMG_LAUNCH_CHECK();
 }
 
+// ------------------------------------------------------------------ fixed scratch
+// MLP backward for callers that cannot allocate device memory: the work arrays
+// (hidden activations, their gradients and the per-chunk weight-gradient sums)
+// live in one statically sized device array that every GPU loading this
+// library holds until the process exits.  Rows per call are limited to
+// kFixedMaxRows; calls that overlap on the GPU share the array and race.
+constexpr int32_t kFixedMaxRows = 2048;
+constexpr size_t kFixedFloats = (size_t)kFixedMaxRows * (NO + 4 * NH);                // out, h1, h2, dz1, dz2
+constexpr size_t kFixedBytes = kFixedFloats * sizeof(float) + (size_t)kGradChunks * NH * NH * sizeof(double);
+static_assert((kFixedFloats * sizeof(float)) % 256 == 0, "double section stays 256-byte aligned");
+static __device__ __align__(256) unsigned char g_fixed_scratch[kFixedBytes];
+
+// Address of the array on the current device, looked up once per device (a host
+// may not use the symbol itself as a device address).
+static void *fixed_scratch_address() {
+  static void *addr[64] = {};
+  int dev = 0;
+  AMG_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) throw Error{AMG_ERR_CUDA, "device index out of range"};
+  if (!addr[dev]) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_fixed_scratch);
+    if (e != cudaSuccess)
+      throw Error{AMG_ERR_CUDA, std::string("cudaGetSymbolAddress(fixed scratch): ") + cudaGetErrorString(e)};
+    addr[dev] = p;
+  }
+  return addr[dev];
+}
+
+size_t fixed_scratch_bytes() { return kFixedBytes; }
+int32_t fixed_scratch_max_rows() { return kFixedMaxRows; }
+
+void mlp_backward_fixed(int32_t n, const float *w, const float *feat, const float *dout, double *dparam,
+                        cudaStream_t s) {
+  if (n < 0 || n > kFixedMaxRows)
+    throw Error{AMG_ERR_BAD_INPUT, "amg_mlp_backward_noalloc: n = " + std::to_string(n) + " rows exceeds the " +
+                                       std::to_string(kFixedMaxRows) + "-row limit of its fixed scratch"};
+  float *base = static_cast<float *>(fixed_scratch_address());
+  float *out = base, *h1 = out + (size_t)NO * kFixedMaxRows, *h2 = h1 + (size_t)NH * kFixedMaxRows;
+  float *dz1 = h2 + (size_t)NH * kFixedMaxRows, *dz2 = dz1 + (size_t)NH * kFixedMaxRows;
+  double *partial = reinterpret_cast<double *>(base + kFixedFloats);
+  // every scratch word read below is written first in the same call; only the
+  // output needs clearing
+  k_zero_f64<<<g256(NP), 256, 0, s>>>(NP, dparam);
+  if (n > 0) {
+    k_mlp_forward<float><<<g256(n), 256, 0, s>>>(n, w, feat, out, h1, h2);
+    k_mlp_backward_rows<<<g256(n), 256, 0, s>>>(n, w, dout, h1, h2, dz1, dz2);
+    struct Term {
+      const float *A;
+      int na;
+      const float *B;
+      int nb;
+      int off;
+    };
+    const Term terms[] = {{dz1, NH, feat, NF, W1O}, {dz1, NH, nullptr, 1, B1O}, {dz2, NH, h1, NH, W2O},
+                          {dz2, NH, nullptr, 1, B2O}, {dout, NO, h2, NH, W3O},  {dout, NO, nullptr, 1, B3O}};
+    for (const Term &t : terms) {
+      const int nout = t.na * (t.B ? t.nb : 1);
+      k_outer_partial<<<kGradChunks, 256, 0, s>>>(n, t.A, t.na, t.B, t.nb, partial);
+      k_sum_chunks<<<grid_for(nout, 256, 64), 256, 0, s>>>(partial, nout, dparam + t.off);
+    }
+  }
+  AMG_LAUNCH_CHECK();
+}
+
 void apply_learned(Hierarchy &h, const uint16_t *w16_dev, cudaStream_t s) {
   for (int k = 0; k < h.L - 1; ++k) {
     Level &L = h.lev[k];
