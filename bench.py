@@ -45,7 +45,135 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-spmv", action="store_true",
                     help="set up the workload and run two level-0 SpMV launches per precision (ncu target)")
+    ap.add_argument("--workload", default="poisson3d_128",
+                    choices=["poisson3d_128", "varcoef3d_160", "fem2d_1024", "batch512"],
+                    help="poisson3d_128 is the benchmark line; the others measure the other configurations")
     return ap.parse_args()
+
+
+def timed(fn, reps):
+    """Median device time of fn() over reps runs (CUDA events), after one warm-up."""
+    import torch
+    fn()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        out = fn()
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return float(np.median(ts)), out
+
+
+def other_workload(args):
+    """One JSON line for a configuration other than the benchmark line."""
+    import torch
+    from paper_1403_1649_gb300 import amg, build
+    from paper_1403_1649_gb300 import problems as P
+    build.build()
+    dev = torch.device("cuda", 0)
+    reps = max(args.steps, 1)
+    line = {"metric": METRIC, "unit": "DoF/s", "n_gpus": 1, "steps": reps, "warmup": 1, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "data": "synthetic"}
+
+    def run_single(A, b, **pk):
+        rp, ci, va = (torch.from_numpy(a).to(dev) for a in (A.rowptr, A.col, A.val))
+        bd = torch.from_numpy(b).to(dev)
+        xd = torch.zeros_like(bd)
+        info = {}
+
+        def go():
+            h = amg.amg_setup(rp, ci, va, amg.amg_default_params(**pk))
+            if pk.get("smoother") == 1:
+                amg.lib().amg_apply_learned_smoother(h, info["w16"].ctypes.data, None)
+            xd.zero_()
+            amg.amg_solve(h, bd, xd, TOL, 2000)
+            i = amg.amg_last_solve_info(h)
+            amg.amg_free(h)
+            return i
+        return go, info
+
+    if args.workload == "varcoef3d_160":
+        A = P.varcoef3d(160, 2)
+        b = P.rhs_uniform(A.n, 2)
+        res = {}
+        for prec in ("bf16", "f64"):
+            go, _ = run_single(A, b, alpha=0.5, seed=2, outer=1, restart=30, precision=PREC[prec], max_iter=2000)
+            t, i = timed(go, reps)
+            res[prec] = {"ms": t, "setup_ms": i["setup_ms"], "solve_ms": i["solve_ms"], "iters": i["iters"],
+                         "final_relres": i["final_relres"]}
+        line.update(value=A.n / (res["bf16"]["ms"] / 1e3), ms_per_step=res["bf16"]["ms"], dtype="bf16+f32+f64",
+                    config={"workload": "3D finite-volume -div(k grad u) 160^3 (n=4,096,000), k log-uniform "
+                                        "[1e-3,1e3] on 8^3 blocks, z x100 on x<80; FGMRES(30), K-cycle (GMRES "
+                                        "variant), BF16 matrix values / FP32 vectors vs FP64, to 1e-8"},
+                    compare=res)
+    elif args.workload == "fem2d_1024":
+        A = P.fem2d(1024, 3)
+        b = P.rhs_uniform(A.n, 3)
+        # train the smoother network on the GPU on small problems of the same family
+        train = [amg.Hierarchy(P.fem2d(m, 200 + q), alpha=0.25, seed=1, coarse_max=16, max_levels=2,
+                               omega_mode=1, omega=2.0 / 3.0) for q, m in enumerate((48, 64, 80, 96))]
+        w = np.zeros(5443, np.float32)
+        rng = np.random.default_rng(3)
+        w[:5248] = (rng.normal(size=5248) * 0.2).astype(np.float32)
+        hist = np.zeros(150)
+        arr = (C_void_p_array(len(train)))(*[t.h for t in train])
+        t0 = time.perf_counter()
+        rc = amg.lib().amg_train_smoother(arr, len(train), 150, 3e-3, 2, 11, w.ctypes.data, hist.ctypes.data, None)
+        train_s = time.perf_counter() - t0
+        assert rc == 0
+        w16 = w.astype(np.float16).view(np.uint16)
+        res = {}
+        for name, pk in (("jacobi_f64", dict(precision=0)), ("jacobi_f32", dict(precision=1)),
+                         ("learned_f32", dict(precision=1, smoother=1)), ("learned_f64", dict(precision=0, smoother=1))):
+            go, info = run_single(A, b, alpha=0.25, seed=3, omega_mode=1, omega=2.0 / 3.0, max_iter=2000, **pk)
+            info["w16"] = w16
+            t, i = timed(go, reps)
+            res[name] = {"ms": t, "setup_ms": i["setup_ms"], "solve_ms": i["solve_ms"], "iters": i["iters"],
+                         "final_relres": i["final_relres"]}
+        line.update(value=A.n / (res["learned_f32"]["ms"] / 1e3), ms_per_step=res["learned_f32"]["ms"],
+                    dtype="f32+f64",
+                    config={"workload": "2D P1 FEM, jittered 1024^2 nodes (n=1,048,576), learned per-row "
+                                        "polynomial smoother (MLP 16-64-64-3, FP16 weights) vs damped Jacobi "
+                                        "omega=2/3, flexible CG to 1e-8",
+                            "training": f"150 Adam steps on 4 two-level FEM problems (48^2..96^2), {train_s:.1f} s, "
+                                        f"two-grid factor {hist[0]:.4f} -> {hist[-1]:.4f}"},
+                    compare=res)
+    else:  # batch512
+        sides = P.batch_sizes(512, 4)
+        t0 = time.perf_counter()
+        mats = [P.varcoef2d(int(m), 4 + q) for q, m in enumerate(sides)]
+        rhs = np.concatenate([P.rhs_uniform(A.n, 4 + q) for q, A in enumerate(mats)])
+        gen_s = time.perf_counter() - t0
+        dmats = [tuple(torch.from_numpy(a).to(dev) for a in (A.rowptr, A.col, A.val)) for A in mats]
+        bd = torch.from_numpy(rhs).to(dev)
+        xd = torch.zeros_like(bd)
+        ntot = int(rhs.size)
+        res = {}
+        for name, pk in (("f32", dict(precision=1)), ("f64", dict(precision=0))):
+            def go():
+                h = amg.amg_setup_batch(dmats, amg.amg_default_params(alpha=0.25, seed=4, max_iter=2000, **pk))
+                xd.zero_()
+                rc, it, rel = amg.amg_solve_batch(h, bd, xd, TOL, len(mats))
+                i = amg.amg_last_solve_info(h)
+                amg.amg_free(h)
+                return i, it, rel
+            t, (i, it, rel) = timed(go, reps)
+            res[name] = {"ms": t, "setup_ms": i["setup_ms"], "solve_ms": i["solve_ms"], "max_iters": int(it.max()),
+                         "mean_iters": float(it.mean()), "worst_relres": float(rel.max())}
+        line.update(value=ntot / (res["f32"]["ms"] / 1e3), ms_per_step=res["f32"]["ms"], dtype="f32+f64",
+                    config={"workload": f"512 independent 2D variable-coefficient 5-point systems, sides uniform "
+                                        f"32..512 (n={ntot:,}), k log-uniform [1e-2,1e2]; one block-diagonal "
+                                        f"hierarchy, per-system flexible CG to 1e-8 (generation {gen_s:.0f} s)"},
+                    compare=res)
+    print(json.dumps(line), flush=True)
+
+
+def C_void_p_array(n):
+    import ctypes
+    return ctypes.c_void_p * n
 
 
 def profile_spmv():
@@ -225,6 +353,9 @@ def main():
     args = parse()
     if args.profile_spmv:
         profile_spmv()
+        return
+    if args.workload != "poisson3d_128" and args.impl == "ours":
+        other_workload(args)
         return
     ws, rank, local = dist_init()
     if args.impl == "reference":

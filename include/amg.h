@@ -81,8 +81,9 @@ typedef struct amg_params {
   int32_t use_graph;     /* 1: replay one outer iteration as a captured CUDA graph          */
   int32_t smoother;      /* 0: damped Jacobi; 1: per-row polynomial smoother whose
                             coefficients are set with amg_set_poly                         */
-  int32_t tail;          /* 1: run the coarse levels (at most 65536 rows, below the
+  int32_t tail;          /* 1: run the coarse levels (at most 4096 rows, below the
                             K-cycle levels) in one thread-block-cluster launch per visit   */
+  int32_t pdl;           /* 1: launch solve kernels with programmatic dependent launch     */
 } amg_params;
 
 typedef struct amg_level_info {
@@ -107,7 +108,7 @@ typedef struct amg_hierarchy amg_hierarchy;
 
 /* Fill *p with the defaults: alpha 0.25, seed 0, coarse_max 64, max_levels 25,
  * kcycle_levels 2, kcycle_t 0.25, omega_mode 0, omega 2/3, precision F64,
- * outer FCG, restart 30, max_iter 500, use_graph 1, smoother 0, tail 1. */
+ * outer FCG, restart 30, max_iter 500, use_graph 1, smoother 0, tail 0, pdl 1. */
 void amg_default_params(amg_params *p);
 
 /* Alg. 1: build the hierarchy of A on the GPU.
@@ -133,13 +134,36 @@ int amg_setup(const amg_csr *A, const amg_params *params, void *stream, amg_hier
 int amg_solve(amg_hierarchy *h, const double *b, double *x, double tol, int32_t *iters,
               double *res_hist, void *stream);
 
+/* ---- batches of independent systems --------------------------------------
+ * nsys systems of different sizes set up as one block-diagonal hierarchy: the
+ * setup of Alg. 1 never couples the blocks (no strong connection between
+ * them), so every level keeps each system's unknowns contiguous, and the
+ * coarsest level is solved with one dense inverse per system.  Coarsening
+ * continues until the largest system is at most coarse_max.  The solve runs all
+ * systems in the same kernels (one captured CUDA graph per outer iteration)
+ * with per-system Krylov scalars: every inner product of flexible CG and of
+ * Alg. 5 is taken per system, each system has its own step lengths, branch of
+ * Alg. 5 and convergence test, and a converged system stops changing.
+ * Flexible CG only (params.outer must be 0). */
+int amg_setup_batch(int32_t nsys, const amg_csr *As, const amg_params *params, void *stream,
+                    amg_hierarchy **out);
+
+/* b, x: the systems' right-hand sides / initial guesses concatenated in system
+ * order (sum of n_s doubles each, host or device); x receives the solutions.
+ * iters, relres (host, nsys entries, nullable): outer iterations and final FP64
+ * relative residual ||b_s - A_s x_s|| / ||b_s|| of every system.  Returns AMG_OK
+ * when every system meets tol, else the first failure code. */
+int amg_solve_batch(amg_hierarchy *h, const double *b, double *x, double tol, int32_t *iters, double *relres,
+                    void *stream);
+
 /* One application of the preconditioner, x = M b (Alg. 5 at level 0 from a
  * zero initial guess).  b, x: n doubles, host or device. */
 int amg_precond(amg_hierarchy *h, const double *b, double *x, void *stream);
 
 /* y = A_k x on level k with the solve-phase matrix (in the hierarchy's
  * precision).  x, y: n_k elements of the vector type of the precision (double
- * for F64, float otherwise), DEVICE pointers.  Asynchronous on `stream`. */
+ * for F64, float otherwise), DEVICE pointers (host pointers: AMG_ERR_BAD_INPUT).
+ * Asynchronous on `stream`. */
 int amg_spmv(amg_hierarchy *h, int32_t level, const void *x, void *y, void *stream);
 
 /* Per-row polynomial smoother coefficients of level k (n_k x 3, row major,
@@ -226,6 +250,13 @@ int amg_hierarchy_info(const amg_hierarchy *h, amg_level_info *levels, int32_t c
  * are left untouched on the coarsest level. */
 int amg_export_level(const amg_hierarchy *h, int32_t level, int32_t *row_ptr, int32_t *col,
                      double *val, int32_t *agg, double *P, double *B);
+
+/* Copy every index array of the hierarchy to the host and check it: CSR and
+ * SELL ranges, aggregate ids, member lists, and for batches the per-level
+ * system offsets, row-to-system map, row tiles and coarsest block offsets.
+ * Returns AMG_ERR_SETUP with the first violation in amg_last_error().  A
+ * diagnostic: it synchronises and copies, and runs no kernel. */
+int amg_validate_hierarchy(const amg_hierarchy *h);
 
 /* Statistics of the last setup/solve on this hierarchy. */
 int amg_last_solve_info(const amg_hierarchy *h, amg_solve_info *info);

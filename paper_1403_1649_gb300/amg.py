@@ -40,7 +40,7 @@ class amg_params(C.Structure):
                 ("max_levels", C.c_int32), ("kcycle_levels", C.c_int32), ("kcycle_t", C.c_double),
                 ("omega_mode", C.c_int32), ("omega", C.c_double), ("precision", C.c_int32),
                 ("outer", C.c_int32), ("restart", C.c_int32), ("max_iter", C.c_int32),
-                ("use_graph", C.c_int32), ("smoother", C.c_int32), ("tail", C.c_int32)]
+                ("use_graph", C.c_int32), ("smoother", C.c_int32), ("tail", C.c_int32), ("pdl", C.c_int32)]
 
 
 class amg_level_info(C.Structure):
@@ -95,6 +95,12 @@ def lib() -> C.CDLL:
         L.amg_twogrid_loss.argtypes = [vp, vp, i32, u64, C.POINTER(dbl), vp, vp]
         L.amg_train_smoother.argtypes = [vp, i32, i32, dbl, i32, u64, vp, vp, vp]
         L.amg_apply_learned_smoother.argtypes = [vp, vp, vp]
+        L.amg_setup_batch.argtypes = [i32, vp, C.POINTER(amg_params), vp, C.POINTER(vp)]
+        L.amg_solve_batch.argtypes = [vp, vp, vp, dbl, vp, vp, vp]
+        L.amg_setup_batch.restype = C.c_int
+        L.amg_validate_hierarchy.argtypes = [vp]
+        L.amg_validate_hierarchy.restype = C.c_int
+        L.amg_solve_batch.restype = C.c_int
         for name in ("amg_setup", "amg_solve", "amg_precond", "amg_spmv", "amg_set_poly", "amg_hierarchy_info",
                      "amg_export_level", "amg_last_solve_info", "amg_features", "amg_mlp_forward",
                      "amg_mlp_backward", "amg_twogrid_loss", "amg_train_smoother", "amg_apply_learned_smoother"):
@@ -157,6 +163,37 @@ def amg_setup(rowptr, col, val, params: amg_params | None = None, stream=None) -
     _check(lib().amg_setup(C.byref(csr), C.byref(p), stream if stream is not None else _stream(rowptr),
                            C.byref(h)))
     return h
+
+
+def amg_setup_batch(systems, params: amg_params | None = None, stream=None) -> C.c_void_p:
+    """Block-diagonal hierarchy of independent systems (list of CSR objects or
+    (rowptr, col, val) triples, numpy or CUDA tensors)."""
+    arr = (amg_csr * len(systems))()
+    keep = []
+    for q, A in enumerate(systems):
+        rp, ci, va = (A.rowptr, A.col, A.val) if hasattr(A, "rowptr") else A
+        if isinstance(rp, np.ndarray):
+            rp = np.ascontiguousarray(rp, np.int32)
+            ci = np.ascontiguousarray(ci, np.int32)
+            va = np.ascontiguousarray(va, np.float64)
+        keep.append((rp, ci, va))
+        arr[q] = amg_csr(len(rp) - 1, len(ci), _ptr(rp), _ptr(ci), _ptr(va))
+    h = C.c_void_p()
+    p = params if params is not None else amg_default_params()
+    _check(lib().amg_setup_batch(len(systems), arr, C.byref(p), stream, C.byref(h)))
+    return h
+
+
+def amg_solve_batch(h, b, x, tol: float, nsys: int, stream=None, allow=(AMG_OK,)):
+    """Solve every system of a batch; b, x concatenated.  Returns (status, iters, relres)."""
+    if isinstance(b, np.ndarray):
+        b = np.ascontiguousarray(b, np.float64)
+    it = np.zeros(nsys, np.int32)
+    rel = np.zeros(nsys)
+    rc = lib().amg_solve_batch(h, _ptr(b), _ptr(x), tol, it.ctypes.data, rel.ctypes.data,
+                               stream if stream is not None else _stream(b, x))
+    _check(rc, allow)
+    return rc, it, rel
 
 
 def amg_solve(h, b, x, tol: float, max_iter: int | None = None, stream=None, allow=(AMG_OK,)):

@@ -136,6 +136,15 @@ struct Level {
   double *slots = nullptr;    // kNumSlots doubles
   int *flag = nullptr;        // predicate of the second inner step of Alg. 5 at this level
   double *partials = nullptr; // kRedBlocks * 8 doubles
+  // batched systems (block-diagonal hierarchy): system s owns rows
+  // [sys_off[s], sys_off[s+1]) on every level; row tiles never cross systems
+  int32_t *sys_off = nullptr, *sys_of = nullptr;
+  std::vector<int32_t> sys_off_host;
+  int32_t ntiles = 0;
+  int32_t *tile_row = nullptr, *sys_tile = nullptr;  // ntiles+1 row starts; nsys+1 first tiles
+  double *bslots = nullptr;   // kNumSlots x nsys per-system scalars
+  int *bflag = nullptr;       // nsys second-step flags, then "any"
+  double *tpart = nullptr;    // 3 x ntiles tile partial sums
 };
 
 // Per-level view used by the cluster kernel that runs the coarse tail of the
@@ -161,6 +170,14 @@ struct TailArgs {
 struct Hierarchy {
   amg_params p{};
   int L = 0;
+  // batched mode: nsys independent systems in one block-diagonal hierarchy
+  bool batched = false;
+  int nsys = 1;
+  double *binv = nullptr;        // coarsest level: per-system dense inverses, back to back
+  int64_t *binv_off = nullptr;   // nsys+1 offsets into binv
+  int32_t bmax = 0;              // largest coarsest block
+  int *bit = nullptr;            // per-system iteration counts, then per-system status
+  int *bactive = nullptr;        // per-system "still iterating", [nsys] = number active
   int tail_t = -1;                 // first level of the cluster tail (-1: none)
   TailLevel *tail_dev = nullptr;   // device copy of the per-level views
   Level lev[kMaxLevels];
@@ -200,6 +217,8 @@ PtrKind pointer_kind(const void *p);
 
 // setup.cu
 void build_hierarchy(Hierarchy &h, const amg_csr &A, cudaStream_t s);
+void build_hierarchy_batch(Hierarchy &h, int32_t nsys, const amg_csr *As, cudaStream_t s);
+void coarsen_all(Hierarchy &h, cudaStream_t s);
 // solve.cu: per-row smoother data (omega/A_ii, 1/A_ii, P weights) in the vector type
 void make_row_data(Hierarchy &h, Level &L, const double *diag, cudaStream_t s);
 // solve.cu
@@ -207,6 +226,8 @@ void prepare_solve(Hierarchy &h, cudaStream_t s);
 int run_solve(Hierarchy &h, const double *b, double *x, double tol, int32_t *iters, double *res_hist,
               cudaStream_t s);
 void run_precond(Hierarchy &h, const double *b, double *x, cudaStream_t s);
+int run_solve_batch(Hierarchy &h, const double *b, double *x, double tol, int32_t *iters, double *relres,
+                    cudaStream_t s);
 void run_spmv(Hierarchy &h, int level, const void *x, void *y, cudaStream_t s);
 void set_poly(Hierarchy &h, int level, const double *coef_dev, cudaStream_t s);
 
@@ -232,6 +253,34 @@ void tail_launch(const TailArgs &a, cudaStream_t s);
 // of ~1.5k rows in a few microseconds per phase, where one full-GPU kernel per
 // step is bound by launch latency; a 17k-row level is faster on all 152 SMs.
 constexpr int kTailMaxRows = 4096;
+
+// ---------------------------------------------------------------- launches
+// Solve kernels are launched with programmatic dependent launch: each kernel
+// may be scheduled while its predecessor in the stream still runs, waits in
+// griddepcontrol.wait until the predecessor has completed and its writes are
+// visible, and at once lets its own successor launch.  This hides the launch
+// latency of the many short kernels of a multigrid cycle.
+bool &pdl_enabled();  // thread-local, set from the hierarchy's parameters
+
+template <typename... KArgs, typename... Args>
+inline void klaunch(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args &&...args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  AMG_CUDA(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
+}
+
+__device__ __forceinline__ void pdl_wait_and_trigger() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
 
 // ---------------------------------------------------------------- device utilities
 __device__ __forceinline__ double warp_sum(double v) {

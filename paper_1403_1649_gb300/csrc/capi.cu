@@ -26,6 +26,11 @@ cudaStream_t &current_stream() {
   return s;
 }
 
+bool &pdl_enabled() {
+  static thread_local bool on = true;
+  return on;
+}
+
 cudaMemPool_t device_pool() {
   static cudaMemPool_t pools[64] = {};
   int dev = 0;
@@ -76,6 +81,7 @@ int guarded(F &&f) {
 // make the internal stream wait for the caller's stream
 void enter(amg_hierarchy *H, void *user) {
   amg::current_stream() = H->stream;
+  amg::pdl_enabled() = H->h.p.pdl != 0;
   AMG_CUDA(cudaEventRecord(H->ev_in, (cudaStream_t)user));
   AMG_CUDA(cudaStreamWaitEvent(H->stream, H->ev_in, 0));
 }
@@ -94,6 +100,16 @@ int check_params(const amg_params *p) {
     return AMG_ERR_BAD_INPUT;
   }
   return AMG_OK;
+}
+
+template <class T>
+std::vector<T> fetch(const T *dev, size_t n) {
+  std::vector<T> v(n);
+  if (n && dev) AMG_CUDA(cudaMemcpy(v.data(), dev, sizeof(T) * n, cudaMemcpyDeviceToHost));
+  return v;
+}
+void expect(bool ok, int k, const char *what) {
+  if (!ok) throw amg::Error{AMG_ERR_SETUP, "level " + std::to_string(k) + ": " + what};
 }
 
 }  // namespace
@@ -117,7 +133,8 @@ void amg_default_params(amg_params *p) {
   p->max_iter = 500;
   p->use_graph = 1;
   p->smoother = 0;
-  p->tail = 1;
+  p->tail = 0;
+  p->pdl = 1;
 }
 
 int amg_setup(const amg_csr *A, const amg_params *params, void *stream, amg_hierarchy **out) {
@@ -186,6 +203,75 @@ int amg_solve(amg_hierarchy *H, const double *b, double *x, double tol, int32_t 
   });
 }
 
+int amg_setup_batch(int32_t nsys, const amg_csr *As, const amg_params *params, void *stream,
+                    amg_hierarchy **out) {
+  if (nsys < 1 || !As || !out) {
+    amg::set_last_error("amg_setup_batch: bad arguments");
+    return AMG_ERR_BAD_INPUT;
+  }
+  for (int32_t q = 0; q < nsys; ++q)
+    if (!As[q].row_ptr || !As[q].col || !As[q].val || As[q].n <= 0 || As[q].nnz < As[q].n) {
+      amg::set_last_error("amg_setup_batch: system " + std::to_string(q) + " has null pointers or bad sizes");
+      return AMG_ERR_BAD_INPUT;
+    }
+  int rc = check_params(params);
+  if (rc) return rc;
+  if (params->outer != 0) {
+    amg::set_last_error("amg_setup_batch: batches use flexible CG (outer = 0)");
+    return AMG_ERR_UNSUPPORTED;
+  }
+  *out = nullptr;
+  amg_hierarchy *H = new amg_hierarchy();
+  rc = guarded([&]() {
+    AMG_CUDA(cudaStreamCreateWithFlags(&H->stream, cudaStreamNonBlocking));
+    AMG_CUDA(cudaEventCreateWithFlags(&H->ev_in, cudaEventDisableTiming));
+    AMG_CUDA(cudaEventCreateWithFlags(&H->ev_out, cudaEventDisableTiming));
+    AMG_CUDA(cudaEventCreate(&H->t0));
+    AMG_CUDA(cudaEventCreate(&H->t1));
+    H->h.p = *params;
+    enter(H, stream);
+    AMG_CUDA(cudaEventRecord(H->t0, H->stream));
+    const int64_t l0 = amg::launch_counter();
+    amg::build_hierarchy_batch(H->h, nsys, As, H->stream);
+    amg::prepare_solve(H->h, H->stream);
+    H->h.info.setup_launches = amg::launch_counter() - l0;
+    AMG_CUDA(cudaEventRecord(H->t1, H->stream));
+    AMG_CUDA(cudaEventSynchronize(H->t1));
+    float ms = 0.f;
+    AMG_CUDA(cudaEventElapsedTime(&ms, H->t0, H->t1));
+    H->h.info.setup_ms = ms;
+    leave(H, stream);
+    return AMG_OK;
+  });
+  if (rc != AMG_OK) {
+    amg_free(H);
+    return rc;
+  }
+  *out = H;
+  return AMG_OK;
+}
+
+int amg_solve_batch(amg_hierarchy *H, const double *b, double *x, double tol, int32_t *iters, double *relres,
+                    void *stream) {
+  if (!H || !b || !x || !(tol >= 0.0) || !H->h.batched) {
+    amg::set_last_error("amg_solve_batch: null pointer, negative tolerance or not a batch hierarchy");
+    return AMG_ERR_BAD_INPUT;
+  }
+  return guarded([&]() {
+    enter(H, stream);
+    AMG_CUDA(cudaEventRecord(H->t0, H->stream));
+    const int rc = amg::run_solve_batch(H->h, b, x, tol, iters, relres, H->stream);
+    AMG_CUDA(cudaEventRecord(H->t1, H->stream));
+    AMG_CUDA(cudaEventSynchronize(H->t1));
+    float ms = 0.f;
+    AMG_CUDA(cudaEventElapsedTime(&ms, H->t0, H->t1));
+    H->h.info.solve_ms = ms;
+    leave(H, stream);
+    if (rc != AMG_OK) amg::set_last_error("amg_solve_batch: some system did not converge");
+    return rc;
+  });
+}
+
 int amg_precond(amg_hierarchy *H, const double *b, double *x, void *stream) {
   if (!H || !b || !x) return AMG_ERR_BAD_INPUT;
   return guarded([&]() {
@@ -199,6 +285,10 @@ int amg_precond(amg_hierarchy *H, const double *b, double *x, void *stream) {
 int amg_spmv(amg_hierarchy *H, int32_t level, const void *x, void *y, void *stream) {
   if (!H || !x || !y || level < 0 || level >= H->h.L) {
     amg::set_last_error("amg_spmv: bad arguments");
+    return AMG_ERR_BAD_INPUT;
+  }
+  if (amg::pointer_kind(x) != amg::PTR_DEVICE || amg::pointer_kind(y) != amg::PTR_DEVICE) {
+    amg::set_last_error("amg_spmv: x and y must be device pointers");
     return AMG_ERR_BAD_INPUT;
   }
   return guarded([&]() {
@@ -344,6 +434,74 @@ int amg_export_level(const amg_hierarchy *H, int32_t level, int32_t *row_ptr, in
     if (agg && !last) AMG_CUDA(cudaMemcpy(agg, L.agg, sizeof(int32_t) * (size_t)L.n, cudaMemcpyDeviceToHost));
     if (P && !last) AMG_CUDA(cudaMemcpy(P, L.pw64, sizeof(double) * (size_t)L.n, cudaMemcpyDeviceToHost));
     if (B) AMG_CUDA(cudaMemcpy(B, L.B, sizeof(double) * (size_t)L.n, cudaMemcpyDeviceToHost));
+    return AMG_OK;
+  });
+}
+
+int amg_validate_hierarchy(const amg_hierarchy *H) {
+  if (!H) return AMG_ERR_BAD_INPUT;
+  return guarded([&]() {
+    const amg::Hierarchy &h = H->h;
+    AMG_CUDA(cudaStreamSynchronize(H->stream));
+    for (int k = 0; k < h.L; ++k) {
+      const amg::Level &L = h.lev[k];
+      const bool last = k == h.L - 1;
+      auto rp = fetch(L.rp, (size_t)L.n + 1);
+      auto ci = fetch(L.ci, (size_t)L.nnz);
+      expect(rp[0] == 0 && rp[L.n] == L.nnz, k, "row pointer ends");
+      for (int32_t i = 0; i < L.n; ++i) expect(rp[i] <= rp[i + 1], k, "row pointers not monotone");
+      for (int32_t c : ci) expect(c >= 0 && c < L.n, k, "column out of range");
+      auto sp = fetch(L.sptr, (size_t)L.nslices + 1);
+      auto sc = fetch(L.scol, (size_t)L.sell_entries);
+      expect(sp[0] == 0 && sp[L.nslices] == L.sell_entries, k, "SELL pointer ends");
+      for (int32_t q = 0; q < L.nslices; ++q) expect(sp[q] <= sp[q + 1] && (sp[q + 1] - sp[q]) % 32 == 0, k, "SELL slice");
+      for (int32_t c : sc) expect(c >= 0 && c < L.n, k, "SELL column out of range");
+      if (!last) {
+        auto agg = fetch(L.agg, (size_t)L.n);
+        auto ap = fetch(L.aptr, (size_t)L.nc + 1);
+        auto am = fetch(L.amem, (size_t)L.n);
+        expect(L.nc == h.lev[k + 1].n, k, "coarse size");
+        for (int32_t a : agg) expect(a >= 0 && a < L.nc, k, "aggregate id out of range");
+        expect(ap[0] == 0 && ap[L.nc] == L.n, k, "member pointer ends");
+        std::vector<char> seen(L.n, 0);
+        for (int32_t I = 0; I < L.nc; ++I)
+          for (int32_t m = ap[I]; m < ap[I + 1]; ++m) {
+            expect(am[m] >= 0 && am[m] < L.n && !seen[am[m]] && agg[am[m]] == I, k, "member lists");
+            seen[am[m]] = 1;
+          }
+      }
+      if (h.batched) {
+        auto so = fetch(L.sys_off, (size_t)h.nsys + 1);
+        expect(so == L.sys_off_host, k, "system offsets differ between host and device");
+        expect(so[0] == 0 && so[h.nsys] == L.n, k, "system offset ends");
+        for (int q = 0; q < h.nsys; ++q) expect(so[q] < so[q + 1], k, "empty or unordered system");
+        auto sy = fetch(L.sys_of, (size_t)L.n);
+        for (int q = 0; q < h.nsys; ++q)
+          for (int32_t i = so[q]; i < so[q + 1]; ++i) expect(sy[i] == q, k, "row-to-system map");
+        auto tr = fetch(L.tile_row, (size_t)L.ntiles + 1);
+        auto st = fetch(L.sys_tile, (size_t)h.nsys + 1);
+        expect(st[0] == 0 && st[h.nsys] == L.ntiles && tr[L.ntiles] == L.n, k, "tile ends");
+        for (int q = 0; q < h.nsys; ++q)
+          for (int32_t t = st[q]; t < st[q + 1]; ++t)
+            expect(tr[t] >= so[q] && tr[t] < tr[t + 1] && tr[t + 1] <= so[q + 1], k, "tile crosses a system");
+        if (!last && k + 1 < h.L) {
+          auto agg = fetch(L.agg, (size_t)L.n);
+          const auto &sn = h.lev[k + 1].sys_off_host;
+          for (int q = 0; q < h.nsys; ++q)
+            for (int32_t i = so[q]; i < so[q + 1]; ++i)
+              expect(agg[i] >= sn[q] && agg[i] < sn[q + 1], k, "aggregate leaves its system");
+        }
+      }
+    }
+    if (h.batched) {
+      const amg::Level &Lc = h.lev[h.L - 1];
+      auto bo = fetch(h.binv_off, (size_t)h.nsys + 1);
+      for (int q = 0; q < h.nsys; ++q) {
+        const int64_t m = Lc.sys_off_host[q + 1] - Lc.sys_off_host[q];
+        expect(bo[q + 1] - bo[q] == m * m, h.L - 1, "coarsest block offsets");
+      }
+      expect(h.nL == Lc.n, h.L - 1, "coarsest size");
+    }
     return AMG_OK;
   });
 }

@@ -142,6 +142,51 @@ __global__ void k_sort_unique(int32_t n, const int32_t *__restrict__ off, int32_
   }
 }
 
+// Structurally symmetric patterns: N_i = {j : C_ij or C_ji} is a subset of row
+// i of A, so it can be marked in place (the entry (j, i) is found by binary
+// search in the sorted row j) and compacted in CSR order, which is already
+// ascending and duplicate-free.  A missing mirror entry sets *nonsym and the
+// caller falls back to the general construction.
+__global__ void k_sym_mirror(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                             const uint8_t *__restrict__ C, uint8_t *__restrict__ S, int32_t *__restrict__ scount,
+                             int *__restrict__ nonsym) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int32_t cnt = 0;
+    for (int32_t p = rp[i]; p < rp[i + 1]; ++p) {
+      const int32_t j = ci[p];
+      if (j == i) {
+        S[p] = 0;
+        continue;
+      }
+      int32_t lo = rp[j], hi = rp[j + 1] - 1, q = -1;
+      while (lo <= hi) {
+        const int32_t mid = (lo + hi) >> 1;
+        const int32_t c = ci[mid];
+        if (c == i) {
+          q = mid;
+          break;
+        }
+        if (c < i) lo = mid + 1; else hi = mid - 1;
+      }
+      if (q < 0) atomicOr(nonsym, 1);
+      const uint8_t sv = C[p] | (q >= 0 ? C[q] : (uint8_t)0);
+      S[p] = sv;
+      cnt += sv;
+    }
+    scount[i] = cnt;
+  }
+}
+
+__global__ void k_sym_mirror_fill(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                  const uint8_t *__restrict__ S, const int32_t *__restrict__ Sptr,
+                                  int32_t *__restrict__ Scol) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int32_t k = Sptr[i];
+    for (int32_t p = rp[i]; p < rp[i + 1]; ++p)
+      if (S[p]) Scol[k++] = ci[p];
+  }
+}
+
 __global__ void k_compact(int32_t n, const int32_t *__restrict__ off, const int32_t *__restrict__ tmp,
                           const int32_t *__restrict__ Sptr, int32_t *__restrict__ Scol) {
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -414,7 +459,7 @@ __global__ void __launch_bounds__(kGalWarps * 32) k_galerkin(
         if (next == INT_MAX) break;
         cur = next;
       }
-      if (!FILL && lane == 0) ccount[I] = out;
+      if (ccount && lane == 0) ccount[I] = out;
       __syncwarp();
       continue;
     }
@@ -461,7 +506,31 @@ __global__ void __launch_bounds__(kGalWarps * 32) k_galerkin(
       if (next == INT_MAX) break;
       cur = next;
     }
-    if (!FILL && lane == 0) ccount[I] = out;
+    if (ccount && lane == 0) ccount[I] = out;
+  }
+}
+
+// entries of the run of keys (I, *): the summed lengths of the member rows,
+// an upper bound on the number of coarse nonzeros of row I
+__global__ void k_run_length(int32_t nc, const int32_t *__restrict__ aptr, const int32_t *__restrict__ amem,
+                             const int32_t *__restrict__ rp, int32_t *__restrict__ len) {
+  for (int32_t I = blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += gridDim.x * blockDim.x) {
+    int32_t t = 0;
+    for (int32_t m = aptr[I]; m < aptr[I + 1]; ++m) t += rp[amem[m] + 1] - rp[amem[m]];
+    len[I] = t;
+  }
+}
+
+// copy row I from its upper-bound slot to the compact coarse CSR
+__global__ void k_compact_rows(int32_t nc, const int32_t *__restrict__ ub, const int32_t *__restrict__ crp,
+                               const int32_t *__restrict__ tci, const double *__restrict__ tval,
+                               int32_t *__restrict__ cci, double *__restrict__ cval) {
+  for (int32_t I = blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += gridDim.x * blockDim.x) {
+    const int32_t len = crp[I + 1] - crp[I];
+    for (int32_t t = 0; t < len; ++t) {
+      cci[crp[I] + t] = tci[ub[I] + t];
+      cval[crp[I] + t] = tval[ub[I] + t];
+    }
   }
 }
 
@@ -589,18 +658,29 @@ __global__ void k_div_dev(int32_t n, double *__restrict__ y, const double *__res
 // Largest |eigenvalue| of a small symmetric matrix by bisection on the inertia
 // of T - sigma I (Sylvester's law: the number of negative pivots of Gaussian
 // elimination without pivoting equals the number of eigenvalues below sigma).
-__device__ int count_below(const double *T, int m, double sigma) {
-  double a[8][8];
-  for (int r = 0; r < m; ++r)
-    for (int c = 0; c < m; ++c) a[r][c] = T[r * m + c] - (r == c ? sigma : 0.0);
+constexpr int kArnoldiMax = 5;  // Arnoldi steps (m <= 5, Eq. damped Jacobi)
+
+// fully unrolled over the 5 x 5 bound so that the matrix stays in registers;
+// rows and columns beyond m act as an identity block (no negative pivots)
+__device__ int count_below(const double (&T)[kArnoldiMax][kArnoldiMax], int m, double sigma) {
+  double a[kArnoldiMax][kArnoldiMax];
+#pragma unroll
+  for (int r = 0; r < kArnoldiMax; ++r)
+#pragma unroll
+    for (int c = 0; c < kArnoldiMax; ++c)
+      a[r][c] = (r < m && c < m) ? T[r][c] - (r == c ? sigma : 0.0) : (r == c ? 1.0 : 0.0);
   int neg = 0;
-  for (int k = 0; k < m; ++k) {
+#pragma unroll
+  for (int k = 0; k < kArnoldiMax; ++k) {
     double piv = a[k][k];
     if (piv == 0.0) piv = 1e-300;  // sigma sits on an eigenvalue of a leading block
     if (piv < 0.0) neg++;
-    for (int r = k + 1; r < m; ++r) {
-      const double f = a[r][k] / piv;
-      for (int c = k + 1; c < m; ++c) a[r][c] -= f * a[k][c];
+    const double inv = 1.0 / piv;
+#pragma unroll
+    for (int r = k + 1; r < kArnoldiMax; ++r) {
+      const double f = a[r][k] * inv;
+#pragma unroll
+      for (int c = k + 1; c < kArnoldiMax; ++c) a[r][c] -= f * a[k][c];
     }
   }
   return neg;
@@ -621,13 +701,15 @@ __global__ void k_omega_from_H(const double *__restrict__ H, const double *__res
       mm = j + 1;
       break;
     }
-  double T[64];
+  double T[kArnoldiMax][kArnoldiMax];
   double g = 0.0;
-  for (int a = 0; a < mm; ++a) {
+#pragma unroll
+  for (int a = 0; a < kArnoldiMax; ++a) {
     double rs = 0.0;
-    for (int b = 0; b < mm; ++b) {
-      T[a * mm + b] = 0.5 * (H[a * 8 + b] + H[b * 8 + a]);
-      rs += fabs(T[a * mm + b]);
+#pragma unroll
+    for (int b = 0; b < kArnoldiMax; ++b) {
+      T[a][b] = (a < mm && b < mm) ? 0.5 * (H[a * 8 + b] + H[b * 8 + a]) : 0.0;
+      rs += fabs(T[a][b]);
     }
     g = fmax(g, rs);
   }
@@ -667,8 +749,25 @@ __global__ void k_dense_from_csr(int32_t n, const int32_t *__restrict__ rp, cons
 
 // In-place dense Cholesky (lower) by one thread block, then the inverse
 // A^-1 = L^-T L^-1 column by column (one thread per column).
+__device__ void cholesky_inverse_body(int32_t n, double *__restrict__ A, double *__restrict__ Ainv,
+                                      int *__restrict__ err);
+
 __global__ void k_cholesky_inverse(int32_t n, double *__restrict__ A, double *__restrict__ Ainv,
                                    int *__restrict__ err) {
+  cholesky_inverse_body(n, A, Ainv, err);
+}
+
+// one thread block per system block of a batch
+__global__ void k_cholesky_inverse_batched(int32_t nsys, const int32_t *__restrict__ off,
+                                           const int64_t *__restrict__ boff, double *__restrict__ A,
+                                           double *__restrict__ Ainv, int *__restrict__ err) {
+  const int32_t s = blockIdx.x;
+  if (s >= nsys) return;
+  cholesky_inverse_body(off[s + 1] - off[s], A + boff[s], Ainv + boff[s], err);
+}
+
+__device__ void cholesky_inverse_body(int32_t n, double *__restrict__ A, double *__restrict__ Ainv,
+                                      int *__restrict__ err) {
   __shared__ int bad;
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
@@ -709,6 +808,34 @@ __global__ void k_cholesky_inverse(int32_t n, double *__restrict__ A, double *__
   }
 }
 
+__global__ void k_gather_i32(int32_t n, const int32_t *__restrict__ idx, const int32_t *__restrict__ src,
+                             int32_t *__restrict__ dst) {
+  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[idx[i]];
+}
+
+// block-diagonal assembly: rows of system s shifted by (row0, nnz0)
+__global__ void k_shift_rowptr(int32_t n, const int32_t *__restrict__ rp, int64_t nnz0, int32_t *__restrict__ out) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += gridDim.x * blockDim.x)
+    out[i] = (int32_t)(rp[i] + nnz0);
+}
+__global__ void k_shift_col(int64_t nnz, const int32_t *__restrict__ ci, int32_t row0, int32_t *__restrict__ out) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x)
+    out[p] = ci[p] + row0;
+}
+
+// coarsest level of a batch: one dense block per system, copied from the CSR
+__global__ void k_dense_blocks(int32_t nsys, const int32_t *__restrict__ off, const int64_t *__restrict__ boff,
+                               const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                               const double *__restrict__ val, double *__restrict__ dense) {
+  const int32_t s = blockIdx.x;
+  if (s >= nsys) return;
+  const int32_t r0 = off[s], m = off[s + 1] - r0;
+  double *D = dense + boff[s];
+  for (int32_t i = threadIdx.x; i < m; i += blockDim.x)
+    for (int32_t p = rp[r0 + i]; p < rp[r0 + i + 1]; ++p) D[(int64_t)i * m + (ci[p] - r0)] = val[p];
+}
+
 __global__ void k_fill_f64(int64_t n, double *p, double v) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     p[i] = v;
@@ -736,7 +863,7 @@ struct Coarsening {
   int32_t rounds = 0;
 };
 
-Coarsening coarsen_level(Hierarchy &h, int k, cudaStream_t s, int32_t *agg_out) {
+Coarsening coarsen_level(Hierarchy &h, int k, cudaStream_t s, int32_t *agg_out, int32_t *next_sys_off) {
   Level &L = h.lev[k];
   const int32_t n = L.n;
   const int64_t nnz = L.nnz;
@@ -747,19 +874,34 @@ Coarsening coarsen_level(Hierarchy &h, int k, cudaStream_t s, int32_t *agg_out) 
   AMG_CUDA(cudaMemsetAsync(cursor.p, 0, sizeof(int32_t) * (n + 1), s));
   AMG_COUNT(), k_strength<<<grid_for(n, 256), 256, 0, s>>>(n, L.rp, L.ci, L.val, h.p.alpha, C.p, rowcnt.p, colcnt.p);
   AMG_LAUNCH_CHECK();
-  AMG_COUNT(), k_add_i32<<<gb, 256, 0, s>>>(n, rowcnt.p, colcnt.p, deg.p);
-  int32_t total = 0;
-  exclusive_scan<int32_t, int32_t>(deg.p, off.p, n, s, &total);
-  DevBuf<int32_t> tmp((size_t)total + 1), ucount(n + 1), Sptr(n + 1);
-  AMG_COUNT(), k_sym_fill<<<grid_for(n, 256), 256, 0, s>>>(n, L.rp, L.ci, C.p, rowcnt.p, off.p, cursor.p, tmp.p);
-  AMG_LAUNCH_CHECK();
-  AMG_COUNT(), k_sort_unique<<<grid_for(n, 128), 128, 0, s>>>(n, off.p, tmp.p, ucount.p);
-  AMG_LAUNCH_CHECK();
+  DevBuf<int32_t> ucount(n + 1), Sptr(n + 1);
+  DevBuf<int32_t> Scol;
   int32_t ns = 0;
-  exclusive_scan<int32_t, int32_t>(ucount.p, Sptr.p, n, s, &ns);
-  DevBuf<int32_t> Scol((size_t)ns + 1);
-  AMG_COUNT(), k_compact<<<grid_for(n, 256), 256, 0, s>>>(n, off.p, tmp.p, Sptr.p, Scol.p);
-  AMG_LAUNCH_CHECK();
+  {  // N_i for a structurally symmetric pattern: mark in place, compact
+    DevBuf<uint8_t> S(nnz);
+    DevBuf<int> nonsym(1);
+    AMG_CUDA(cudaMemsetAsync(nonsym.p, 0, sizeof(int), s));
+    AMG_COUNT(), k_sym_mirror<<<grid_for(n, 256), 256, 0, s>>>(n, L.rp, L.ci, C.p, S.p, ucount.p, nonsym.p);
+    AMG_LAUNCH_CHECK();
+    exclusive_scan<int32_t, int32_t>(ucount.p, Sptr.p, n, s, &ns);
+    if (!read_scalar(nonsym.p, s)) {
+      Scol.resize((size_t)ns + 1);
+      AMG_COUNT(), k_sym_mirror_fill<<<grid_for(n, 256), 256, 0, s>>>(n, L.rp, L.ci, S.p, Sptr.p, Scol.p);
+      AMG_LAUNCH_CHECK();
+    } else {  // general pattern: collect C rows and transposed entries, sort, deduplicate
+      AMG_COUNT(), k_add_i32<<<gb, 256, 0, s>>>(n, rowcnt.p, colcnt.p, deg.p);
+      int32_t total = 0;
+      exclusive_scan<int32_t, int32_t>(deg.p, off.p, n, s, &total);
+      DevBuf<int32_t> tmp((size_t)total + 1);
+      AMG_COUNT(), k_sym_fill<<<grid_for(n, 256), 256, 0, s>>>(n, L.rp, L.ci, C.p, rowcnt.p, off.p, cursor.p, tmp.p);
+      AMG_COUNT(), k_sort_unique<<<grid_for(n, 128), 128, 0, s>>>(n, off.p, tmp.p, ucount.p);
+      AMG_LAUNCH_CHECK();
+      exclusive_scan<int32_t, int32_t>(ucount.p, Sptr.p, n, s, &ns);
+      Scol.resize((size_t)ns + 1);
+      AMG_COUNT(), k_compact<<<grid_for(n, 256), 256, 0, s>>>(n, off.p, tmp.p, Sptr.p, Scol.p);
+      AMG_LAUNCH_CHECK();
+    }
+  }
 
   // PMIS(2)
   DevBuf<uint64_t> key(n), Tw(n);
@@ -768,13 +910,37 @@ Coarsening coarsen_level(Hierarchy &h, int k, cudaStream_t s, int32_t *agg_out) 
   AMG_COUNT(), k_mis_keys<<<gb, 256, 0, s>>>(n, colcnt.p, h.p.seed, k, key.p, st.p);
   AMG_LAUNCH_CHECK();
   Coarsening out;
-  for (int round = 0; round < 100000; ++round) {
-    AMG_CUDA(cudaMemsetAsync(und.p, 0, sizeof(int32_t), s));
-    AMG_COUNT(), k_pmis_max1<<<grid_for(n, 256), 256, 0, s>>>(n, Sptr.p, Scol.p, st.p, key.p, Tw.p, Ti.p);
-    AMG_COUNT(), k_pmis_max2_decide<<<grid_for(n, 256), 256, 0, s>>>(n, Sptr.p, Scol.p, Tw.p, Ti.p, st.p, und.p);
-    AMG_LAUNCH_CHECK();
-    out.rounds = round + 1;
-    if (read_scalar(und.p, s) == 0) break;
+  {
+    // Round r counts its undecided nodes into und[r % 2]; the host reads round
+    // r-1's count while round r runs.  Once a round leaves no undecided node the
+    // round after it changes nothing, so one speculative round is harmless.
+    DevBuf<int32_t> und2(2);
+    int32_t *pin = reinterpret_cast<int32_t *>(h.host_pinned);
+    cudaEvent_t ev[2];
+    AMG_CUDA(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+    AMG_CUDA(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+    bool done = false;
+    for (int round = 0; round < 100000 && !done; ++round) {
+      const int b = round & 1;
+      AMG_CUDA(cudaMemsetAsync(und2.p + b, 0, sizeof(int32_t), s));
+      AMG_COUNT(), k_pmis_max1<<<grid_for(n, 256), 256, 0, s>>>(n, Sptr.p, Scol.p, st.p, key.p, Tw.p, Ti.p);
+      AMG_COUNT(), k_pmis_max2_decide<<<grid_for(n, 256), 256, 0, s>>>(n, Sptr.p, Scol.p, Tw.p, Ti.p, st.p,
+                                                                       und2.p + b);
+      AMG_LAUNCH_CHECK();
+      AMG_CUDA(cudaMemcpyAsync(pin + b, und2.p + b, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      AMG_CUDA(cudaEventRecord(ev[b], s));
+      if (round >= 1) {
+        AMG_CUDA(cudaEventSynchronize(ev[b ^ 1]));
+        if (pin[b ^ 1] == 0) {
+          out.rounds = round;  // rounds 0..round-1 did the work
+          done = true;
+        }
+      }
+      if (!done && round + 1 >= 100000) out.rounds = round + 1;
+    }
+    AMG_CUDA(cudaStreamSynchronize(s));
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
   }
   // aggregation
   DevBuf<int32_t> r1(n), r2(n), isroot(n + 1), cid(n + 1), err(1);
@@ -786,6 +952,10 @@ Coarsening coarsen_level(Hierarchy &h, int k, cudaStream_t s, int32_t *agg_out) 
   exclusive_scan<int32_t, int32_t>(isroot.p, cid.p, n, s, &nc);
   AMG_COUNT(), k_agg_final<<<gb, 256, 0, s>>>(n, r2.p, cid.p, agg_out, err.p);
   AMG_LAUNCH_CHECK();
+  if (next_sys_off) {  // coarse rows of system s start at the number of roots before its first row
+    AMG_COUNT(), k_gather_i32<<<blocks_for(h.nsys + 1), 256, 0, s>>>(h.nsys + 1, L.sys_off, cid.p, next_sys_off);
+    AMG_LAUNCH_CHECK();
+  }
   if (read_scalar(err.p, s) != 0) throw Error{AMG_ERR_SETUP, "aggregation left a node unassigned"};
   out.nc = nc;
   return out;
@@ -867,6 +1037,7 @@ double estimate_omega(Hierarchy &h, int k, const double *diag, cudaStream_t s) {
 void build_hierarchy(Hierarchy &h, const amg_csr &A, cudaStream_t s) {
   const amg_params &p = h.p;
   const int32_t n = A.n;
+  if (!h.host_pinned) AMG_CUDA(cudaMallocHost(&h.host_pinned, 64 * sizeof(double)));
   // ---- level 0: copy and validate the input
   Level &L0 = h.lev[0];
   L0.n = n;
@@ -897,17 +1068,88 @@ void build_hierarchy(Hierarchy &h, const amg_csr &A, cudaStream_t s) {
   L0.B = h.arena.get<double>(n);
   AMG_COUNT(), k_fill_f64<<<grid_for(n, 256), 256, 0, s>>>(n, L0.B, 1.0);  // B_0 = 1
   AMG_LAUNCH_CHECK();
+  coarsen_all(h, s);
+}
 
+// Batch of nsys systems as one block-diagonal matrix.  Strength, MIS and
+// aggregation never couple the blocks, and roots are numbered in ascending
+// fine index, so every level keeps each system's rows contiguous.
+void build_hierarchy_batch(Hierarchy &h, int32_t nsys, const amg_csr *As, cudaStream_t s) {
+  if (!h.host_pinned) AMG_CUDA(cudaMallocHost(&h.host_pinned, 64 * sizeof(double)));
+  h.batched = true;
+  h.nsys = nsys;
+  Level &L0 = h.lev[0];
+  std::vector<int32_t> roff(nsys + 1, 0);
+  std::vector<int64_t> zoff(nsys + 1, 0);
+  for (int32_t q = 0; q < nsys; ++q) {
+    roff[q + 1] = roff[q] + As[q].n;
+    zoff[q + 1] = zoff[q] + As[q].nnz;
+  }
+  if (zoff[nsys] > INT32_MAX) throw Error{AMG_ERR_BAD_INPUT, "batch has more than 2^31 nonzeros"};
+  L0.n = roff[nsys];
+  L0.nnz = zoff[nsys];
+  L0.rp = h.arena.get<int32_t>((size_t)L0.n + 1);
+  L0.ci = h.arena.get<int32_t>((size_t)L0.nnz);
+  L0.val = h.arena.get<double>((size_t)L0.nnz);
+  size_t maxn = 0, maxz = 0;
+  for (int32_t q = 0; q < nsys; ++q) {
+    maxn = std::max(maxn, (size_t)As[q].n + 1);
+    maxz = std::max(maxz, (size_t)As[q].nnz);
+  }
+  DevBuf<int32_t> trp(maxn), tci(maxz);
+  for (int32_t q = 0; q < nsys; ++q) {
+    const amg_csr &A = As[q];
+    const cudaMemcpyKind kind = pointer_kind(A.row_ptr) == PTR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    AMG_CUDA(cudaMemcpyAsync(trp.p, A.row_ptr, sizeof(int32_t) * ((size_t)A.n + 1), kind, s));
+    AMG_CUDA(cudaMemcpyAsync(tci.p, A.col, sizeof(int32_t) * (size_t)A.nnz, kind, s));
+    AMG_CUDA(cudaMemcpyAsync(L0.val + zoff[q], A.val, sizeof(double) * (size_t)A.nnz, kind, s));
+    AMG_COUNT(), k_shift_rowptr<<<grid_for(A.n + 1, 256), 256, 0, s>>>(A.n, trp.p, zoff[q], L0.rp + roff[q]);
+    AMG_COUNT(), k_shift_col<<<grid_for(A.nnz, 256), 256, 0, s>>>(A.nnz, tci.p, roff[q], L0.ci + zoff[q]);
+    AMG_LAUNCH_CHECK();
+  }
+  {
+    DevBuf<int> err(1);
+    AMG_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+    AMG_COUNT(), k_check_csr<<<blocks_for(L0.n), 256, 0, s>>>(L0.n, L0.nnz, L0.rp, L0.ci, L0.val, err.p);
+    AMG_LAUNCH_CHECK();
+    if (read_scalar(err.p, s)) throw Error{AMG_ERR_BAD_INPUT, "invalid CSR in the batch"};
+  }
+  L0.sys_off_host = roff;
+  L0.sys_off = h.arena.get<int32_t>(nsys + 1);
+  AMG_CUDA(cudaMemcpyAsync(L0.sys_off, roff.data(), sizeof(int32_t) * (nsys + 1), cudaMemcpyHostToDevice, s));
+  L0.B = h.arena.get<double>(L0.n);
+  AMG_COUNT(), k_fill_f64<<<grid_for(L0.n, 256), 256, 0, s>>>(L0.n, L0.B, 1.0);
+  AMG_LAUNCH_CHECK();
+  AMG_CUDA(cudaStreamSynchronize(s));
+  coarsen_all(h, s);
+}
+
+void coarsen_all(Hierarchy &h, cudaStream_t s) {
+  const amg_params &p = h.p;
   // ---- Alg. 1: coarsen until the level is small
   int k = 0;
   for (;;) {
     Level &L = h.lev[k];
-    if (L.n <= p.coarse_max || k + 1 >= p.max_levels || k + 1 >= kMaxLevels) break;
+    int32_t largest = L.n;  // a batch stops when its largest system is small
+    if (h.batched) {
+      largest = 0;
+      for (int32_t q = 0; q < h.nsys; ++q) largest = std::max(largest, L.sys_off_host[q + 1] - L.sys_off_host[q]);
+    }
+    if (largest <= p.coarse_max || k + 1 >= p.max_levels || k + 1 >= kMaxLevels) break;
     int32_t *agg = h.arena.get<int32_t>(L.n);
-    Coarsening cr = coarsen_level(h, k, s, agg);
+    int32_t *next_off = h.batched ? h.arena.get<int32_t>(h.nsys + 1) : nullptr;
+    Coarsening cr = coarsen_level(h, k, s, agg, next_off);
     L.mis_rounds = cr.rounds;
     if (10LL * cr.nc >= 9LL * L.n) break;  // coarsening stalled: this level is the coarsest
     const int32_t nc = cr.nc;
+    if (h.batched) {
+      Level &Cn = h.lev[k + 1];
+      Cn.sys_off = next_off;
+      Cn.sys_off_host.resize(h.nsys + 1);
+      AMG_CUDA(cudaMemcpyAsync(Cn.sys_off_host.data(), next_off, sizeof(int32_t) * (h.nsys + 1),
+                               cudaMemcpyDeviceToHost, s));
+      AMG_CUDA(cudaStreamSynchronize(s));
+    }
     L.agg = agg;
     L.nc = nc;
     // members of every aggregate, ascending
@@ -931,19 +1173,23 @@ void build_hierarchy(Hierarchy &h, const amg_csr &A, cudaStream_t s) {
     AMG_LAUNCH_CHECK();
     // Galerkin keyed sum: count, offsets, fill
     Cl.rp = h.arena.get<int32_t>((size_t)nc + 1);
-    {
-      DevBuf<int32_t> ccount(nc + 1);
+    {  // one walk per coarse row into upper-bound slots, then compaction
+      DevBuf<int32_t> ccount(nc + 1), rlen(nc + 1), ub(nc + 1);
       const int gw = grid_for((int64_t)nc * 32, 256, 152 * 64);
-      AMG_COUNT(), k_galerkin<false><<<gw, 256, 0, s>>>(nc, L.aptr, L.amem, L.rp, L.ci, L.val, agg, L.pw64, ccount.p,
-                                          nullptr, nullptr, nullptr);
+      AMG_COUNT(), k_run_length<<<grid_for(nc, 256), 256, 0, s>>>(nc, L.aptr, L.amem, L.rp, rlen.p);
+      AMG_LAUNCH_CHECK();
+      exclusive_scan<int32_t, int32_t>(rlen.p, ub.p, nc, s);
+      DevBuf<int32_t> tci(L.nnz + 1);
+      DevBuf<double> tval(L.nnz + 1);
+      AMG_COUNT(), k_galerkin<true><<<gw, 256, 0, s>>>(nc, L.aptr, L.amem, L.rp, L.ci, L.val, agg, L.pw64,
+                                                       ccount.p, ub.p, tci.p, tval.p);
       AMG_LAUNCH_CHECK();
       int32_t cnnz = 0;
       exclusive_scan<int32_t, int32_t>(ccount.p, Cl.rp, nc, s, &cnnz);
       Cl.nnz = cnnz;
       Cl.ci = h.arena.get<int32_t>(cnnz);
       Cl.val = h.arena.get<double>(cnnz);
-      AMG_COUNT(), k_galerkin<true><<<gw, 256, 0, s>>>(nc, L.aptr, L.amem, L.rp, L.ci, L.val, agg, L.pw64, nullptr, Cl.rp,
-                                         Cl.ci, Cl.val);
+      AMG_COUNT(), k_compact_rows<<<grid_for(nc, 256), 256, 0, s>>>(nc, ub.p, Cl.rp, tci.p, tval.p, Cl.ci, Cl.val);
       AMG_LAUNCH_CHECK();
     }
     ++k;
@@ -963,6 +1209,32 @@ void build_hierarchy(Hierarchy &h, const amg_csr &A, cudaStream_t s) {
 
   // ---- coarsest level: dense factorisation and inverse
   Level &Lc = h.lev[h.L - 1];
+  if (h.batched) {  // one dense block per system
+    std::vector<int64_t> boff(h.nsys + 1, 0);
+    int32_t bmax = 0;
+    for (int32_t q = 0; q < h.nsys; ++q) {
+      const int32_t m = Lc.sys_off_host[q + 1] - Lc.sys_off_host[q];
+      bmax = std::max(bmax, m);
+      boff[q + 1] = boff[q] + (int64_t)m * m;
+    }
+    if (bmax > kMaxDense)
+      throw Error{AMG_ERR_SETUP, "a system's coarsest level has " + std::to_string(bmax) + " unknowns"};
+    h.bmax = bmax;
+    h.nL = Lc.n;
+    h.binv = h.arena.get<double>((size_t)boff[h.nsys]);
+    h.binv_off = h.arena.get<int64_t>(h.nsys + 1);
+    AMG_CUDA(cudaMemcpyAsync(h.binv_off, boff.data(), sizeof(int64_t) * (h.nsys + 1), cudaMemcpyHostToDevice, s));
+    DevBuf<double> dense((size_t)boff[h.nsys]);
+    DevBuf<int> err(1);
+    AMG_CUDA(cudaMemsetAsync(dense.p, 0, sizeof(double) * (size_t)boff[h.nsys], s));
+    AMG_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+    AMG_COUNT(), k_dense_blocks<<<h.nsys, 128, 0, s>>>(h.nsys, Lc.sys_off, h.binv_off, Lc.rp, Lc.ci, Lc.val, dense.p);
+    AMG_COUNT(), k_cholesky_inverse_batched<<<h.nsys, 256, 0, s>>>(h.nsys, Lc.sys_off, h.binv_off, dense.p, h.binv,
+                                                                   err.p);
+    AMG_LAUNCH_CHECK();
+    if (read_scalar(err.p, s)) throw Error{AMG_ERR_SETUP, "a system's coarsest matrix is not positive definite"};
+    return;
+  }
   if (Lc.n > kMaxDense)
     throw Error{AMG_ERR_SETUP, "coarsest level has " + std::to_string(Lc.n) + " unknowns (limit " +
                                    std::to_string(kMaxDense) + "); coarsening stalled"};

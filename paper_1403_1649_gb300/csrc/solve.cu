@@ -107,6 +107,7 @@ __device__ __forceinline__ double dot_operand(int op, double x, double y, double
 
 template <class MV, class VT, int EPI>
 __global__ void __launch_bounds__(kThreads, 4) k_sell(SellArgs<VT> a) {
+  pdl_wait_and_trigger();
   if (a.pred && *a.pred == 0) return;
   const int lane = threadIdx.x & 31;
   const MV *__restrict__ sval = static_cast<const MV *>(a.sval);
@@ -169,6 +170,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_sell(SellArgs<VT> a) {
 template <class VT>
 __global__ void k_scale(int32_t n, VT *__restrict__ out, const VT *__restrict__ wd, const VT *__restrict__ rhs,
                         const int *pred) {
+  pdl_wait_and_trigger();
   if (pred && *pred == 0) return;
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = wd[i] * rhs[i];
 }
@@ -179,6 +181,7 @@ template <class VT>
 __global__ void k_restrict(int32_t nc, const int32_t *__restrict__ aptr, const int32_t *__restrict__ amem,
                            const VT *__restrict__ pw, const VT *__restrict__ r, VT *__restrict__ bc,
                            const VT *__restrict__ wdc, VT *__restrict__ x0c, const int *pred) {
+  pdl_wait_and_trigger();
   if (pred && *pred == 0) return;
   for (int32_t I = blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += gridDim.x * blockDim.x) {
     VT s = VT(0);
@@ -195,6 +198,7 @@ __global__ void k_restrict(int32_t nc, const int32_t *__restrict__ aptr, const i
 template <class VT>
 __global__ void k_prolong(int32_t n, const int32_t *__restrict__ agg, const VT *__restrict__ pw,
                           const VT *__restrict__ xc, VT *__restrict__ x, const int *pred) {
+  pdl_wait_and_trigger();
   if (pred && *pred == 0) return;
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     x[i] += pw[i] * xc[agg[i]];
@@ -204,6 +208,7 @@ __global__ void k_prolong(int32_t n, const int32_t *__restrict__ agg, const VT *
 template <class VT>
 __global__ void k_coarse(int32_t nL, const double *__restrict__ Ainv, const VT *__restrict__ b, VT *__restrict__ x,
                          const VT *__restrict__ wdc_unused, const int *pred) {
+  pdl_wait_and_trigger();
   if (pred && *pred == 0) return;
   const int lane = threadIdx.x & 31;
   for (int32_t i = blockIdx.x * kWarps + (threadIdx.x >> 5); i < nL; i += gridDim.x * kWarps) {
@@ -235,6 +240,7 @@ __device__ __forceinline__ double sum_partials(const double *__restrict__ part, 
 
 // Alg. 5 after v = A c: rho_1 and alpha_1 (CG: c^T v, c^T r; GMRES: ||v||^2, v^T r)
 __global__ void k_fin_k1(const double *__restrict__ part, int nb, double *__restrict__ slots, const int *pred) {
+  pdl_wait_and_trigger();
   if (pred && *pred == 0) return;
   const double rho1 = sum_partials(part, 0, nb);
   const double a1 = sum_partials(part, 1, nb);
@@ -251,6 +257,7 @@ template <class VT>
 __global__ void k_axpy_rt(int32_t n, const VT *__restrict__ r, const VT *__restrict__ v, VT *__restrict__ rt,
                           const VT *__restrict__ wd, VT *__restrict__ x0, const double *__restrict__ slots,
                           double *__restrict__ part, const int *pred) {
+  pdl_wait_and_trigger();
   if (pred && *pred == 0) return;
   const VT s1 = (VT)slots[S_S1];
   double acc[3] = {0.0, 0.0, 0.0};
@@ -269,6 +276,7 @@ __global__ void k_axpy_rt(int32_t n, const VT *__restrict__ r, const VT *__restr
 // and ||r~|| > t ||r||.  Never predicated, so a skipped parent clears it.
 __global__ void k_decide(const double *__restrict__ part, int nb, double *__restrict__ slots, double t,
                          const int *parent, int *__restrict__ flag) {
+  pdl_wait_and_trigger();
   const double nrt2 = sum_partials(part, 0, nb);
   const double nr2 = sum_partials(part, 1, nb);
   if (threadIdx.x == 0) {
@@ -282,6 +290,7 @@ __global__ void k_decide(const double *__restrict__ part, int nb, double *__rest
 
 // Alg. 5 after w = A d: gamma, beta, alpha_2, rho_2 and the combination weights
 __global__ void k_fin_k3(const double *__restrict__ part, int nb, double *__restrict__ slots, const int *pred) {
+  pdl_wait_and_trigger();
   if (pred && *pred == 0) return;
   const double gam = sum_partials(part, 0, nb);
   const double bet = sum_partials(part, 1, nb);
@@ -301,6 +310,7 @@ __global__ void k_fin_k3(const double *__restrict__ part, int nb, double *__rest
 template <class VT>
 __global__ void k_combine(int32_t n, const VT *__restrict__ c, const VT *__restrict__ d, VT *__restrict__ x,
                           const double *__restrict__ slots, const int *__restrict__ flag, const int *pred) {
+  pdl_wait_and_trigger();
   if (pred && *pred == 0) return;
   const bool two = *flag != 0;
   const VT cc = (VT)(two ? slots[S_CC] : slots[S_S1]);
@@ -313,6 +323,7 @@ __global__ void k_combine(int32_t n, const VT *__restrict__ c, const VT *__restr
 template <class VT>
 __global__ void k_to_vt(int32_t n, const double *__restrict__ in, VT *__restrict__ out, const VT *__restrict__ wd,
                         VT *__restrict__ x0, const int *pred) {
+  pdl_wait_and_trigger();
   if (pred && *pred == 0) return;
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const VT v = (VT)in[i];
@@ -325,6 +336,7 @@ __global__ void k_to_vt(int32_t n, const double *__restrict__ in, VT *__restrict
 template <class VT>
 __global__ void k_from_vt_dot(int32_t n, const VT *__restrict__ zin, double *__restrict__ z,
                               const double *__restrict__ q, double *__restrict__ part, const int *pred) {
+  pdl_wait_and_trigger();
   if (pred && *pred == 0) return;
   double acc[3] = {0.0, 0.0, 0.0};
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -339,6 +351,7 @@ __global__ void k_from_vt_dot(int32_t n, const VT *__restrict__ zin, double *__r
 __global__ void k_fcg_p(int32_t n, const double *__restrict__ z, double *__restrict__ p,
                         const double *__restrict__ part_zq, int nb, double *__restrict__ slots,
                         const int *__restrict__ restart, const int *pred) {
+  pdl_wait_and_trigger();
   if (pred && *pred == 0) return;
   const double zq = sum_partials(part_zq, 0, nb);
   const bool rs = *restart != 0;
@@ -358,6 +371,7 @@ __global__ void k_fcg_update(int32_t n, double *__restrict__ x, double *__restri
                              const double *__restrict__ q, const double *__restrict__ part_pq, int nb,
                              double *__restrict__ slots, double *__restrict__ part_rr, VT *__restrict__ rvt,
                              const VT *__restrict__ wd, VT *__restrict__ x0, const int *pred) {
+  pdl_wait_and_trigger();
   if (pred && *pred == 0) return;
   const double pq = sum_partials(part_pq, 0, nb);
   const double pr = sum_partials(part_pq, 1, nb);
@@ -387,6 +401,7 @@ __global__ void k_fcg_update(int32_t n, double *__restrict__ x, double *__restri
 __global__ void k_fcg_fin(const double *__restrict__ part_rr, int nb, double *__restrict__ slots,
                           double *__restrict__ hist, int *__restrict__ it, int *__restrict__ active,
                           int *__restrict__ restart, int *__restrict__ status) {
+  pdl_wait_and_trigger();
   if (*active == 0) return;
   const double tol = slots[S_TOL];
   const int max_iter = (int)slots[S_MAXIT];
@@ -418,6 +433,7 @@ __global__ void k_fcg_fin(const double *__restrict__ part_rr, int nb, double *__
 // block partial dot (generic)
 __global__ void k_dot64(int32_t n, const double *__restrict__ a, const double *__restrict__ b,
                         double *__restrict__ part, const int *pred) {
+  pdl_wait_and_trigger();
   if (pred && *pred == 0) return;
   double acc[3] = {0.0, 0.0, 0.0};
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) acc[0] += a[i] * b[i];
@@ -425,6 +441,7 @@ __global__ void k_dot64(int32_t n, const double *__restrict__ a, const double *_
 }
 
 __global__ void k_store_sum(const double *__restrict__ part, int nb, double *__restrict__ dst) {
+  pdl_wait_and_trigger();
   const double v = sum_partials(part, 0, nb);
   if (threadIdx.x == 0) *dst = v;
 }
@@ -434,6 +451,7 @@ __global__ void k_residual64(int32_t n, int32_t nslices, const int64_t *__restri
                              const int32_t *__restrict__ scol, const double *__restrict__ sval,
                              const double *__restrict__ x, const double *__restrict__ b, double *__restrict__ r,
                              double *__restrict__ part) {
+  pdl_wait_and_trigger();
   const int lane = threadIdx.x & 31;
   double acc[3] = {0.0, 0.0, 0.0};
   for (int32_t sl = blockIdx.x * kWarps + (threadIdx.x >> 5); sl < nslices; sl += gridDim.x * kWarps) {
@@ -461,6 +479,7 @@ constexpr int kMaxRestart = 32;
 // columns per sweep over the rows
 __global__ void k_mdot(int32_t n, const double *__restrict__ V, int ncol, const double *__restrict__ w,
                        double *__restrict__ part, const int *pred) {
+  pdl_wait_and_trigger();
   if (pred && *pred == 0) return;
   __shared__ double sh[kWarps][8];
   for (int c0 = 0; c0 < ncol; c0 += 8) {
@@ -491,6 +510,7 @@ __global__ void k_mdot(int32_t n, const double *__restrict__ V, int ncol, const 
 // h_l = sum of the partials of column l; H(l, j) += h_l; hc = h
 __global__ void k_fin_mdot(const double *__restrict__ part, int nb, int ncol, double *__restrict__ H, int ldh,
                            int j, double *__restrict__ hc, int accumulate, const int *pred) {
+  pdl_wait_and_trigger();
   if (pred && *pred == 0) return;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int l = wid; l < ncol; l += blockDim.x >> 5) {
@@ -507,6 +527,7 @@ __global__ void k_fin_mdot(const double *__restrict__ part, int nb, int ncol, do
 // w -= sum_l hc_l V_l
 __global__ void k_maxpy(int32_t n, const double *__restrict__ V, int ncol, const double *__restrict__ hc,
                         double *__restrict__ w, const int *pred) {
+  pdl_wait_and_trigger();
   if (pred && *pred == 0) return;
   __shared__ double h[kMaxRestart + 1];
   for (int l = threadIdx.x; l < ncol; l += blockDim.x) h[l] = hc[l];
@@ -522,6 +543,7 @@ __global__ void k_maxpy(int32_t n, const double *__restrict__ V, int ncol, const
 __global__ void k_fg_normalize(int32_t n, const double *__restrict__ w, double *__restrict__ vnext,
                                const double *__restrict__ part, int nb, double *__restrict__ H, int ldh, int j,
                                const int *pred) {
+  pdl_wait_and_trigger();
   if (pred && *pred == 0) return;
   const double nrm = sqrt(sum_partials(part, 0, nb));
   if (blockIdx.x == 0 && threadIdx.x == 0) H[(j + 1) * ldh + j] = nrm;
@@ -535,6 +557,7 @@ __global__ void k_fg_normalize(int32_t n, const double *__restrict__ w, double *
 __global__ void k_fg_givens(double *__restrict__ H, int ldh, int j, int m, double *__restrict__ fg,
                             double *__restrict__ slots, double *__restrict__ hist, int *__restrict__ it,
                             int *__restrict__ active, int *__restrict__ status) {
+  pdl_wait_and_trigger();
   if (threadIdx.x != 0 || blockIdx.x != 0 || *active == 0) return;
   double *g = fg, *cs = fg + m + 1, *sn = fg + 2 * m + 1;
   for (int l = 0; l < j; ++l) {
@@ -570,6 +593,7 @@ __global__ void k_fg_givens(double *__restrict__ H, int ldh, int j, int m, doubl
 
 // y = H(0:j, 0:j)^-1 g by back substitution (one thread), into fg[3m+1 ..]
 __global__ void k_fg_trisolve(const double *__restrict__ H, int ldh, int j, int m, double *__restrict__ fg) {
+  pdl_wait_and_trigger();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const double *g = fg;
   double *y = fg + 3 * m + 1;
@@ -583,6 +607,7 @@ __global__ void k_fg_trisolve(const double *__restrict__ H, int ldh, int j, int 
 // x += sum_l y_l Z_l
 __global__ void k_fg_xupdate(int32_t n, double *__restrict__ x, const double *__restrict__ Z, int ncol,
                              const double *__restrict__ y) {
+  pdl_wait_and_trigger();
   __shared__ double ys[kMaxRestart + 1];
   for (int l = threadIdx.x; l < ncol; l += blockDim.x) ys[l] = y[l];
   __syncthreads();
@@ -596,6 +621,7 @@ __global__ void k_fg_xupdate(int32_t n, double *__restrict__ x, const double *__
 // V_0 = r / ||r||, g = (||r||, 0, ...)
 __global__ void k_fg_start(int32_t n, const double *__restrict__ r, double *__restrict__ v0,
                            const double *__restrict__ slots, int slot_rr, double *__restrict__ fg, int m) {
+  pdl_wait_and_trigger();
   const double beta = sqrt(slots[slot_rr]);
   if (blockIdx.x == 0)
     for (int l = threadIdx.x; l <= m; l += blockDim.x) fg[l] = (l == 0) ? beta : 0.0;
@@ -603,10 +629,246 @@ __global__ void k_fg_start(int32_t n, const double *__restrict__ r, double *__re
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v0[i] = r[i] * inv;
 }
 
+// ---------------------------------------------------------------- batched systems
+// Per-system scalars of the block-diagonal solve.  Inner products are
+// segmented by system: every row tile lies inside one system; tile partials
+// are summed per system in tile order (deterministic).
+
+__global__ void k_sys_of(int32_t n, int32_t nsys, const int32_t *__restrict__ off, int32_t *__restrict__ sys) {
+  pdl_wait_and_trigger();
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int32_t lo = 0, hi = nsys - 1;
+    while (lo < hi) {  // last system whose first row is <= i
+      const int32_t mid = (lo + hi + 1) >> 1;
+      if (off[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    sys[i] = lo;
+  }
+}
+
+// tile partials of up to three inner products a_d . b_d (nullptr b: a . a)
+template <class VT>
+__global__ void k_segdot(int32_t ntiles, const int32_t *__restrict__ tile_row, int ndot, const VT *a0,
+                         const VT *b0, const VT *a1, const VT *b1, const VT *a2, const VT *b2,
+                         double *__restrict__ tpart, const int *pred) {
+  pdl_wait_and_trigger();
+  if (pred && *pred == 0) return;
+  for (int32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int32_t i = tile_row[t] + threadIdx.x; i < tile_row[t + 1]; i += blockDim.x) {
+      s0 += (double)a0[i] * (double)b0[i];
+      if (ndot > 1) s1 += (double)a1[i] * (double)b1[i];
+      if (ndot > 2) s2 += (double)a2[i] * (double)b2[i];
+    }
+    __shared__ double sh[3][kWarps];
+    s0 = warp_sum(s0);
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
+    if ((threadIdx.x & 31) == 0) {
+      sh[0][threadIdx.x >> 5] = s0;
+      sh[1][threadIdx.x >> 5] = s1;
+      sh[2][threadIdx.x >> 5] = s2;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+      double v = 0.0;
+      for (int w = 0; w < kWarps; ++w) v += sh[threadIdx.x][w];
+      if ((int)threadIdx.x < ndot) tpart[(int64_t)threadIdx.x * ntiles + t] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// dot d of system s = sum of its tiles' partials; out[(slot0 + d) * nsys + s]
+__global__ void k_segfin(int32_t nsys, int32_t ntiles, const int32_t *__restrict__ sys_tile, int ndot,
+                         const double *__restrict__ tpart, double *__restrict__ bslots, int slot0, const int *pred) {
+  pdl_wait_and_trigger();
+  if (pred && *pred == 0) return;
+  const int lane = threadIdx.x & 31;
+  for (int32_t s = blockIdx.x * kWarps + (threadIdx.x >> 5); s < nsys; s += gridDim.x * kWarps) {
+    for (int d = 0; d < ndot; ++d) {
+      double v = 0.0;
+      for (int32_t t = sys_tile[s] + lane; t < sys_tile[s + 1]; t += 32) v += tpart[(int64_t)d * ntiles + t];
+      v = warp_sum(v);
+      if (lane == 0) bslots[(int64_t)(slot0 + d) * nsys + s] = v;
+    }
+  }
+}
+
+#define BS(slot, s) bslots[(int64_t)(slot)*nsys + (s)]
+
+// per-system status of a batch while it runs: kIterating, kUpdatedConverged
+// (the updated residual met tol; the true residual is checked next), then
+// AMG_OK or a negative AMG_ERR_* code once the system has stopped
+constexpr int kIterating = 2;
+constexpr int kUpdatedConverged = 1;
+
+// Alg. 5 per system: s1 = alpha_1 / rho_1 (dots in S_RHO1, S_A1)
+__global__ void k_bfin_k1(int32_t nsys, double *__restrict__ bslots, const int *pred) {
+  pdl_wait_and_trigger();
+  if (pred && *pred == 0) return;
+  for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < nsys; s += gridDim.x * blockDim.x)
+    BS(S_S1, s) = BS(S_A1, s) / BS(S_RHO1, s);
+}
+
+template <class VT>
+__global__ void k_baxpy_rt(int32_t n, const int32_t *__restrict__ sys, int32_t nsys, const VT *__restrict__ r,
+                           const VT *__restrict__ v, VT *__restrict__ rt, const VT *__restrict__ wd,
+                           VT *__restrict__ x0, const double *__restrict__ bslots, const int *pred) {
+  pdl_wait_and_trigger();
+  if (pred && *pred == 0) return;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const VT t = r[i] - (VT)BS(S_S1, sys[i]) * v[i];
+    rt[i] = t;
+    x0[i] = wd[i] * t;
+  }
+}
+
+// per-system test ||r~|| <= t ||r|| (norms squared in S_NRT2, S_NR2); flag[nsys] = any
+__global__ void k_bdecide(int32_t nsys, const double *__restrict__ bslots, double t, const int *parent,
+                          int *__restrict__ flag) {
+  pdl_wait_and_trigger();
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  const int active = parent ? *parent : 1;
+  for (int32_t s = threadIdx.x; s < nsys; s += blockDim.x) {
+    const bool second = active && !(sqrt(BS(S_NRT2, s)) <= t * sqrt(BS(S_NR2, s)));
+    flag[s] = second ? 1 : 0;
+    if (second) any = 1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) flag[nsys] = any;
+}
+
+__global__ void k_bfin_k3(int32_t nsys, double *__restrict__ bslots, const int *pred) {
+  pdl_wait_and_trigger();
+  if (pred && *pred == 0) return;
+  for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < nsys; s += gridDim.x * blockDim.x) {
+    const double rho1 = BS(S_RHO1, s), gam = BS(S_GAM, s), bet = BS(S_BET, s), a2 = BS(S_A2, s);
+    const double rho2 = bet - gam * gam / rho1;
+    BS(S_CC, s) = BS(S_S1, s) - gam * a2 / (rho1 * rho2);
+    BS(S_CD, s) = a2 / rho2;
+  }
+}
+
+template <class VT>
+__global__ void k_bcombine(int32_t n, const int32_t *__restrict__ sys, int32_t nsys, const VT *__restrict__ c,
+                           const VT *__restrict__ d, VT *__restrict__ x, const double *__restrict__ bslots,
+                           const int *__restrict__ flag, const int *pred) {
+  pdl_wait_and_trigger();
+  if (pred && *pred == 0) return;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int32_t s = sys[i];
+    x[i] = flag[s] ? (VT)BS(S_CC, s) * c[i] + (VT)BS(S_CD, s) * d[i] : (VT)BS(S_S1, s) * c[i];
+  }
+}
+
+// exact coarsest solve, one dense inverse per system; one warp per row
+template <class VT>
+__global__ void k_bcoarse(int32_t nL, const int32_t *__restrict__ sys, const int32_t *__restrict__ off,
+                          const double *__restrict__ binv, const int64_t *__restrict__ boff, const VT *__restrict__ b,
+                          VT *__restrict__ x, const int *pred) {
+  pdl_wait_and_trigger();
+  if (pred && *pred == 0) return;
+  const int lane = threadIdx.x & 31;
+  for (int32_t i = blockIdx.x * kWarps + (threadIdx.x >> 5); i < nL; i += gridDim.x * kWarps) {
+    const int32_t s = sys[i], r0 = off[s], m = off[s + 1] - r0;
+    const double *Bi = binv + boff[s] + (int64_t)(i - r0) * m;
+    double acc = 0.0;
+    for (int32_t j = lane; j < m; j += 32) acc += Bi[j] * (double)b[r0 + j];
+    acc = warp_sum(acc);
+    if (lane == 0) x[i] = (VT)acc;
+  }
+}
+
+// flexible CG per system.  bact[s]: still iterating; brs[s]: restart (beta = 0)
+__global__ void k_bfcg_beta(int32_t nsys, double *__restrict__ bslots, const int *__restrict__ brs) {
+  pdl_wait_and_trigger();
+  for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < nsys; s += gridDim.x * blockDim.x)
+    BS(S_BETA, s) = brs[s] ? 0.0 : -BS(S_ZQ, s) / BS(S_PQ, s);
+}
+
+__global__ void k_bfcg_p(int32_t n, const int32_t *__restrict__ sys, int32_t nsys, const double *__restrict__ z,
+                         double *__restrict__ p, const double *__restrict__ bslots) {
+  pdl_wait_and_trigger();
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    p[i] = z[i] + BS(S_BETA, sys[i]) * p[i];
+}
+
+__global__ void k_bfcg_alpha(int32_t nsys, double *__restrict__ bslots) {
+  pdl_wait_and_trigger();
+  for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < nsys; s += gridDim.x * blockDim.x)
+    BS(S_ALPHA, s) = BS(S_PR, s) / BS(S_PQ, s);
+}
+
+__global__ void k_bfcg_update(int32_t n, const int32_t *__restrict__ sys, int32_t nsys, double *__restrict__ x,
+                              double *__restrict__ r, const double *__restrict__ p, const double *__restrict__ q,
+                              const double *__restrict__ bslots, const int *__restrict__ bact) {
+  pdl_wait_and_trigger();
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int32_t s = sys[i];
+    if (!bact[s]) continue;  // converged systems keep x and r untouched
+    const double a = BS(S_ALPHA, s);
+    x[i] += a * p[i];
+    r[i] -= a * q[i];
+  }
+}
+
+// end of an iteration: per-system relative residual, iteration count, status;
+// bact[nsys] = number of systems still iterating; hist[k] (k < hist_len) gets
+// the largest relative residual of pass k
+__global__ void k_bfcg_fin(int32_t nsys, double *__restrict__ bslots, int *__restrict__ bact, int *__restrict__ brs,
+                           int *__restrict__ bit, int *__restrict__ bstat, double tol, int max_iter,
+                           double *__restrict__ hist, int hist_len, int *__restrict__ it) {
+  pdl_wait_and_trigger();
+  __shared__ int nact;
+  __shared__ double worst;
+  if (threadIdx.x == 0) {
+    nact = 0;
+    worst = 0.0;
+  }
+  __syncthreads();
+  for (int32_t s = threadIdx.x; s < nsys; s += blockDim.x) {
+    brs[s] = 0;
+    if (!bact[s]) continue;
+    const double rel = sqrt(BS(S_RR, s) / BS(S_NB2, s));
+    BS(S_REL, s) = rel;
+    const int k = bit[s] + 1;
+    bit[s] = k;
+    atomicMax(reinterpret_cast<unsigned long long *>(&worst), __double_as_longlong(isfinite(rel) ? rel : 1e300));
+    if (!(BS(S_PQ, s) > 0.0)) {
+      bstat[s] = AMG_ERR_BREAKDOWN;
+      bact[s] = 0;
+    } else if (!isfinite(rel)) {
+      bstat[s] = AMG_ERR_NAN;
+      bact[s] = 0;
+    } else if (rel <= tol) {
+      bstat[s] = kUpdatedConverged;
+      bact[s] = 0;
+    } else if (k >= max_iter) {
+      bstat[s] = AMG_ERR_NOT_CONVERGED;
+      bact[s] = 0;
+    } else {
+      atomicAdd(&nact, 1);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    bact[nsys] = nact;
+    const int k = *it + 1;
+    *it = k;
+    if (k < hist_len) hist[k] = worst;
+  }
+}
+
+#undef BS
+
 template <class VT>
 __global__ void k_convert_row_data(int32_t n, const double *__restrict__ diag, double omega,
                                    const double *__restrict__ pw64, VT *__restrict__ wd, VT *__restrict__ dinv,
                                    VT *__restrict__ pw) {
+  pdl_wait_and_trigger();
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     wd[i] = (VT)(omega / diag[i]);
     dinv[i] = (VT)(1.0 / diag[i]);
@@ -616,6 +878,7 @@ __global__ void k_convert_row_data(int32_t n, const double *__restrict__ diag, d
 
 template <class VT>
 __global__ void k_copy_cast(int32_t n, const double *__restrict__ in, VT *__restrict__ out) {
+  pdl_wait_and_trigger();
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = (VT)in[i];
 }
 
@@ -623,6 +886,7 @@ __global__ void k_copy_cast(int32_t n, const double *__restrict__ in, VT *__rest
 namespace {
 
 inline int ew_grid(int64_t n) { return grid_for(n, kThreads, kRedBlocks); }
+void prepare_batched(Hierarchy &h, cudaStream_t s);
 // k_sell keeps 4 blocks of 256 threads resident per SM (64 registers): one wave
 inline int sell_grid(const Level &L) { return grid_for((int64_t)L.nslices, kWarps, 4 * 152); }
 
@@ -659,7 +923,7 @@ struct Engine {
 
   template <int EPI>
   void sell(const SellArgs<VT> &a, int k) {
-    k_sell<MV, VT, EPI><<<sell_grid(h.lev[k]), kThreads, 0, s>>>(a);
+    klaunch(k_sell<MV, VT, EPI>, sell_grid(h.lev[k]), kThreads, s, a);
     check();
   }
 
@@ -668,7 +932,11 @@ struct Engine {
   void cycle(int k, const VT *rhs, VT *out, bool x0_ready, const int *pred) {
     Level &L = h.lev[k];
     if (k == h.L - 1) {
-      k_coarse<VT><<<grid_for(h.nL, kWarps, 152), kThreads, 0, s>>>(h.nL, h.coarse_inv, rhs, out, nullptr, pred);
+      if (h.batched)
+        klaunch(k_bcoarse<VT>, grid_for(h.nL, kWarps, 152 * 8), kThreads, s, h.nL, (const int32_t *)L.sys_of,
+                (const int32_t *)L.sys_off, (const double *)h.binv, (const int64_t *)h.binv_off, rhs, out, pred);
+      else
+        klaunch(k_coarse<VT>, grid_for(h.nL, kWarps, 152), kThreads, s, h.nL, h.coarse_inv, rhs, out, nullptr, pred);
       check();
       return;
     }
@@ -676,7 +944,7 @@ struct Engine {
     VT *tmp = V(L.tmp);
     const bool poly = h.p.smoother == 1 && L.poly != nullptr;
     if (poly) {  // x = sum_q diag(c_q) (D^-1 A)^q D^-1 b
-      k_scale<VT><<<ew_grid(L.n), kThreads, 0, s>>>(L.n, V(L.u0), V(L.dinv), rhs, pred);
+      klaunch(k_scale<VT>, ew_grid(L.n), kThreads, s, L.n, V(L.u0), V(L.dinv), rhs, pred);
       check();
       SellArgs<VT> a = sell_args(k, V(L.u0), V(L.u1), pred);
       a.dinv = V(L.dinv);
@@ -688,7 +956,7 @@ struct Engine {
       a.p1 = V(L.u1);
       sell<E_POLYPRE>(a, k);
     } else if (!x0_ready) {
-      k_scale<VT><<<ew_grid(L.n), kThreads, 0, s>>>(L.n, tmp, V(L.wd), rhs, pred);  // pre-smoothing
+      klaunch(k_scale<VT>, ew_grid(L.n), kThreads, s, L.n, tmp, V(L.wd), rhs, pred);  // pre-smoothing
       check();
     }
     {  // r_k = b_k - A_k x_k
@@ -699,7 +967,7 @@ struct Engine {
     const bool coarse_is_last = (k + 1 == h.L - 1);
     const bool tail = (k + 1 == h.tail_t);
     // r_{k+1} = R_k r_k  (and x0 of level k+1 when it smooths)
-    k_restrict<VT><<<ew_grid(L.nc), kThreads, 0, s>>>(L.nc, L.aptr, L.amem, V(L.pw), V(L.r), V(C.bc),
+    klaunch(k_restrict<VT>, ew_grid(L.nc), kThreads, s, L.nc, L.aptr, L.amem, V(L.pw), V(L.r), V(C.bc),
                                                       (coarse_is_last || tail) ? nullptr : V(C.wd), V(C.tmp), pred);
     check();
     if (tail) {  // levels k+1..L-1 in one cluster launch
@@ -723,7 +991,7 @@ struct Engine {
       cycle(k + 1, V(C.bc), V(C.xc), true, pred);  // Alg. 4 recursion
     }
     // x_k += P_k x_{k+1}
-    k_prolong<VT><<<ew_grid(L.n), kThreads, 0, s>>>(L.n, L.agg, V(L.pw), V(C.xc), tmp, pred);
+    klaunch(k_prolong<VT>, ew_grid(L.n), kThreads, s, L.n, L.agg, V(L.pw), V(C.xc), tmp, pred);
     check();
     // r_k = b_k - A_k x_k;  x_k += omega D^-1 r_k  (or the transposed polynomial)
     SellArgs<VT> a = sell_args(k, tmp, out, pred);
@@ -761,8 +1029,56 @@ struct Engine {
   }
   bool zq_fuse = false;
 
+  // per-system inner products of the batch into bslots[slot0 ..]
+  void segdot(int k, int ndot, const VT *a0, const VT *b0, const VT *a1, const VT *b1, const VT *a2, const VT *b2,
+              int slot0, const int *pred) {
+    Level &L = h.lev[k];
+    klaunch(k_segdot<VT>, grid_for(L.ntiles, 1, 152 * 8), kThreads, s, L.ntiles, (const int32_t *)L.tile_row, ndot,
+            a0, b0, a1, b1, a2, b2, L.tpart, pred);
+    klaunch(k_segfin, grid_for(h.nsys, kWarps, 152), kThreads, s, (int32_t)h.nsys, L.ntiles,
+            (const int32_t *)L.sys_tile, ndot, (const double *)L.tpart, L.bslots, slot0, pred);
+    launches += 2;
+    AMG_LAUNCH_CHECK();
+  }
+
+  // Alg. 5 coarse part at level m for every system of a batch, with per-system
+  // scalars; the second inner step runs when any system needs it
+  void krylov2_batched(int m, const int *pred) {
+    Level &L = h.lev[m];
+    const int32_t ns = h.nsys;
+    cycle(m, V(L.bc), V(L.c), true, pred);
+    sell<E_Y>(sell_args(m, V(L.c), V(L.v), pred), m);
+    if (gmres_variant)
+      segdot(m, 2, V(L.v), V(L.v), V(L.v), V(L.bc), nullptr, nullptr, S_RHO1, pred);
+    else
+      segdot(m, 2, V(L.c), V(L.v), V(L.c), V(L.bc), nullptr, nullptr, S_RHO1, pred);
+    klaunch(k_bfin_k1, grid_for(ns, kThreads, 152), kThreads, s, ns, L.bslots, pred);
+    klaunch(k_baxpy_rt<VT>, ew_grid(L.n), kThreads, s, L.n, (const int32_t *)L.sys_of, ns, (const VT *)V(L.bc),
+            (const VT *)V(L.v), V(L.rt), (const VT *)V(L.wd), V(L.tmp), (const double *)L.bslots, pred);
+    segdot(m, 2, V(L.rt), V(L.rt), V(L.bc), V(L.bc), nullptr, nullptr, S_NRT2, pred);
+    klaunch(k_bdecide, 1, 1024, s, ns, (const double *)L.bslots, h.p.kcycle_t, pred, L.bflag);
+    launches += 3;
+    AMG_LAUNCH_CHECK();
+    const int *any = L.bflag + ns;
+    cycle(m, V(L.rt), V(L.d), true, any);
+    sell<E_Y>(sell_args(m, V(L.d), V(L.w), any), m);
+    if (gmres_variant)
+      segdot(m, 3, V(L.w), V(L.v), V(L.w), V(L.w), V(L.w), V(L.rt), S_GAM, any);
+    else
+      segdot(m, 3, V(L.d), V(L.v), V(L.d), V(L.w), V(L.d), V(L.rt), S_GAM, any);
+    klaunch(k_bfin_k3, grid_for(ns, kThreads, 152), kThreads, s, ns, L.bslots, any);
+    klaunch(k_bcombine<VT>, ew_grid(L.n), kThreads, s, L.n, (const int32_t *)L.sys_of, ns, (const VT *)V(L.c),
+            (const VT *)V(L.d), V(L.xc), (const double *)L.bslots, (const int *)L.bflag, pred);
+    launches += 2;
+    AMG_LAUNCH_CHECK();
+  }
+
   // Alg. 5 coarse part at level m: rhs = bc[m], result in xc[m]; lev[m].tmp holds wd*bc.
   void krylov2(int m, const int *pred) {
+    if (h.batched) {
+      krylov2_batched(m, pred);
+      return;
+    }
     Level &L = h.lev[m];
     const int nb = sell_grid(L);
     // c = cycle(m, r)
@@ -778,15 +1094,15 @@ struct Engine {
       }
       sell<E_Y>(a, m);
     }
-    k_fin_k1<<<1, kThreads, 0, s>>>(L.partials, nb, L.slots, pred);
+    klaunch(k_fin_k1, 1, kThreads, s, L.partials, nb, L.slots, pred);
     check();
     const bool deeper_smooths = true;  // level m is not the coarsest here
     (void)deeper_smooths;
     const int ng = ew_grid(L.n);
-    k_axpy_rt<VT><<<ng, kThreads, 0, s>>>(L.n, V(L.bc), V(L.v), V(L.rt), V(L.wd), V(L.tmp), L.slots,
+    klaunch(k_axpy_rt<VT>, ng, kThreads, s, L.n, V(L.bc), V(L.v), V(L.rt), V(L.wd), V(L.tmp), L.slots,
                                           L.partials + 3 * kRedBlocks, pred);
     check();
-    k_decide<<<1, kThreads, 0, s>>>(L.partials + 3 * kRedBlocks, ng, L.slots, h.p.kcycle_t, pred, L.flag);
+    klaunch(k_decide, 1, kThreads, s, L.partials + 3 * kRedBlocks, ng, L.slots, h.p.kcycle_t, pred, L.flag);
     check();
     // second inner step, predicated on the decision
     cycle(m, V(L.rt), V(L.d), true, L.flag);
@@ -806,9 +1122,9 @@ struct Engine {
       }
       sell<E_Y>(a, m);
     }
-    k_fin_k3<<<1, kThreads, 0, s>>>(L.partials, nb, L.slots, L.flag);
+    klaunch(k_fin_k3, 1, kThreads, s, L.partials, nb, L.slots, L.flag);
     check();
-    k_combine<VT><<<ng, kThreads, 0, s>>>(L.n, V(L.c), V(L.d), V(L.xc), L.slots, L.flag, pred);
+    klaunch(k_combine<VT>, ng, kThreads, s, L.n, V(L.c), V(L.d), V(L.xc), L.slots, L.flag, pred);
     check();
   }
 
@@ -820,17 +1136,56 @@ struct Engine {
       cycle(0, (const VT *)r, (VT *)z, false, pred);
       zq_fuse = false;
       if (with_zq && h.L == 1) {
-        k_dot64<<<ew_grid(L0.n), kThreads, 0, s>>>(L0.n, z, h.q, L0.partials + 4 * kRedBlocks, pred);
+        klaunch(k_dot64, ew_grid(L0.n), kThreads, s, L0.n, z, h.q, L0.partials + 4 * kRedBlocks, pred);
         check();
       }
     } else {
-      k_to_vt<VT><<<ew_grid(L0.n), kThreads, 0, s>>>(L0.n, r, V(h.pre_in), V(L0.wd), V(L0.tmp), pred);
+      klaunch(k_to_vt<VT>, ew_grid(L0.n), kThreads, s, L0.n, r, V(h.pre_in), V(L0.wd), V(L0.tmp), pred);
       check();
       cycle(0, V(h.pre_in), V(h.pre_out), true, pred);
-      k_from_vt_dot<VT><<<ew_grid(L0.n), kThreads, 0, s>>>(L0.n, V(h.pre_out), z, h.q,
+      klaunch(k_from_vt_dot<VT>, ew_grid(L0.n), kThreads, s, L0.n, V(h.pre_out), z, h.q,
                                                            L0.partials + 4 * kRedBlocks, pred);
       check();
     }
+  }
+
+  // one flexible-CG iteration of every system of a batch (graph-capturable)
+  void fcg_iteration_batched(double tol) {
+    Level &L0 = h.lev[0];
+    const int32_t ns = h.nsys, n = L0.n;
+    const int ng = ew_grid(n);
+    int *bact = h.bactive, *brs = h.bactive + ns + 1;
+    // z = M r
+    precond(h.r, h.z, nullptr, false);
+    Engine<double, double> e64(h, s);
+    e64.segdot(0, 1, h.z, h.q, nullptr, nullptr, nullptr, nullptr, S_ZQ, nullptr);
+    launches += e64.launches;
+    klaunch(k_bfcg_beta, grid_for(ns, kThreads, 152), kThreads, s, ns, L0.bslots, (const int *)brs);
+    klaunch(k_bfcg_p, ng, kThreads, s, n, (const int32_t *)L0.sys_of, ns, (const double *)h.z, h.pdir,
+            (const double *)L0.bslots);
+    {  // q = A p in FP64
+      SellArgs<double> a{};
+      a.n = n;
+      a.nslices = L0.nslices;
+      a.sptr = L0.sptr;
+      a.scol = L0.scol;
+      a.sval = L0.sval64;
+      a.x = h.pdir;
+      a.out = h.q;
+      klaunch(k_sell<double, double, E_Y>, sell_grid(L0), kThreads, s, a);
+    }
+    launches += 3;
+    e64.launches = 0;
+    e64.segdot(0, 2, h.pdir, h.q, h.pdir, h.r, nullptr, nullptr, S_PQ, nullptr);
+    klaunch(k_bfcg_alpha, grid_for(ns, kThreads, 152), kThreads, s, ns, L0.bslots);
+    klaunch(k_bfcg_update, ng, kThreads, s, n, (const int32_t *)L0.sys_of, ns, h.x, h.r, (const double *)h.pdir,
+            (const double *)h.q, (const double *)L0.bslots, (const int *)bact);
+    e64.segdot(0, 1, h.r, h.r, nullptr, nullptr, nullptr, nullptr, S_RR, nullptr);
+    launches += e64.launches + 2;
+    klaunch(k_bfcg_fin, 1, 1024, s, ns, L0.bslots, bact, brs, h.bit, h.bit + ns, tol, h.p.max_iter, h.hist,
+            h.p.max_iter + 8, h.it_dev);
+    ++launches;
+    AMG_LAUNCH_CHECK();
   }
 
   // one flexible-CG iteration, all on the device (graph-capturable)
@@ -843,7 +1198,7 @@ struct Engine {
     // z = M r (+ z^T q partials)
     precond(h.r, h.z, active, true);
     // p = z + beta p
-    k_fcg_p<<<ng, kThreads, 0, s>>>(L0.n, h.z, h.pdir, part + 4 * kRedBlocks, nzq, L0.slots, restart, active);
+    klaunch(k_fcg_p, ng, kThreads, s, L0.n, h.z, h.pdir, part + 4 * kRedBlocks, nzq, L0.slots, restart, active);
     check();
     {  // q = A p (FP64), p^T q, p^T r
       SellArgs<double> a{};
@@ -860,16 +1215,16 @@ struct Engine {
       a.dop[1][0] = OP_X; a.dop[1][1] = OP_U1;
       a.partials = part + 5 * kRedBlocks;
       a.pred = active;
-      k_sell<double, double, E_Y><<<nsg, kThreads, 0, s>>>(a);
+      klaunch(k_sell<double, double, E_Y>, nsg, kThreads, s, a);
       check();
     }
     // x, r update (+ the next preconditioner input in reduced precision)
     const bool red = !std::is_same<VT, double>::value;
-    k_fcg_update<VT><<<ng, kThreads, 0, s>>>(L0.n, h.x, h.r, h.pdir, h.q, part + 5 * kRedBlocks, nsg, L0.slots,
+    klaunch(k_fcg_update<VT>, ng, kThreads, s, L0.n, h.x, h.r, h.pdir, h.q, part + 5 * kRedBlocks, nsg, L0.slots,
                                              part + 7 * kRedBlocks, nullptr, V(L0.wd), V(L0.tmp), active);
     check();
     (void)red;
-    k_fcg_fin<<<1, kThreads, 0, s>>>(part + 7 * kRedBlocks, ng, L0.slots, h.hist, h.it_dev, active, restart,
+    klaunch(k_fcg_fin, 1, kThreads, s, part + 7 * kRedBlocks, ng, L0.slots, h.hist, h.it_dev, active, restart,
                                      h.status_dev);
     check();
   }
@@ -905,7 +1260,7 @@ void alloc_level_vectors(Hierarchy &h, Level &L, int k) {
 // V-cycles only), and no polynomial smoother on those levels.
 void configure_tail(Hierarchy &h, cudaStream_t s) {
   h.tail_t = -1;
-  if (!h.p.tail) return;
+  if (!h.p.tail || h.batched) return;  // the cluster tail has no per-system scalars
   for (int t = 1; t <= h.L - 2; ++t) {
     if (h.lev[t].n > kTailMaxRows) continue;
     bool ok = true;
@@ -973,7 +1328,8 @@ void prepare_t(Hierarchy &h, cudaStream_t s) {
     h.gpart = h.arena.get<double>((size_t)(kMaxRestart + 1) * kRedBlocks);
     AMG_CUDA(cudaMemsetAsync(h.H, 0, sizeof(double) * (m + 1) * m, s));
   }
-  AMG_CUDA(cudaMallocHost(&h.host_pinned, 64 * sizeof(double)));
+  if (!h.host_pinned) AMG_CUDA(cudaMallocHost(&h.host_pinned, 64 * sizeof(double)));
+  if (h.batched) prepare_batched(h, s);
   configure_tail(h, s);
 }
 
@@ -982,13 +1338,14 @@ void make_row_data_t(Hierarchy &h, Level &L, const double *diag, cudaStream_t s)
   L.wd = h.arena.get<VT>((size_t)L.n + 1);
   L.dinv = h.arena.get<VT>((size_t)L.n + 1);
   L.pw = h.arena.get<VT>((size_t)L.n + 1);
-  k_convert_row_data<VT><<<ew_grid(L.n), kThreads, 0, s>>>(L.n, diag, L.omega, L.pw64, (VT *)L.wd,
+  klaunch(k_convert_row_data<VT>, ew_grid(L.n), kThreads, s, L.n, diag, L.omega, L.pw64, (VT *)L.wd,
                                                            (VT *)L.dinv, (VT *)L.pw);
   AMG_LAUNCH_CHECK();
 }
 
 __global__ void k_set_state(int *it, int *active, int *restart, int *status, int it_v, int active_v,
                             int restart_v, int status_v) {
+  pdl_wait_and_trigger();
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     if (it_v >= 0) *it = it_v;
     *active = active_v;
@@ -998,6 +1355,7 @@ __global__ void k_set_state(int *it, int *active, int *restart, int *status, int
 }
 
 __global__ void k_set_slot(double *slots, int idx, double v) {
+  pdl_wait_and_trigger();
   if (threadIdx.x == 0 && blockIdx.x == 0) slots[idx] = v;
 }
 
@@ -1015,9 +1373,9 @@ void copy_out(double *dst, const double *src_dev, int32_t n, cudaStream_t s) {
 void true_residual(Hierarchy &h, int dst, cudaStream_t s, int64_t &launches) {
   Level &L0 = h.lev[0];
   const int nsg = sell_grid(L0);
-  k_residual64<<<nsg, kThreads, 0, s>>>(L0.n, L0.nslices, L0.sptr, L0.scol, L0.sval64, h.x, h.b, h.r,
+  klaunch(k_residual64, nsg, kThreads, s, L0.n, L0.nslices, L0.sptr, L0.scol, L0.sval64, h.x, h.b, h.r,
                                         L0.partials + 7 * kRedBlocks);
-  k_store_sum<<<1, kThreads, 0, s>>>(L0.partials + 7 * kRedBlocks, nsg, L0.slots + dst);
+  klaunch(k_store_sum, 1, kThreads, s, L0.partials + 7 * kRedBlocks, nsg, L0.slots + dst);
   launches += 2;
   AMG_LAUNCH_CHECK();
 }
@@ -1033,26 +1391,26 @@ int run_solve_t(Hierarchy &h, const double *b, double *x, double tol, int32_t *i
   copy_in(h.b, b, n, s);
   copy_in(h.x, x, n, s);
   // ||b||^2 and the initial residual
-  k_dot64<<<ew_grid(n), kThreads, 0, s>>>(n, h.b, h.b, L0.partials + 6 * kRedBlocks, nullptr);
-  k_store_sum<<<1, kThreads, 0, s>>>(L0.partials + 6 * kRedBlocks, ew_grid(n), L0.slots + S_NB2);
+  klaunch(k_dot64, ew_grid(n), kThreads, s, n, h.b, h.b, L0.partials + 6 * kRedBlocks, nullptr);
+  klaunch(k_store_sum, 1, kThreads, s, L0.partials + 6 * kRedBlocks, ew_grid(n), L0.slots + S_NB2);
   launches += 2;
   AMG_LAUNCH_CHECK();
   true_residual(h, S_RR, s, launches);
-  k_set_slot<<<1, 32, 0, s>>>(L0.slots, S_TOL, tol);
-  k_set_slot<<<1, 32, 0, s>>>(L0.slots, S_MAXIT, (double)h.p.max_iter);
+  klaunch(k_set_slot, 1, 32, s, L0.slots, S_TOL, tol);
+  klaunch(k_set_slot, 1, 32, s, L0.slots, S_MAXIT, (double)h.p.max_iter);
   AMG_CUDA(cudaMemcpyAsync(h.host_pinned, L0.slots, sizeof(double) * kNumSlots, cudaMemcpyDeviceToHost, s));
   AMG_CUDA(cudaStreamSynchronize(s));
   double nb2 = h.host_pinned[S_NB2];
   const double rr0 = h.host_pinned[S_RR];
   const bool zero_b = !(nb2 > 0.0);
-  if (zero_b) nb2 = 1.0, k_set_slot<<<1, 32, 0, s>>>(L0.slots, S_NB2, 1.0);
+  if (zero_b) nb2 = 1.0, klaunch(k_set_slot, 1, 32, s, L0.slots, S_NB2, 1.0);
   double rel = std::sqrt(rr0 / nb2);
   std::vector<double> hist(1, rel);
   int status = AMG_OK;
   int it = 0;
   if (!std::isfinite(rel)) status = AMG_ERR_NAN;
   else if (rel > tol) {
-    k_set_state<<<1, 32, 0, s>>>(h.it_dev, active, restart, h.status_dev, 0, 1, 1, 0);
+    klaunch(k_set_state, 1, 32, s, h.it_dev, active, restart, h.status_dev, 0, 1, 1, 0);
     AMG_CUDA(cudaMemcpyAsync(h.hist, &hist[0], sizeof(double), cudaMemcpyHostToDevice, s));
     AMG_LAUNCH_CHECK();
     // capture one outer iteration as a graph
@@ -1102,7 +1460,7 @@ int run_solve_t(Hierarchy &h, const double *b, double *x, double tol, int32_t *i
           break;
         }
         // iterative refinement: restart flexible CG from the true residual
-        k_set_state<<<1, 32, 0, s>>>(h.it_dev, active, restart, h.status_dev, -1, 1, 1, 0);
+        klaunch(k_set_state, 1, 32, s, h.it_dev, active, restart, h.status_dev, -1, 1, 1, 0);
         AMG_LAUNCH_CHECK();
         continue;
       }
@@ -1144,11 +1502,11 @@ int run_fgmres_t(Hierarchy &h, const double *b, double *x, double tol, int32_t *
   copy_in(h.b, b, n, s);
   copy_in(h.x, x, n, s);
   const int ng = ew_grid(n);
-  k_dot64<<<ng, kThreads, 0, s>>>(n, h.b, h.b, L0.partials + 6 * kRedBlocks, nullptr);
-  k_store_sum<<<1, kThreads, 0, s>>>(L0.partials + 6 * kRedBlocks, ng, L0.slots + S_NB2);
-  k_set_slot<<<1, 32, 0, s>>>(L0.slots, S_TOL, tol);
-  k_set_slot<<<1, 32, 0, s>>>(L0.slots, S_MAXIT, (double)h.p.max_iter);
-  k_set_state<<<1, 32, 0, s>>>(h.it_dev, active, h.it_dev + 2, h.status_dev, 0, 1, 0, 0);
+  klaunch(k_dot64, ng, kThreads, s, n, h.b, h.b, L0.partials + 6 * kRedBlocks, nullptr);
+  klaunch(k_store_sum, 1, kThreads, s, L0.partials + 6 * kRedBlocks, ng, L0.slots + S_NB2);
+  klaunch(k_set_slot, 1, 32, s, L0.slots, S_TOL, tol);
+  klaunch(k_set_slot, 1, 32, s, L0.slots, S_MAXIT, (double)h.p.max_iter);
+  klaunch(k_set_state, 1, 32, s, h.it_dev, active, h.it_dev + 2, h.status_dev, 0, 1, 0, 0);
   launches += 5;
   AMG_LAUNCH_CHECK();
   double *w = h.q;
@@ -1165,7 +1523,7 @@ int run_fgmres_t(Hierarchy &h, const double *b, double *x, double tol, int32_t *
       nb2 = h.host_pinned[S_NB2];
       if (!(nb2 > 0.0)) {
         nb2 = 1.0;
-        k_set_slot<<<1, 32, 0, s>>>(L0.slots, S_NB2, 1.0);
+        klaunch(k_set_slot, 1, 32, s, L0.slots, S_NB2, 1.0);
         ++launches;
       }
       hist.push_back(std::sqrt(h.host_pinned[S_RR] / nb2));
@@ -1175,8 +1533,8 @@ int run_fgmres_t(Hierarchy &h, const double *b, double *x, double tol, int32_t *
     if (!std::isfinite(rel)) { status = AMG_ERR_NAN; break; }
     if (rel <= tol) { status = AMG_OK; break; }
     if (it >= h.p.max_iter) { status = AMG_ERR_NOT_CONVERGED; break; }
-    k_fg_start<<<ng, kThreads, 0, s>>>(n, h.r, h.V, L0.slots, S_RR, h.fg, m);
-    k_set_state<<<1, 32, 0, s>>>(h.it_dev, active, h.it_dev + 2, h.status_dev, -1, 1, 0, 0);
+    klaunch(k_fg_start, ng, kThreads, s, n, h.r, h.V, L0.slots, S_RR, h.fg, m);
+    klaunch(k_set_state, 1, 32, s, h.it_dev, active, h.it_dev + 2, h.status_dev, -1, 1, 0, 0);
     launches += 2;
     AMG_LAUNCH_CHECK();
     int jused = 0, dst = 0;
@@ -1194,20 +1552,20 @@ int run_fgmres_t(Hierarchy &h, const double *b, double *x, double tol, int32_t *
         a.x = zj;
         a.out = w;
         a.pred = active;
-        k_sell<double, double, E_Y><<<sell_grid(L0), kThreads, 0, s>>>(a);
+        klaunch(k_sell<double, double, E_Y>, sell_grid(L0), kThreads, s, a);
         eng.check();
       }
       for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
-        k_mdot<<<ng, kThreads, 0, s>>>(n, h.V, j + 1, w, h.gpart, active);
-        k_fin_mdot<<<1, 1024, 0, s>>>(h.gpart, ng, j + 1, h.H, m, j, h.hc, pass, active);
-        k_maxpy<<<ng, kThreads, 0, s>>>(n, h.V, j + 1, h.hc, w, active);
+        klaunch(k_mdot, ng, kThreads, s, n, h.V, j + 1, w, h.gpart, active);
+        klaunch(k_fin_mdot, 1, 1024, s, h.gpart, ng, j + 1, h.H, m, j, h.hc, pass, active);
+        klaunch(k_maxpy, ng, kThreads, s, n, h.V, j + 1, h.hc, w, active);
         eng.launches += 3;
         AMG_LAUNCH_CHECK();
       }
-      k_dot64<<<ng, kThreads, 0, s>>>(n, w, w, L0.partials + 6 * kRedBlocks, active);
-      k_fg_normalize<<<ng, kThreads, 0, s>>>(n, w, h.V + (size_t)(j + 1) * n, L0.partials + 6 * kRedBlocks, ng,
+      klaunch(k_dot64, ng, kThreads, s, n, w, w, L0.partials + 6 * kRedBlocks, active);
+      klaunch(k_fg_normalize, ng, kThreads, s, n, w, h.V + (size_t)(j + 1) * n, L0.partials + 6 * kRedBlocks, ng,
                                              h.H, m, j, active);
-      k_fg_givens<<<1, 32, 0, s>>>(h.H, m, j, m, h.fg, L0.slots, h.hist, h.it_dev, active, h.status_dev);
+      klaunch(k_fg_givens, 1, 32, s, h.H, m, j, m, h.fg, L0.slots, h.hist, h.it_dev, active, h.status_dev);
       eng.launches += 3;
       AMG_LAUNCH_CHECK();
       (void)before;
@@ -1218,8 +1576,8 @@ int run_fgmres_t(Hierarchy &h, const double *b, double *x, double tol, int32_t *
       jused = j + 1;
       if (dst != 0) break;
     }
-    k_fg_trisolve<<<1, 32, 0, s>>>(h.H, m, jused, m, h.fg);
-    k_fg_xupdate<<<ng, kThreads, 0, s>>>(n, h.x, h.Z, jused, h.fg + 3 * m + 1);
+    klaunch(k_fg_trisolve, 1, 32, s, h.H, m, jused, m, h.fg);
+    klaunch(k_fg_xupdate, ng, kThreads, s, n, h.x, h.Z, jused, h.fg + 3 * m + 1);
     launches += 2;
     AMG_LAUNCH_CHECK();
     if (dst == AMG_ERR_NAN) { status = AMG_ERR_NAN; break; }
@@ -1238,6 +1596,171 @@ int run_fgmres_t(Hierarchy &h, const double *b, double *x, double tol, int32_t *
   if (iters) *iters = it;
   if (res_hist) std::memcpy(res_hist, hist.data(), sizeof(double) * hist.size());
   return status;
+}
+
+__global__ void k_bset(int32_t nsys, const double *__restrict__ bslots, double tol, int *__restrict__ bact,
+                       int *__restrict__ bit) {
+  pdl_wait_and_trigger();
+  // bact[0..nsys) active, bact[nsys] count, bact[nsys+1 ..] restart flags; bit: iters, status
+  __shared__ int nact;
+  if (threadIdx.x == 0) nact = 0;
+  __syncthreads();
+  for (int32_t s = threadIdx.x; s < nsys; s += blockDim.x) {
+    const double rel = sqrt(bslots[(int64_t)S_RR * nsys + s] / bslots[(int64_t)S_NB2 * nsys + s]);
+    const int a = rel > tol ? 1 : 0;
+    bact[s] = a;
+    bact[nsys + 1 + s] = 1;
+    bit[s] = 0;
+    bit[nsys + s] = a ? kIterating : AMG_OK;
+    if (a) atomicAdd(&nact, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) bact[nsys] = nact;
+}
+
+// restart the systems whose updated residual met tol but whose true residual did not
+__global__ void k_brestart(int32_t nsys, const double *__restrict__ bslots, double tol, int max_iter,
+                           int *__restrict__ bact, int *__restrict__ bit) {
+  pdl_wait_and_trigger();
+  __shared__ int nact;
+  if (threadIdx.x == 0) nact = 0;
+  __syncthreads();
+  for (int32_t s = threadIdx.x; s < nsys; s += blockDim.x) {
+    const double rel = sqrt(bslots[(int64_t)S_TRUE_RR * nsys + s] / bslots[(int64_t)S_NB2 * nsys + s]);
+    int &st = bit[nsys + s];
+    if (st == kUpdatedConverged) st = rel <= tol ? AMG_OK : (bit[s] >= max_iter ? AMG_ERR_NOT_CONVERGED : kIterating);
+    if (st == kIterating) {
+      bact[s] = 1;
+      bact[nsys + 1 + s] = 1;
+      atomicAdd(&nact, 1);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) bact[nsys] = nact;
+}
+
+__global__ void k_fix_zero_norm(int32_t nsys, double *__restrict__ bslots) {
+  pdl_wait_and_trigger();
+  for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < nsys; s += gridDim.x * blockDim.x)
+    if (!(bslots[(int64_t)S_NB2 * nsys + s] > 0.0)) bslots[(int64_t)S_NB2 * nsys + s] = 1.0;
+}
+
+template <class MV, class VT>
+int run_solve_batch_t(Hierarchy &h, const double *b, double *x, double tol, int32_t *iters, double *relres,
+                      cudaStream_t s) {
+  Level &L0 = h.lev[0];
+  const int32_t n = L0.n, ns = h.nsys;
+  Engine<MV, VT> eng(h, s);
+  Engine<double, double> e64(h, s);
+  int64_t launches = 0;
+  copy_in(h.b, b, n, s);
+  copy_in(h.x, x, n, s);
+  e64.segdot(0, 1, h.b, h.b, nullptr, nullptr, nullptr, nullptr, S_NB2, nullptr);
+  klaunch(k_fix_zero_norm, grid_for(ns, kThreads, 152), kThreads, s, ns, L0.bslots);
+  klaunch(k_residual64, sell_grid(L0), kThreads, s, n, L0.nslices, (const int64_t *)L0.sptr,
+          (const int32_t *)L0.scol, (const double *)L0.sval64, (const double *)h.x, (const double *)h.b, h.r,
+          L0.partials + 7 * kRedBlocks);
+  e64.segdot(0, 1, h.r, h.r, nullptr, nullptr, nullptr, nullptr, S_RR, nullptr);
+  klaunch(k_bset, 1, 1024, s, ns, (const double *)L0.bslots, tol, h.bactive, h.bit);
+  AMG_CUDA(cudaMemsetAsync(h.it_dev, 0, sizeof(int), s));
+  launches += 3;
+  AMG_LAUNCH_CHECK();
+  // capture one iteration of all systems
+  if (h.graph_exec) {
+    cudaGraphExecDestroy(h.graph_exec);
+    cudaGraphDestroy(h.graph);
+    h.graph_exec = nullptr;
+  }
+  if (h.p.use_graph) {
+    AMG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    eng.fcg_iteration_batched(tol);
+    AMG_CUDA(cudaStreamEndCapture(s, &h.graph));
+    AMG_CUDA(cudaGraphInstantiate(&h.graph_exec, h.graph, 0));
+    h.graph_launches = eng.launches;
+    eng.launches = 0;
+    h.graph_kind = -1;  // not the single-system iteration
+  }
+  int *pin = reinterpret_cast<int *>(h.host_pinned + 32);
+  int rounds = 0;
+  for (;;) {
+    AMG_CUDA(cudaMemcpyAsync(pin, h.bactive + ns, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AMG_CUDA(cudaStreamSynchronize(s));
+    if (pin[0] > 0 && rounds < 100 * h.p.max_iter) {
+      if (h.p.use_graph) {
+        AMG_CUDA(cudaGraphLaunch(h.graph_exec, s));
+        launches += h.graph_launches;
+      } else {
+        eng.fcg_iteration_batched(tol);
+      }
+      ++rounds;
+      continue;
+    }
+    // every system stopped: check the true residuals, restart those that miss tol
+    klaunch(k_residual64, sell_grid(L0), kThreads, s, n, L0.nslices, (const int64_t *)L0.sptr,
+            (const int32_t *)L0.scol, (const double *)L0.sval64, (const double *)h.x, (const double *)h.b, h.r,
+            L0.partials + 7 * kRedBlocks);
+    e64.segdot(0, 1, h.r, h.r, nullptr, nullptr, nullptr, nullptr, S_TRUE_RR, nullptr);
+    klaunch(k_brestart, 1, 1024, s, ns, (const double *)L0.bslots, tol, h.p.max_iter, h.bactive, h.bit);
+    launches += 2;
+    AMG_CUDA(cudaMemcpyAsync(pin, h.bactive + ns, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AMG_CUDA(cudaStreamSynchronize(s));
+    if (pin[0] == 0 || rounds >= 100 * h.p.max_iter) break;
+  }
+  launches += eng.launches + e64.launches;
+  std::vector<int> bit(2 * ns);
+  std::vector<double> sl((size_t)kNumSlots * ns);
+  AMG_CUDA(cudaMemcpyAsync(bit.data(), h.bit, sizeof(int) * 2 * ns, cudaMemcpyDeviceToHost, s));
+  AMG_CUDA(cudaMemcpyAsync(sl.data(), L0.bslots, sizeof(double) * kNumSlots * ns, cudaMemcpyDeviceToHost, s));
+  copy_out(x, h.x, n, s);
+  AMG_CUDA(cudaStreamSynchronize(s));
+  int status = AMG_OK, maxit = 0;
+  double worst = 0.0;
+  for (int32_t q = 0; q < ns; ++q) {
+    const double rel = std::sqrt(sl[(size_t)S_TRUE_RR * ns + q] / sl[(size_t)S_NB2 * ns + q]);
+    if (iters) iters[q] = bit[q];
+    if (relres) relres[q] = rel;
+    maxit = std::max(maxit, bit[q]);
+    worst = std::max(worst, rel);
+    const int st = bit[ns + q];
+    if (st != AMG_OK && status == AMG_OK) status = st < 0 ? st : AMG_ERR_NOT_CONVERGED;
+  }
+  h.info.iters = maxit;
+  h.info.final_relres = worst;
+  h.info.status = status;
+  h.info.kernel_launches = launches;
+  return status;
+}
+
+// per-level system map, row tiles and per-system scalars of a batch
+void prepare_batched(Hierarchy &h, cudaStream_t s) {
+  const int32_t ns = h.nsys;
+  constexpr int32_t kTile = 2048;
+  for (int k = 0; k < h.L; ++k) {
+    Level &L = h.lev[k];
+    L.sys_of = h.arena.get<int32_t>((size_t)L.n + 1);
+    klaunch(k_sys_of, ew_grid(L.n), kThreads, s, L.n, ns, (const int32_t *)L.sys_off, L.sys_of);
+    std::vector<int32_t> trow, stile(ns + 1, 0);
+    for (int32_t q = 0; q < ns; ++q) {
+      stile[q] = (int32_t)trow.size();
+      for (int32_t r = L.sys_off_host[q]; r < L.sys_off_host[q + 1]; r += kTile) trow.push_back(r);
+    }
+    stile[ns] = (int32_t)trow.size();
+    L.ntiles = (int32_t)trow.size();
+    trow.push_back(L.n);
+    L.tile_row = h.arena.get<int32_t>(trow.size());
+    L.sys_tile = h.arena.get<int32_t>(ns + 1);
+    L.tpart = h.arena.get<double>(3 * (size_t)L.ntiles + 1);
+    L.bslots = h.arena.get<double>((size_t)kNumSlots * ns);
+    L.bflag = h.arena.get<int>((size_t)ns + 1);
+    AMG_CUDA(cudaMemcpyAsync(L.tile_row, trow.data(), sizeof(int32_t) * trow.size(), cudaMemcpyHostToDevice, s));
+    AMG_CUDA(cudaMemcpyAsync(L.sys_tile, stile.data(), sizeof(int32_t) * (ns + 1), cudaMemcpyHostToDevice, s));
+    AMG_CUDA(cudaMemsetAsync(L.bslots, 0, sizeof(double) * kNumSlots * ns, s));
+    AMG_CUDA(cudaMemsetAsync(L.bflag, 0, sizeof(int) * (ns + 1), s));
+    AMG_CUDA(cudaStreamSynchronize(s));  // trow / stile leave scope
+  }
+  h.bit = h.arena.get<int>(2 * (size_t)ns);
+  h.bactive = h.arena.get<int>(2 * (size_t)ns + 2);
+  AMG_LAUNCH_CHECK();
 }
 
 template <class MV, class VT>
@@ -1278,7 +1801,7 @@ void set_poly(Hierarchy &h, int level, const double *coef, cudaStream_t s) {
     AMG_CUDA(cudaMemcpyAsync(L.poly, tmp.p, sizeof(double) * cnt, cudaMemcpyDeviceToDevice, s));
   } else {
     if (!L.poly) L.poly = h.arena.get<float>(cnt);
-    k_copy_cast<float><<<ew_grid((int64_t)cnt), kThreads, 0, s>>>((int32_t)cnt, tmp.p, (float *)L.poly);
+    klaunch(k_copy_cast<float>, ew_grid((int64_t)cnt), kThreads, s, (int32_t)cnt, tmp.p, (float *)L.poly);
     AMG_LAUNCH_CHECK();
   }
   AMG_CUDA(cudaStreamSynchronize(s));
@@ -1295,6 +1818,13 @@ void make_row_data(Hierarchy &h, Level &L, const double *diag, cudaStream_t s) {
 
 void prepare_solve(Hierarchy &h, cudaStream_t s) {
   AMG_DISPATCH(h.p.precision, (prepare_t<MV, VT>(h, s)));
+}
+
+int run_solve_batch(Hierarchy &h, const double *b, double *x, double tol, int32_t *iters, double *relres,
+                    cudaStream_t s) {
+  int rc = 0;
+  AMG_DISPATCH(h.p.precision, (rc = run_solve_batch_t<MV, VT>(h, b, x, tol, iters, relres, s)));
+  return rc;
 }
 
 int run_solve(Hierarchy &h, const double *b, double *x, double tol, int32_t *iters, double *res_hist,

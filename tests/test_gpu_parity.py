@@ -212,6 +212,17 @@ def test_cluster_tail_matches_kernel_per_step(gpu, name, prec):
     assert i1["final_relres"] <= 1e-8 and i1["kernel_launches"] < i0["kernel_launches"]
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_programmatic_dependent_launch_changes_nothing(gpu, prec):
+    """Launching with programmatic dependent launch only changes scheduling:
+    the solution is bit-identical."""
+    A, alpha, seed = case("varcoef3d_24")
+    b = P.rhs_uniform(A.n, 20)
+    xa, ia = gpu.Hierarchy(A, alpha=alpha, seed=seed, precision=prec, pdl=1).solve(b, tol=1e-8)
+    xb, ib = gpu.Hierarchy(A, alpha=alpha, seed=seed, precision=prec, pdl=0).solve(b, tol=1e-8)
+    assert ia["iters"] == ib["iters"] and np.array_equal(xa, xb)
+
+
 def test_single_level_one_iteration(gpu):
     A = P.poisson2d(7)
     g = gpu.Hierarchy(A, coarse_max=64)
@@ -236,6 +247,11 @@ def test_bad_inputs_rejected(gpu):
     nanv.val[5] = np.nan
     with pytest.raises(gpu.AMGError):
         gpu.Hierarchy(nanv)
+    g = gpu.Hierarchy(A)
+    xh, yh = np.ones(A.n), np.zeros(A.n)
+    with pytest.raises(gpu.AMGError) as e:  # amg_spmv takes device pointers only
+        gpu.amg_spmv(g.h, 0, xh, yh)
+    assert e.value.code == gpu.AMG_ERR_BAD_INPUT and "device" in gpu.amg_last_error()
 
 
 def test_not_converged_and_zero_rhs(gpu):
