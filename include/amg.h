@@ -81,8 +81,9 @@ typedef struct amg_params {
   int32_t use_graph;     /* 1: replay one outer iteration as a captured CUDA graph          */
   int32_t smoother;      /* 0: damped Jacobi; 1: per-row polynomial smoother whose
                             coefficients are set with amg_set_poly                         */
-  int32_t tail;          /* 1: run the coarse levels (at most 4096 rows, below the
-                            K-cycle levels) in one thread-block-cluster launch per visit   */
+  int32_t tail;          /* run the coarse levels (at most 4096 rows, below the K-cycle
+                            levels) in one launch per visit: 1 = a cluster of 8 blocks,
+                            2 = a single block; 0 = one kernel per step                    */
   int32_t pdl;           /* 1: launch solve kernels with programmatic dependent launch     */
 } amg_params;
 
@@ -163,7 +164,9 @@ int amg_precond(amg_hierarchy *h, const double *b, double *x, void *stream);
 /* y = A_k x on level k with the solve-phase matrix (in the hierarchy's
  * precision).  x, y: n_k elements of the vector type of the precision (double
  * for F64, float otherwise), DEVICE pointers (host pointers: AMG_ERR_BAD_INPUT).
- * Asynchronous on `stream`. */
+ * Asynchronous: the kernel is launched on `stream` itself when it is not the
+ * legacy default stream (so that calls can be captured into a CUDA graph),
+ * else on the hierarchy's internal stream, ordered after the caller's work. */
 int amg_spmv(amg_hierarchy *h, int32_t level, const void *x, void *y, void *stream);
 
 /* Per-row polynomial smoother coefficients of level k (n_k x 3, row major,

@@ -4,7 +4,8 @@
 //   setup CSR   rp[n+1] int32, ci[nnz] int32, val[nnz] f64   (bit-exact level matrix)
 //   solve SELL  slices of 32 rows, column-major inside a slice: entry e of row
 //               32*s + l sits at sptr[s] + 32*e + l; padding has col = own row,
-//               value 0.  Values in the preconditioner precision (f64/f32/bf16).
+//               value 0.  Values in the preconditioner precision (f64/f32/bf16);
+//               in f32/bf16 the diagonal is split off into sdiag[n] f32.
 //   agg[n]      coarse id of every node;  pw[n] the nonzero of row i of P_k
 //   aptr[nc+1], amem[n]   members of every aggregate in ascending fine index
 //   wd[n]       omega / A_ii  (damped Jacobi, Eq. damped Jacobi)
@@ -121,14 +122,22 @@ struct Level {
   // transfer
   int32_t *agg = nullptr, *aptr = nullptr, *amem = nullptr;
   double *pw64 = nullptr;  // P weights in FP64 (exported)
-  // solve-phase matrix (SELL-32)
+  // solve-phase matrix (SELL-32).  FP64: every entry of A.  FP32 / BF16: the
+  // off-diagonal entries only, rounded, with the diagonal in sdiag (FP32) as
+  // a_ii plus the rounding errors of the row's off-diagonals, so that row sums
+  // stay exact and the rounded matrix stays spectrally equivalent to A.
   int32_t nslices = 0;
   int64_t sell_entries = 0;
   int64_t *sptr = nullptr;
   int32_t *scol = nullptr;
   void *sval = nullptr;
-  double *sval64 = nullptr;   // level 0 only: FP64 values for the outer Krylov when
-                              // the preconditioner runs in reduced precision
+  float *sdiag = nullptr;
+  // level 0 only: every entry in FP64 for the outer Krylov method and the true
+  // residual (the same arrays as sptr / scol / sval in FP64 mode)
+  int64_t *sptr64 = nullptr;
+  int32_t *scol64 = nullptr;
+  double *sval64 = nullptr;
+  int64_t sell64_entries = 0;
   // solve-phase vectors and per-row data in the vector type
   void *wd = nullptr, *dinv = nullptr, *pw = nullptr, *poly = nullptr;
   void *r = nullptr, *bc = nullptr, *xc = nullptr, *c = nullptr, *v = nullptr, *rt = nullptr,
@@ -154,6 +163,7 @@ struct TailLevel {
   const int64_t *sptr;
   const int32_t *scol;
   const void *sval;
+  const float *sdiag;  // split diagonal of a reduced-precision level (else null)
   const void *wd, *pw;
   const int32_t *agg, *aptr, *amem;
   void *bc, *xc, *r, *c, *v, *rt, *d, *w;
@@ -248,7 +258,7 @@ int32_t fixed_scratch_max_rows();
 
 // tail.cu
 template <class MV, class VT>
-void tail_launch(const TailArgs &a, cudaStream_t s);
+void tail_launch(const TailArgs &a, int blocks, cudaStream_t s);
 // Largest first level of the cluster tail.  Eight SMs of a cluster run a level
 // of ~1.5k rows in a few microseconds per phase, where one full-GPU kernel per
 // step is bound by launch latency; a 17k-row level is faster on all 152 SMs.

@@ -95,7 +95,8 @@ int check_params(const amg_params *p) {
   if (!p) return AMG_ERR_BAD_INPUT;
   if (!(p->alpha >= 0.0 && p->alpha < 1.0) || p->coarse_max < 1 || p->max_levels < 1 || p->kcycle_levels < 0 ||
       p->precision < 0 || p->precision > 2 || p->outer < 0 || p->outer > 1 || p->max_iter < 1 ||
-      p->restart < 1 || p->omega_mode < 0 || p->omega_mode > 1 || p->smoother < 0 || p->smoother > 1) {
+      p->restart < 1 || p->omega_mode < 0 || p->omega_mode > 1 || p->smoother < 0 || p->smoother > 1 ||
+      p->tail < 0 || p->tail > 2) {
     amg::set_last_error("invalid amg_params");
     return AMG_ERR_BAD_INPUT;
   }
@@ -292,7 +293,13 @@ int amg_spmv(amg_hierarchy *H, int32_t level, const void *x, void *y, void *stre
     return AMG_ERR_BAD_INPUT;
   }
   return guarded([&]() {
-    enter(H, stream);
+    if (stream) {  // no allocation: launch straight on the caller's stream (graph-capturable)
+      amg::current_stream() = (cudaStream_t)stream;
+      amg::pdl_enabled() = H->h.p.pdl != 0;
+      amg::run_spmv(H->h, level, x, y, (cudaStream_t)stream);
+      return AMG_OK;
+    }
+    enter(H, stream);  // legacy default stream: run on the hierarchy's stream
     amg::run_spmv(H->h, level, x, y, H->stream);
     leave(H, stream);
     return AMG_OK;
@@ -456,6 +463,12 @@ int amg_validate_hierarchy(const amg_hierarchy *H) {
       expect(sp[0] == 0 && sp[L.nslices] == L.sell_entries, k, "SELL pointer ends");
       for (int32_t q = 0; q < L.nslices; ++q) expect(sp[q] <= sp[q + 1] && (sp[q + 1] - sp[q]) % 32 == 0, k, "SELL slice");
       for (int32_t c : sc) expect(c >= 0 && c < L.n, k, "SELL column out of range");
+      if (k == 0 && L.sptr64 != L.sptr) {
+        auto sp64 = fetch(L.sptr64, (size_t)L.nslices + 1);
+        auto sc64 = fetch(L.scol64, (size_t)L.sell64_entries);
+        expect(sp64[0] == 0 && sp64[L.nslices] == L.sell64_entries, k, "FP64 SELL pointer ends");
+        for (int32_t c : sc64) expect(c >= 0 && c < L.n, k, "FP64 SELL column out of range");
+      }
       if (!last) {
         auto agg = fetch(L.agg, (size_t)L.n);
         auto ap = fetch(L.aptr, (size_t)L.nc + 1);

@@ -546,13 +546,16 @@ __global__ void k_diag(int32_t n, const int32_t *__restrict__ rp, const int32_t 
 }
 
 // SELL-32: width of every slice = longest row in it
+// width of each slice = its longest row (off-diagonal entries only when split)
 __global__ void k_slice_width(int32_t n, int32_t nslices, const int32_t *__restrict__ rp,
-                              int64_t *__restrict__ width32) {
+                              const int32_t *__restrict__ ci, bool split, int64_t *__restrict__ width32) {
   const int lane = threadIdx.x & 31;
   const int32_t sl = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (sl >= nslices) return;
   const int32_t row = sl * kSlice + lane;
-  int32_t len = row < n ? rp[row + 1] - rp[row] : 0;
+  int32_t len = 0;
+  if (row < n)
+    for (int32_t p = rp[row]; p < rp[row + 1]; ++p) len += (split && ci[p] == row) ? 0 : 1;
   len = __reduce_max_sync(0xffffffffu, len);
   if (lane == 0) width32[sl] = (int64_t)len * kSlice;
 }
@@ -565,29 +568,51 @@ template <> __device__ __forceinline__ __nv_bfloat16 conv_val<__nv_bfloat16>(dou
   return __double2bfloat16(v);
 }
 
+template <class MV> __device__ __forceinline__ double back_to_double(MV v);
+template <> __device__ __forceinline__ double back_to_double<double>(double v) { return v; }
+template <> __device__ __forceinline__ double back_to_double<float>(float v) { return (double)v; }
+template <> __device__ __forceinline__ double back_to_double<__nv_bfloat16>(__nv_bfloat16 v) {
+  return (double)__bfloat162float(v);
+}
+
+// CSR -> SELL-32 (column-major within a slice; padding: own row, value 0).
+// split: skip the diagonal entry and store sdiag[i] = a_ii + sum_j (a_ij - fl(a_ij))
+// over the row's off-diagonals, in FP64 then rounded once to FP32.
 template <class MV>
 __global__ void k_build_sell(int32_t n, int32_t nslices, const int32_t *__restrict__ rp,
-                            const int32_t *__restrict__ ci, const double *__restrict__ val,
-                            const int64_t *__restrict__ sptr, int32_t *__restrict__ scol, MV *__restrict__ sval) {
+                             const int32_t *__restrict__ ci, const double *__restrict__ val,
+                             const int64_t *__restrict__ sptr, int32_t *__restrict__ scol, MV *__restrict__ sval,
+                             float *__restrict__ sdiag) {
   const int lane = threadIdx.x & 31;
   const int32_t sl = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (sl >= nslices) return;
   const int32_t row = sl * kSlice + lane;
   const int64_t base = sptr[sl];
   const int32_t width = (int32_t)((sptr[sl + 1] - base) / kSlice);
-  const int32_t p0 = row < n ? rp[row] : 0;
-  const int32_t len = row < n ? rp[row + 1] - p0 : 0;
   const int32_t pad_col = row < n ? row : n - 1;
-  for (int32_t e = 0; e < width; ++e) {
-    const int64_t at = base + (int64_t)e * kSlice + lane;
-    if (e < len) {
-      scol[at] = ci[p0 + e];
-      sval[at] = conv_val<MV>(val[p0 + e]);
-    } else {
-      scol[at] = pad_col;
-      sval[at] = conv_val<MV>(0.0);
+  int32_t e = 0;
+  double dii = 0.0, comp = 0.0;
+  if (row < n)
+    for (int32_t p = rp[row]; p < rp[row + 1]; ++p) {
+      const int32_t c = ci[p];
+      const double v = val[p];
+      if (sdiag && c == row) {
+        dii = v;
+        continue;
+      }
+      const MV m = conv_val<MV>(v);
+      const int64_t at = base + (int64_t)e * kSlice + lane;
+      scol[at] = c;
+      sval[at] = m;
+      if (sdiag) comp = __dadd_rn(comp, __dadd_rn(v, -back_to_double<MV>(m)));
+      ++e;
     }
+  for (; e < width; ++e) {
+    const int64_t at = base + (int64_t)e * kSlice + lane;
+    scol[at] = pad_col;
+    sval[at] = conv_val<MV>(0.0);
   }
+  if (sdiag && row < n) sdiag[row] = __double2float_rn(__dadd_rn(dii, comp));
 }
 
 // ============================================================== Arnoldi omega
@@ -961,39 +986,53 @@ Coarsening coarsen_level(Hierarchy &h, int k, cudaStream_t s, int32_t *agg_out, 
   return out;
 }
 
+// SELL-32 of level L: the preconditioner's matrix in its precision and, on
+// level 0, every entry in FP64 for the outer iteration
 void build_solve_matrix(Hierarchy &h, Level &L, cudaStream_t s) {
   const int32_t n = L.n;
   L.nslices = (n + kSlice - 1) / kSlice;
-  DevBuf<int64_t> w32(L.nslices + 1);
-  AMG_COUNT(), k_slice_width<<<blocks_for((int64_t)L.nslices * 32), 256, 0, s>>>(n, L.nslices, L.rp, w32.p);
-  AMG_LAUNCH_CHECK();
-  L.sptr = h.arena.get<int64_t>(L.nslices + 1);
-  int64_t entries = 0;
-  exclusive_scan<int64_t, int64_t>(w32.p, L.sptr, L.nslices, s, &entries);
-  L.sell_entries = entries;
-  L.scol = h.arena.get<int32_t>(entries);
   const unsigned g = blocks_for((int64_t)L.nslices * 32);
+  auto layout = [&](bool split, int64_t *&sptr, int32_t *&scol, int64_t &entries) {
+    DevBuf<int64_t> w32(L.nslices + 1);
+    AMG_COUNT(), k_slice_width<<<g, 256, 0, s>>>(n, L.nslices, L.rp, L.ci, split, w32.p);
+    AMG_LAUNCH_CHECK();
+    sptr = h.arena.get<int64_t>(L.nslices + 1);
+    exclusive_scan<int64_t, int64_t>(w32.p, sptr, L.nslices, s, &entries);
+    scol = h.arena.get<int32_t>(entries);
+  };
+  const bool split = h.p.precision != AMG_PREC_F64;
+  layout(split, L.sptr, L.scol, L.sell_entries);
+  const int64_t entries = L.sell_entries;
+  if (split) L.sdiag = h.arena.get<float>(n);
   switch (h.p.precision) {
     case AMG_PREC_F64:
       L.sval = h.arena.get<double>(entries);
-      AMG_COUNT(), k_build_sell<double><<<g, 256, 0, s>>>(n, L.nslices, L.rp, L.ci, L.val, L.sptr, L.scol, (double *)L.sval);
+      AMG_COUNT(), k_build_sell<double><<<g, 256, 0, s>>>(n, L.nslices, L.rp, L.ci, L.val, L.sptr, L.scol,
+                                                          (double *)L.sval, nullptr);
       break;
     case AMG_PREC_F32:
       L.sval = h.arena.get<float>(entries);
-      AMG_COUNT(), k_build_sell<float><<<g, 256, 0, s>>>(n, L.nslices, L.rp, L.ci, L.val, L.sptr, L.scol, (float *)L.sval);
+      AMG_COUNT(), k_build_sell<float><<<g, 256, 0, s>>>(n, L.nslices, L.rp, L.ci, L.val, L.sptr, L.scol,
+                                                         (float *)L.sval, L.sdiag);
       break;
     default:
       L.sval = h.arena.get<__nv_bfloat16>(entries);
       AMG_COUNT(), k_build_sell<__nv_bfloat16><<<g, 256, 0, s>>>(n, L.nslices, L.rp, L.ci, L.val, L.sptr, L.scol,
-                                                   (__nv_bfloat16 *)L.sval);
+                                                                 (__nv_bfloat16 *)L.sval, L.sdiag);
   }
   AMG_LAUNCH_CHECK();
-  if (&L == &h.lev[0] && h.p.precision != AMG_PREC_F64) {
-    L.sval64 = h.arena.get<double>(entries);
-    AMG_COUNT(), k_build_sell<double><<<g, 256, 0, s>>>(n, L.nslices, L.rp, L.ci, L.val, L.sptr, L.scol, L.sval64);
+  if (&L != &h.lev[0]) return;
+  if (split) {
+    layout(false, L.sptr64, L.scol64, L.sell64_entries);
+    L.sval64 = h.arena.get<double>(L.sell64_entries);
+    AMG_COUNT(), k_build_sell<double><<<g, 256, 0, s>>>(n, L.nslices, L.rp, L.ci, L.val, L.sptr64, L.scol64,
+                                                        L.sval64, nullptr);
     AMG_LAUNCH_CHECK();
-  } else if (&L == &h.lev[0]) {
+  } else {
+    L.sptr64 = L.sptr;
+    L.scol64 = L.scol;
     L.sval64 = (double *)L.sval;
+    L.sell64_entries = L.sell_entries;
   }
 }
 

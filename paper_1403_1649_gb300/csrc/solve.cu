@@ -35,6 +35,7 @@ struct SellArgs {
   const int64_t *sptr;
   const int32_t *scol;
   const void *sval;
+  const float *sdiag;  // split diagonal (reduced precision), else null
   const VT *x;    // SpMV input
   VT *out;        // output vector
   const VT *rhs;  // right-hand side (residual / smoothing epilogues)
@@ -139,6 +140,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_sell(SellArgs<VT> a) {
     }
     const int32_t row = sl * 32 + lane;
     if (row < a.n) {
+      if (a.sdiag) y += (VT)a.sdiag[row] * a.x[row];
       VT o;
       if (EPI == E_Y) o = y;
       else if (EPI == E_RESID) o = a.rhs[row] - y;
@@ -914,6 +916,7 @@ struct Engine {
     a.sptr = L.sptr;
     a.scol = L.scol;
     a.sval = L.sval;
+    a.sdiag = L.sdiag;
     a.x = x;
     a.out = out;
     a.pred = pred;
@@ -981,7 +984,7 @@ struct Engine {
       ta.Ainv = h.coarse_inv;
       ta.lev = h.tail_dev;
       ta.pred = pred;
-      tail_launch<MV, VT>(ta, s);
+      tail_launch<MV, VT>(ta, h.p.tail == 2 ? 1 : 8, s);
       ++launches;
     } else if (coarse_is_last) {
       cycle(k + 1, V(C.bc), V(C.xc), true, pred);  // exact coarse solve
@@ -1167,8 +1170,8 @@ struct Engine {
       SellArgs<double> a{};
       a.n = n;
       a.nslices = L0.nslices;
-      a.sptr = L0.sptr;
-      a.scol = L0.scol;
+      a.sptr = L0.sptr64;
+      a.scol = L0.scol64;
       a.sval = L0.sval64;
       a.x = h.pdir;
       a.out = h.q;
@@ -1204,8 +1207,8 @@ struct Engine {
       SellArgs<double> a{};
       a.n = L0.n;
       a.nslices = L0.nslices;
-      a.sptr = L0.sptr;
-      a.scol = L0.scol;
+      a.sptr = L0.sptr64;
+      a.scol = L0.scol64;
       a.sval = L0.sval64;
       a.x = h.pdir;
       a.out = h.q;
@@ -1282,6 +1285,7 @@ void configure_tail(Hierarchy &h, cudaStream_t s) {
     T.sptr = L.sptr;
     T.scol = L.scol;
     T.sval = L.sval;
+    T.sdiag = L.sdiag;
     T.wd = L.wd;
     T.pw = L.pw;
     T.agg = L.agg;
@@ -1373,7 +1377,7 @@ void copy_out(double *dst, const double *src_dev, int32_t n, cudaStream_t s) {
 void true_residual(Hierarchy &h, int dst, cudaStream_t s, int64_t &launches) {
   Level &L0 = h.lev[0];
   const int nsg = sell_grid(L0);
-  klaunch(k_residual64, nsg, kThreads, s, L0.n, L0.nslices, L0.sptr, L0.scol, L0.sval64, h.x, h.b, h.r,
+  klaunch(k_residual64, nsg, kThreads, s, L0.n, L0.nslices, L0.sptr64, L0.scol64, L0.sval64, h.x, h.b, h.r,
                                         L0.partials + 7 * kRedBlocks);
   klaunch(k_store_sum, 1, kThreads, s, L0.partials + 7 * kRedBlocks, nsg, L0.slots + dst);
   launches += 2;
@@ -1546,8 +1550,8 @@ int run_fgmres_t(Hierarchy &h, const double *b, double *x, double tol, int32_t *
         SellArgs<double> a{};
         a.n = n;
         a.nslices = L0.nslices;
-        a.sptr = L0.sptr;
-        a.scol = L0.scol;
+        a.sptr = L0.sptr64;
+        a.scol = L0.scol64;
         a.sval = L0.sval64;
         a.x = zj;
         a.out = w;
@@ -1657,8 +1661,8 @@ int run_solve_batch_t(Hierarchy &h, const double *b, double *x, double tol, int3
   copy_in(h.x, x, n, s);
   e64.segdot(0, 1, h.b, h.b, nullptr, nullptr, nullptr, nullptr, S_NB2, nullptr);
   klaunch(k_fix_zero_norm, grid_for(ns, kThreads, 152), kThreads, s, ns, L0.bslots);
-  klaunch(k_residual64, sell_grid(L0), kThreads, s, n, L0.nslices, (const int64_t *)L0.sptr,
-          (const int32_t *)L0.scol, (const double *)L0.sval64, (const double *)h.x, (const double *)h.b, h.r,
+  klaunch(k_residual64, sell_grid(L0), kThreads, s, n, L0.nslices, (const int64_t *)L0.sptr64,
+          (const int32_t *)L0.scol64, (const double *)L0.sval64, (const double *)h.x, (const double *)h.b, h.r,
           L0.partials + 7 * kRedBlocks);
   e64.segdot(0, 1, h.r, h.r, nullptr, nullptr, nullptr, nullptr, S_RR, nullptr);
   klaunch(k_bset, 1, 1024, s, ns, (const double *)L0.bslots, tol, h.bactive, h.bit);
@@ -1696,8 +1700,8 @@ int run_solve_batch_t(Hierarchy &h, const double *b, double *x, double tol, int3
       continue;
     }
     // every system stopped: check the true residuals, restart those that miss tol
-    klaunch(k_residual64, sell_grid(L0), kThreads, s, n, L0.nslices, (const int64_t *)L0.sptr,
-            (const int32_t *)L0.scol, (const double *)L0.sval64, (const double *)h.x, (const double *)h.b, h.r,
+    klaunch(k_residual64, sell_grid(L0), kThreads, s, n, L0.nslices, (const int64_t *)L0.sptr64,
+            (const int32_t *)L0.scol64, (const double *)L0.sval64, (const double *)h.x, (const double *)h.b, h.r,
             L0.partials + 7 * kRedBlocks);
     e64.segdot(0, 1, h.r, h.r, nullptr, nullptr, nullptr, nullptr, S_TRUE_RR, nullptr);
     klaunch(k_brestart, 1, 1024, s, ns, (const double *)L0.bslots, tol, h.p.max_iter, h.bactive, h.bit);

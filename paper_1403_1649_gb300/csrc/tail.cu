@@ -5,7 +5,8 @@
 // This kernel runs, for levels t..L-1, either one V-cycle (Alg. 4) or the whole
 // Krylov-accelerated coarse part of Alg. 5 at level t (two V-cycles, the inner
 // products, the test ||r~|| <= t ||r|| and the combination) inside a single
-// cluster of kTailCluster blocks.  Phases are separated by cluster barriers;
+// cluster of CL blocks (CL = 8, or CL = 1: one block, which needs no co-scheduled
+// SMs).  Phases are separated by cluster barriers;
 // inner products are reduced through distributed shared memory in a fixed rank
 // order, so every block computes the same value and takes the same branch.
 // Vectors written inside the kernel are read with ld.global.cg (L2), never
@@ -18,7 +19,6 @@ namespace cg = cooperative_groups;
 
 namespace amg {
 
-constexpr int kTailCluster = 8;
 constexpr int kTailThreads = 1024;
 constexpr int kTailWarps = kTailThreads / 32;
 
@@ -29,7 +29,7 @@ __device__ __forceinline__ double to_vt(double v, double) { return v; }
 
 struct TailCtx {
   cg::cluster_group cl;
-  int rank, gtid, gsize, gwarp, nwarps, lane;
+  int nblocks, rank, gtid, gsize, gwarp, nwarps, lane;
   int buf;
 };
 
@@ -63,7 +63,7 @@ __device__ void cluster_sum(TailCtx &c, double v0, double v1, double v2, double 
   }
   c.cl.sync();
   out[0] = out[1] = out[2] = 0.0;
-  for (int r = 0; r < kTailCluster; ++r) {
+  for (int r = 0; r < c.nblocks; ++r) {
     const double *peer = c.cl.map_shared_rank(&s_red[c.buf][0], r);
     out[0] += peer[0];
     out[1] += peer[1];
@@ -93,6 +93,8 @@ __device__ __forceinline__ VT sell_row(const TailLevel &L, int32_t sl, int lane,
     for (int q = 0; q < 4; ++q)
       if (e + q < width) y += to_vt(vv[q], VT(0)) * xf(cc[q]);
   }
+  const int32_t row = sl * 32 + lane;
+  if (L.sdiag && row < L.n) y += (VT)L.sdiag[row] * xf(row);
   return y;
 }
 
@@ -158,13 +160,14 @@ __device__ void tail_vcycle(TailCtx &c, const TailArgs &a, const VT *rhs_t, VT *
   }
 }
 
-template <class MV, class VT>
-__global__ void __cluster_dims__(kTailCluster, 1, 1) __launch_bounds__(kTailThreads, 1) k_tail(TailArgs a) {
+template <class MV, class VT, int CL>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kTailThreads, 1) k_tail(TailArgs a) {
   if (a.pred && *a.pred == 0) return;  // uniform: every block reads the same flag
   TailCtx c{cg::this_cluster()};
+  c.nblocks = CL;
   c.rank = (int)c.cl.block_rank();
   c.gtid = c.rank * kTailThreads + threadIdx.x;
-  c.gsize = kTailCluster * kTailThreads;
+  c.gsize = CL * kTailThreads;
   c.lane = threadIdx.x & 31;
   c.gwarp = c.gtid >> 5;
   c.nwarps = c.gsize >> 5;
@@ -246,13 +249,16 @@ __global__ void __cluster_dims__(kTailCluster, 1, 1) __launch_bounds__(kTailThre
 }
 
 template <class MV, class VT>
-void tail_launch(const TailArgs &a, cudaStream_t s) {
-  k_tail<MV, VT><<<kTailCluster, kTailThreads, 0, s>>>(a);
+void tail_launch(const TailArgs &a, int blocks, cudaStream_t s) {
+  if (blocks == 1)
+    k_tail<MV, VT, 1><<<1, kTailThreads, 0, s>>>(a);
+  else
+    k_tail<MV, VT, 8><<<8, kTailThreads, 0, s>>>(a);
   AMG_LAUNCH_CHECK();
 }
 
-template void tail_launch<double, double>(const TailArgs &, cudaStream_t);
-template void tail_launch<float, float>(const TailArgs &, cudaStream_t);
-template void tail_launch<__nv_bfloat16, float>(const TailArgs &, cudaStream_t);
+template void tail_launch<double, double>(const TailArgs &, int, cudaStream_t);
+template void tail_launch<float, float>(const TailArgs &, int, cudaStream_t);
+template void tail_launch<__nv_bfloat16, float>(const TailArgs &, int, cudaStream_t);
 
 }  // namespace amg

@@ -195,13 +195,15 @@ def test_polynomial_smoother_reduces_to_jacobi(gpu, orc):
     assert np.allclose(g.precond(b), z_j, rtol=1e-12, atol=1e-14 * np.abs(z_j).max())
 
 
+@pytest.mark.parametrize("tail", [1, 2])
 @pytest.mark.parametrize("name,prec", [("varcoef3d_24", 0), ("poisson2d_64", 0), ("fem2d_48", 1)])
-def test_cluster_tail_matches_kernel_per_step(gpu, name, prec):
-    """The coarse levels run as one cluster launch or as one kernel per step:
-    same preconditioner up to rounding, same iterations."""
+def test_cluster_tail_matches_kernel_per_step(gpu, name, prec, tail):
+    """The coarse levels run as one launch (a cluster of 8 blocks, or a single
+    block) or as one kernel per step: same preconditioner up to rounding, same
+    iterations."""
     A, alpha, seed = case(name)
     b = P.rhs_uniform(A.n, 19)
-    g1 = gpu.Hierarchy(A, alpha=alpha, seed=seed, precision=prec, tail=1)
+    g1 = gpu.Hierarchy(A, alpha=alpha, seed=seed, precision=prec, tail=tail)
     g0 = gpu.Hierarchy(A, alpha=alpha, seed=seed, precision=prec, tail=0)
     z1, z0 = g1.precond(b), g0.precond(b)
     tol = 1e-12 if prec == 0 else 1e-5
