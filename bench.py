@@ -95,25 +95,10 @@ def other_workload(args):
             return i
         return go, info
 
-    if args.workload == "varcoef3d_160":
-        A = P.varcoef3d(160, 2)
-        b = P.rhs_uniform(A.n, 2)
-        res = {}
-        for prec in ("bf16", "f64"):
-            go, _ = run_single(A, b, alpha=0.5, seed=2, outer=1, restart=30, precision=PREC[prec], max_iter=2000)
-            t, i = timed(go, reps)
-            res[prec] = {"ms": t, "setup_ms": i["setup_ms"], "solve_ms": i["solve_ms"], "iters": i["iters"],
-                         "final_relres": i["final_relres"]}
-        line.update(value=A.n / (res["bf16"]["ms"] / 1e3), ms_per_step=res["bf16"]["ms"], dtype="bf16+f32+f64",
-                    config={"workload": "3D finite-volume -div(k grad u) 160^3 (n=4,096,000), k log-uniform "
-                                        "[1e-3,1e3] on 8^3 blocks, z x100 on x<80; FGMRES(30), K-cycle (GMRES "
-                                        "variant), BF16 matrix values / FP32 vectors vs FP64, to 1e-8"},
-                    compare=res)
-    elif args.workload == "fem2d_1024":
-        A = P.fem2d(1024, 3)
-        b = P.rhs_uniform(A.n, 3)
-        # train the smoother network on the GPU on small problems of the same family
-        train = [amg.Hierarchy(P.fem2d(m, 200 + q), alpha=0.25, seed=1, coarse_max=16, max_levels=2,
+    def train_weights(family, seed):
+        """Smoother network trained on the GPU (own forward/backward/Adam kernels)
+        on four small two-level problems of the workload's family."""
+        train = [amg.Hierarchy(family(m, seed + q), alpha=0.25, seed=1, coarse_max=16, max_levels=2,
                                omega_mode=1, omega=2.0 / 3.0) for q, m in enumerate((48, 64, 80, 96))]
         w = np.zeros(5443, np.float32)
         rng = np.random.default_rng(3)
@@ -122,9 +107,43 @@ def other_workload(args):
         arr = (C_void_p_array(len(train)))(*[t.h for t in train])
         t0 = time.perf_counter()
         rc = amg.lib().amg_train_smoother(arr, len(train), 150, 3e-3, 2, 11, w.ctypes.data, hist.ctypes.data, None)
-        train_s = time.perf_counter() - t0
-        assert rc == 0
-        w16 = w.astype(np.float16).view(np.uint16)
+        assert rc == 0, amg.amg_last_error()
+        return w.astype(np.float16).view(np.uint16), time.perf_counter() - t0, hist
+
+    if args.workload == "varcoef3d_160":
+        A = P.varcoef3d(160, 2)
+        b = P.rhs_uniform(A.n, 2)
+        res = {}
+        allow = (amg.AMG_OK, amg.AMG_ERR_NOT_CONVERGED)
+        for name, pk in (("fgmres30_bf16", dict(outer=1, precision=2)), ("fgmres30_f64", dict(outer=1, precision=0)),
+                         ("fcg_bf16", dict(outer=0, precision=2)), ("fcg_f32", dict(outer=0, precision=1)),
+                         ("fcg_f64", dict(outer=0, precision=0))):
+            cap = 600 if pk["outer"] == 1 else 2000
+            rp, ci, va = (torch.from_numpy(a).to(dev) for a in (A.rowptr, A.col, A.val))
+            bd = torch.from_numpy(b).to(dev)
+            xd = torch.zeros_like(bd)
+
+            def go():
+                h = amg.amg_setup(rp, ci, va, amg.amg_default_params(alpha=0.5, seed=2, restart=30, max_iter=cap, **pk))
+                xd.zero_()
+                amg.amg_solve(h, bd, xd, TOL, cap, allow=allow)
+                i = amg.amg_last_solve_info(h)
+                amg.amg_free(h)
+                return i
+            t, i = timed(go, reps)
+            res[name] = {"ms": t, "setup_ms": i["setup_ms"], "solve_ms": i["solve_ms"], "iters": i["iters"],
+                         "final_relres": i["final_relres"], "converged": i["status"] == amg.AMG_OK}
+        line.update(value=A.n / (res["fcg_bf16"]["ms"] / 1e3), ms_per_step=res["fcg_bf16"]["ms"], dtype="bf16+f32+f64",
+                    config={"workload": "3D finite-volume -div(k grad u) 160^3 (n=4,096,000), k log-uniform "
+                                        "[1e-3,1e3] on 8^3 blocks, z x100 on x<80; K-cycle AMG, BF16 matrix values "
+                                        "(compensated FP32 diagonal) / FP32 vectors vs FP64, to 1e-8",
+                            "headline": "flexible CG with the BF16 preconditioner (FGMRES(30) stalls on this "
+                                        "problem: see fgmres30_* final_relres after 600 iterations)"},
+                    compare=res)
+    elif args.workload == "fem2d_1024":
+        A = P.fem2d(1024, 3)
+        b = P.rhs_uniform(A.n, 3)
+        w16, train_s, hist = train_weights(P.fem2d, 200)
         res = {}
         for name, pk in (("jacobi_f64", dict(precision=0)), ("jacobi_f32", dict(precision=1)),
                          ("learned_f32", dict(precision=1, smoother=1)), ("learned_f64", dict(precision=0, smoother=1))):
@@ -147,26 +166,38 @@ def other_workload(args):
         mats = [P.varcoef2d(int(m), 4 + q) for q, m in enumerate(sides)]
         rhs = np.concatenate([P.rhs_uniform(A.n, 4 + q) for q, A in enumerate(mats)])
         gen_s = time.perf_counter() - t0
+        w16, train_s, hist = train_weights(lambda m, sd: P.varcoef2d(m, sd), 300)
         dmats = [tuple(torch.from_numpy(a).to(dev) for a in (A.rowptr, A.col, A.val)) for A in mats]
         bd = torch.from_numpy(rhs).to(dev)
         xd = torch.zeros_like(bd)
         ntot = int(rhs.size)
         res = {}
-        for name, pk in (("f32", dict(precision=1)), ("f64", dict(precision=0))):
+        shapes = {}
+        for name, pk in (("learned_f32_tuned", dict(precision=1, smoother=1, omega_mode=1, omega=2.0 / 3.0, autotune=1)),
+                         ("jacobi_f32_tuned", dict(precision=1, autotune=1)),
+                         ("jacobi_f64", dict(precision=0))):
             def go():
                 h = amg.amg_setup_batch(dmats, amg.amg_default_params(alpha=0.25, seed=4, max_iter=2000, **pk))
+                if pk.get("smoother") == 1:
+                    assert amg.lib().amg_apply_learned_smoother(h, w16.ctypes.data, None) == 0, amg.amg_last_error()
                 xd.zero_()
                 rc, it, rel = amg.amg_solve_batch(h, bd, xd, TOL, len(mats))
                 i = amg.amg_last_solve_info(h)
+                lv = amg.amg_hierarchy_info(h)
                 amg.amg_free(h)
-                return i, it, rel
-            t, (i, it, rel) = timed(go, reps)
+                return i, it, rel, lv
+            t, (i, it, rel, lv) = timed(go, reps)
             res[name] = {"ms": t, "setup_ms": i["setup_ms"], "solve_ms": i["solve_ms"], "max_iters": int(it.max()),
                          "mean_iters": float(it.mean()), "worst_relres": float(rel.max())}
-        line.update(value=ntot / (res["f32"]["ms"] / 1e3), ms_per_step=res["f32"]["ms"], dtype="f32+f64",
+            shapes[name] = [(l["n"], l["spmv_blocks"], l["seg_tile"]) for l in lv]
+        line.update(value=ntot / (res["learned_f32_tuned"]["ms"] / 1e3), ms_per_step=res["learned_f32_tuned"]["ms"],
+                    dtype="f32+f64",
                     config={"workload": f"512 independent 2D variable-coefficient 5-point systems, sides uniform "
                                         f"32..512 (n={ntot:,}), k log-uniform [1e-2,1e2]; one block-diagonal "
-                                        f"hierarchy, per-system flexible CG to 1e-8 (generation {gen_s:.0f} s)"},
+                                        f"hierarchy, per-system flexible CG to 1e-8 (generation {gen_s:.0f} s)",
+                            "training": f"150 Adam steps on 4 two-level variable-coefficient problems (48^2..96^2), "
+                                        f"{train_s:.1f} s, two-grid factor {hist[0]:.4f} -> {hist[-1]:.4f}",
+                            "autotuned_shapes": shapes["learned_f32_tuned"]},
                     compare=res)
     print(json.dumps(line), flush=True)
 

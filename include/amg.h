@@ -85,6 +85,10 @@ typedef struct amg_params {
                             levels) in one launch per visit: 1 = a cluster of 8 blocks,
                             2 = a single block; 0 = one kernel per step                    */
   int32_t pdl;           /* 1: launch solve kernels with programmatic dependent launch     */
+  int32_t autotune;      /* 1: at setup, time each level's SpMV over candidate grid sizes
+                            (and, for a batch, the row tile of the per-system inner
+                            products) and keep the fastest; the choice is reported in
+                            amg_level_info.  Changes rounding order only                  */
 } amg_params;
 
 typedef struct amg_level_info {
@@ -93,6 +97,9 @@ typedef struct amg_level_info {
   int32_t n_coarse;   /* n_{k+1} (0 on the coarsest level)                  */
   int32_t mis_rounds; /* PMIS(2) rounds used to coarsen this level          */
   double omega;       /* damped-Jacobi weight of this level                 */
+  int32_t spmv_blocks; /* thread blocks of this level's SpMV launches          */
+  int32_t seg_tile;    /* rows per tile of the per-system inner products of a
+                          batch (0: not a batch)                              */
 } amg_level_info;
 
 typedef struct amg_solve_info {
@@ -109,7 +116,8 @@ typedef struct amg_hierarchy amg_hierarchy;
 
 /* Fill *p with the defaults: alpha 0.25, seed 0, coarse_max 64, max_levels 25,
  * kcycle_levels 2, kcycle_t 0.25, omega_mode 0, omega 2/3, precision F64,
- * outer FCG, restart 30, max_iter 500, use_graph 1, smoother 0, tail 0, pdl 1. */
+ * outer FCG, restart 30, max_iter 500, use_graph 1, smoother 0, tail 0, pdl 1,
+ * autotune 0. */
 void amg_default_params(amg_params *p);
 
 /* Alg. 1: build the hierarchy of A on the GPU.

@@ -40,12 +40,13 @@ class amg_params(C.Structure):
                 ("max_levels", C.c_int32), ("kcycle_levels", C.c_int32), ("kcycle_t", C.c_double),
                 ("omega_mode", C.c_int32), ("omega", C.c_double), ("precision", C.c_int32),
                 ("outer", C.c_int32), ("restart", C.c_int32), ("max_iter", C.c_int32),
-                ("use_graph", C.c_int32), ("smoother", C.c_int32), ("tail", C.c_int32), ("pdl", C.c_int32)]
+                ("use_graph", C.c_int32), ("smoother", C.c_int32), ("tail", C.c_int32), ("pdl", C.c_int32),
+                ("autotune", C.c_int32)]
 
 
 class amg_level_info(C.Structure):
     _fields_ = [("n", C.c_int32), ("nnz", C.c_int64), ("n_coarse", C.c_int32), ("mis_rounds", C.c_int32),
-                ("omega", C.c_double)]
+                ("omega", C.c_double), ("spmv_blocks", C.c_int32), ("seg_tile", C.c_int32)]
 
 
 class amg_solve_info(C.Structure):
@@ -229,8 +230,8 @@ def amg_hierarchy_info(h) -> list[dict]:
     _check(lib().amg_hierarchy_info(h, None, 0, C.byref(nl)))
     arr = (amg_level_info * nl.value)()
     _check(lib().amg_hierarchy_info(h, arr, nl.value, C.byref(nl)))
-    return [{"n": a.n, "nnz": a.nnz, "n_coarse": a.n_coarse, "mis_rounds": a.mis_rounds, "omega": a.omega}
-            for a in arr]
+    return [{"n": a.n, "nnz": a.nnz, "n_coarse": a.n_coarse, "mis_rounds": a.mis_rounds, "omega": a.omega,
+             "spmv_blocks": a.spmv_blocks, "seg_tile": a.seg_tile} for a in arr]
 
 
 def amg_export_level(h, level: int) -> dict:

@@ -127,6 +127,8 @@ struct Level {
   // a_ii plus the rounding errors of the row's off-diagonals, so that row sums
   // stay exact and the rounded matrix stays spectrally equivalent to A.
   int32_t nslices = 0;
+  int32_t sell_blocks = 0;    // grid of this level's SpMV launches (set at prepare, autotuned)
+  int32_t seg_tile = 0;       // batch: rows per tile of the per-system inner products
   int64_t sell_entries = 0;
   int64_t *sptr = nullptr;
   int32_t *scol = nullptr;

@@ -96,7 +96,7 @@ int check_params(const amg_params *p) {
   if (!(p->alpha >= 0.0 && p->alpha < 1.0) || p->coarse_max < 1 || p->max_levels < 1 || p->kcycle_levels < 0 ||
       p->precision < 0 || p->precision > 2 || p->outer < 0 || p->outer > 1 || p->max_iter < 1 ||
       p->restart < 1 || p->omega_mode < 0 || p->omega_mode > 1 || p->smoother < 0 || p->smoother > 1 ||
-      p->tail < 0 || p->tail > 2) {
+      p->tail < 0 || p->tail > 2 || p->autotune < 0 || p->autotune > 1) {
     amg::set_last_error("invalid amg_params");
     return AMG_ERR_BAD_INPUT;
   }
@@ -136,6 +136,7 @@ void amg_default_params(amg_params *p) {
   p->smoother = 0;
   p->tail = 0;
   p->pdl = 1;
+  p->autotune = 0;
 }
 
 int amg_setup(const amg_csr *A, const amg_params *params, void *stream, amg_hierarchy **out) {
@@ -425,6 +426,8 @@ int amg_hierarchy_info(const amg_hierarchy *H, amg_level_info *levels, int32_t c
       levels[k].n_coarse = (k + 1 < H->h.L) ? L.nc : 0;
       levels[k].mis_rounds = L.mis_rounds;
       levels[k].omega = L.omega;
+      levels[k].spmv_blocks = L.sell_blocks;
+      levels[k].seg_tile = H->h.batched ? L.seg_tile : 0;
     }
   return AMG_OK;
 }

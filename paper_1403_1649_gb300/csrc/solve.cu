@@ -889,8 +889,13 @@ namespace {
 
 inline int ew_grid(int64_t n) { return grid_for(n, kThreads, kRedBlocks); }
 void prepare_batched(Hierarchy &h, cudaStream_t s);
+template <class MV, class VT>
+void autotune_t(Hierarchy &h, cudaStream_t s);
 // k_sell keeps 4 blocks of 256 threads resident per SM (64 registers): one wave
-inline int sell_grid(const Level &L) { return grid_for((int64_t)L.nslices, kWarps, 4 * 152); }
+// by default; the autotuner may choose another grid (at most kRedBlocks, the
+// capacity of the partial-sum buffers)
+inline int default_sell_grid(const Level &L) { return grid_for((int64_t)L.nslices, kWarps, 4 * 152); }
+inline int sell_grid(const Level &L) { return L.sell_blocks > 0 ? L.sell_blocks : default_sell_grid(L); }
 
 template <class MV, class VT>
 struct Engine {
@@ -1250,6 +1255,7 @@ void alloc_level_vectors(Hierarchy &h, Level &L, int k) {
     L.d = vec();
     L.w = vec();
   }
+  if (L.sell_blocks <= 0) L.sell_blocks = default_sell_grid(L);
   L.slots = h.arena.get<double>(kNumSlots);
   L.flag = h.arena.get<int>(4);
   L.partials = h.arena.get<double>((size_t)kRedBlocks * 8);
@@ -1335,6 +1341,7 @@ void prepare_t(Hierarchy &h, cudaStream_t s) {
   if (!h.host_pinned) AMG_CUDA(cudaMallocHost(&h.host_pinned, 64 * sizeof(double)));
   if (h.batched) prepare_batched(h, s);
   configure_tail(h, s);
+  if (h.p.autotune) autotune_t<MV, VT>(h, s);
 }
 
 template <class VT>
@@ -1735,6 +1742,27 @@ int run_solve_batch_t(Hierarchy &h, const double *b, double *x, double tol, int3
   return status;
 }
 
+// row tiles of level L for the per-system inner products: every tile lies in
+// one system and holds at most `tile` rows
+void build_tiles(Hierarchy &h, Level &L, int32_t tile, cudaStream_t s) {
+  const int32_t ns = h.nsys;
+  std::vector<int32_t> trow, stile(ns + 1, 0);
+  for (int32_t q = 0; q < ns; ++q) {
+    stile[q] = (int32_t)trow.size();
+    for (int32_t r = L.sys_off_host[q]; r < L.sys_off_host[q + 1]; r += tile) trow.push_back(r);
+  }
+  stile[ns] = (int32_t)trow.size();
+  L.ntiles = (int32_t)trow.size();
+  L.seg_tile = tile;
+  trow.push_back(L.n);
+  L.tile_row = h.arena.get<int32_t>(trow.size());
+  L.sys_tile = h.arena.get<int32_t>(ns + 1);
+  L.tpart = h.arena.get<double>(3 * (size_t)L.ntiles + 1);
+  AMG_CUDA(cudaMemcpyAsync(L.tile_row, trow.data(), sizeof(int32_t) * trow.size(), cudaMemcpyHostToDevice, s));
+  AMG_CUDA(cudaMemcpyAsync(L.sys_tile, stile.data(), sizeof(int32_t) * (ns + 1), cudaMemcpyHostToDevice, s));
+  AMG_CUDA(cudaStreamSynchronize(s));  // trow / stile leave scope
+}
+
 // per-level system map, row tiles and per-system scalars of a batch
 void prepare_batched(Hierarchy &h, cudaStream_t s) {
   const int32_t ns = h.nsys;
@@ -1743,28 +1771,79 @@ void prepare_batched(Hierarchy &h, cudaStream_t s) {
     Level &L = h.lev[k];
     L.sys_of = h.arena.get<int32_t>((size_t)L.n + 1);
     klaunch(k_sys_of, ew_grid(L.n), kThreads, s, L.n, ns, (const int32_t *)L.sys_off, L.sys_of);
-    std::vector<int32_t> trow, stile(ns + 1, 0);
-    for (int32_t q = 0; q < ns; ++q) {
-      stile[q] = (int32_t)trow.size();
-      for (int32_t r = L.sys_off_host[q]; r < L.sys_off_host[q + 1]; r += kTile) trow.push_back(r);
-    }
-    stile[ns] = (int32_t)trow.size();
-    L.ntiles = (int32_t)trow.size();
-    trow.push_back(L.n);
-    L.tile_row = h.arena.get<int32_t>(trow.size());
-    L.sys_tile = h.arena.get<int32_t>(ns + 1);
-    L.tpart = h.arena.get<double>(3 * (size_t)L.ntiles + 1);
+    build_tiles(h, L, kTile, s);
     L.bslots = h.arena.get<double>((size_t)kNumSlots * ns);
     L.bflag = h.arena.get<int>((size_t)ns + 1);
-    AMG_CUDA(cudaMemcpyAsync(L.tile_row, trow.data(), sizeof(int32_t) * trow.size(), cudaMemcpyHostToDevice, s));
-    AMG_CUDA(cudaMemcpyAsync(L.sys_tile, stile.data(), sizeof(int32_t) * (ns + 1), cudaMemcpyHostToDevice, s));
     AMG_CUDA(cudaMemsetAsync(L.bslots, 0, sizeof(double) * kNumSlots * ns, s));
     AMG_CUDA(cudaMemsetAsync(L.bflag, 0, sizeof(int) * (ns + 1), s));
-    AMG_CUDA(cudaStreamSynchronize(s));  // trow / stile leave scope
   }
   h.bit = h.arena.get<int>(2 * (size_t)ns);
   h.bactive = h.arena.get<int>(2 * (size_t)ns + 2);
   AMG_LAUNCH_CHECK();
+}
+
+// Autotuner of the launch shapes (setup time).  For every level the SpMV is
+// timed with CUDA events over candidate grid sizes (multiples of the 152 SMs up
+// to the partial-sum capacity) and the smallest grid within 3 % of the fastest
+// is kept; for a batch, the row tile of the per-system inner products is chosen
+// the same way.  The shapes change the grouping of partial sums only.
+template <class MV, class VT>
+void autotune_t(Hierarchy &h, cudaStream_t s) {
+  Engine<MV, VT> eng(h, s);
+  cudaEvent_t e0, e1;
+  AMG_CUDA(cudaEventCreate(&e0));
+  AMG_CUDA(cudaEventCreate(&e1));
+  auto time_it = [&](auto &&launch) {
+    for (int r = 0; r < 2; ++r) launch();
+    AMG_CUDA(cudaEventRecord(e0, s));
+    constexpr int kReps = 5;
+    for (int r = 0; r < kReps; ++r) launch();
+    AMG_CUDA(cudaEventRecord(e1, s));
+    AMG_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    AMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    return ms / kReps;
+  };
+  auto pick = [](const std::vector<std::pair<int, float>> &t) {  // smallest within 3 % of the best
+    float best = t[0].second;
+    for (auto &c : t) best = std::min(best, c.second);
+    for (auto &c : t)
+      if (c.second <= 1.03f * best) return c.first;
+    return t[0].first;
+  };
+  try {
+    for (int k = 0; k < h.L; ++k) {
+      Level &L = h.lev[k];
+      DevBuf<VT> x((size_t)L.n + 1), y((size_t)L.n + 1);
+      AMG_CUDA(cudaMemsetAsync(x.p, 0, sizeof(VT) * (L.n + 1), s));
+      const int gmax = grid_for((int64_t)L.nslices, kWarps, kRedBlocks);
+      std::vector<std::pair<int, float>> t;
+      for (int g : {152, 304, 608, 912, 1216}) {
+        const int gg = std::min(g, gmax);
+        if (!t.empty() && t.back().first == gg) continue;
+        L.sell_blocks = gg;
+        const SellArgs<VT> a = eng.sell_args(k, x.p, y.p, nullptr);
+        t.push_back({gg, time_it([&] { eng.template sell<E_Y>(a, k); })});
+      }
+      L.sell_blocks = pick(t);
+      if (h.batched && k < h.L - 1) {
+        std::vector<std::pair<int, float>> tt;
+        for (int tile : {1024, 2048, 4096, 8192}) {
+          build_tiles(h, L, tile, s);
+          tt.push_back({tile, time_it([&] {
+                          eng.segdot(k, 2, x.p, x.p, y.p, y.p, nullptr, nullptr, S_RHO1, nullptr);
+                        })});
+        }
+        build_tiles(h, L, pick(tt), s);
+      }
+    }
+  } catch (...) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    throw;
+  }
+  AMG_CUDA(cudaEventDestroy(e0));
+  AMG_CUDA(cudaEventDestroy(e1));
 }
 
 template <class MV, class VT>

@@ -135,6 +135,31 @@ def test_batch_status_codes_and_termination(env):
         amg.amg_free(h)
 
 
+def test_batch_autotuned_shapes(env):
+    """With autotune the batch keeps its per-system results: the chosen row
+    tiles are among the candidates, every system converges, and the iteration
+    counts match the untuned batch."""
+    amg, _ = env
+    sides = [20, 33, 47, 12, 60, 8, 29]
+    mats = [P.varcoef2d(m, 40 + q) for q, m in enumerate(sides)]
+    b = np.concatenate([P.rhs_uniform(A.n, 60 + q) for q, A in enumerate(mats)])
+    res = {}
+    for tune in (0, 1):
+        h = amg.amg_setup_batch(mats, amg.amg_default_params(alpha=0.25, seed=1, precision=1, autotune=tune))
+        try:
+            info = amg.amg_hierarchy_info(h)
+            for k, lv in enumerate(info):
+                assert lv["spmv_blocks"] >= 1
+                assert lv["seg_tile"] in ((1024, 2048, 4096, 8192) if tune and k < len(info) - 1 else (2048,))
+            x = np.zeros_like(b)
+            rc, it, rel = amg.amg_solve_batch(h, b, x, 1e-8, len(mats))
+            assert rc == amg.AMG_OK and (rel <= 1e-8).all()
+            res[tune] = it
+        finally:
+            amg.amg_free(h)
+    assert (np.abs(res[1] - res[0]) <= 1).all()
+
+
 def test_batch_with_learned_smoother(env):
     amg, _ = env
     mats = [P.fem2d(m, 80 + q) for q, m in enumerate([24, 40, 16])]

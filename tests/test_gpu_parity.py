@@ -225,6 +225,28 @@ def test_programmatic_dependent_launch_changes_nothing(gpu, prec):
     assert ia["iters"] == ib["iters"] and np.array_equal(xa, xb)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_autotuned_spmv_grid_changes_only_rounding(gpu, orc, prec):
+    """The autotuner picks each level's SpMV grid among multiples of the SM count
+    (at most the partial-sum capacity); the hierarchy is the same, and the tuned
+    solve reaches the tolerance in the same number of iterations (FP64: within
+    1e-10 of the untuned solution)."""
+    A, alpha, seed = case("varcoef3d_24")
+    b = P.rhs_uniform(A.n, 21)
+    gt = gpu.Hierarchy(A, alpha=alpha, seed=seed, precision=prec, autotune=1)
+    g0 = gpu.Hierarchy(A, alpha=alpha, seed=seed, precision=prec)
+    for lt, l0 in zip(gt.info(), g0.info()):
+        assert lt["n"] == l0["n"] and lt["nnz"] == l0["nnz"] and lt["seg_tile"] == 0
+        nsl = (lt["n"] + 31) // 32
+        assert 1 <= lt["spmv_blocks"] <= min(1216, max(1, (nsl + 7) // 8))
+        assert l0["spmv_blocks"] == min(608, max(1, (nsl + 7) // 8))
+    xt, it = gt.solve(b, tol=1e-8)
+    x0, i0 = g0.solve(b, tol=1e-8)
+    assert abs(it["iters"] - i0["iters"]) <= (0 if prec == 0 else 1) and it["final_relres"] <= 1e-8
+    if prec == 0:
+        assert np.linalg.norm(xt - x0) <= 1e-10 * np.linalg.norm(x0)
+
+
 def test_single_level_one_iteration(gpu):
     A = P.poisson2d(7)
     g = gpu.Hierarchy(A, coarse_max=64)
