@@ -106,41 +106,63 @@ __device__ __forceinline__ double dot_operand(int op, double x, double y, double
   return op == OP_X ? x : (op == OP_Y ? y : (op == OP_U1 ? u1 : u2));
 }
 
-template <class MV, class VT, int EPI>
-__global__ void __launch_bounds__(kThreads, 4) k_sell(SellArgs<VT> a) {
+// Resident blocks per SM of k_sell: FP32 vectors fit in 40 registers (6 blocks
+// of 256 threads), FP64 vectors need 64 (4 blocks).
+template <class VT>
+constexpr int sell_min_blocks() { return sizeof(VT) == 4 ? 6 : 4; }
+
+// DOTS: the launch fuses inner products (compiled only where used, so that the
+// plain SpMV does not hold their accumulators in registers)
+template <class MV, class VT, int EPI, bool DOTS>
+__global__ void __launch_bounds__(kThreads, sell_min_blocks<VT>()) k_sell(SellArgs<VT> a) {
   pdl_wait_and_trigger();
   if (a.pred && *a.pred == 0) return;
   const int lane = threadIdx.x & 31;
   const MV *__restrict__ sval = static_cast<const MV *>(a.sval);
   double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
+  // U entries of a row per step: 6 with FP32 vectors (a 7-point row without its
+  // split-off diagonal in one step, at 40 registers), 8 with FP64
+  constexpr int U = sizeof(VT) == 4 ? 6 : 8;
   for (int32_t sl = blockIdx.x * kWarps + (threadIdx.x >> 5); sl < a.nslices; sl += gridDim.x * kWarps) {
+    const int32_t row = sl * 32 + lane;
     const int64_t base = a.sptr[sl];
     const int32_t width = (int32_t)((a.sptr[sl + 1] - base) >> 5);
     const int32_t *__restrict__ cp = a.scol + base + lane;
     const MV *__restrict__ vp = sval + base + lane;
-    VT y = VT(0);
-    // eight entries per step, all loads issued before the gathers
-    for (int32_t e = 0; e < width; e += 8) {
-      int32_t c[8];
-      MV v[8];
+    VT y = VT(0), dg = VT(0), xr = VT(0);
+    // the split diagonal (FP32 / BF16 values only) and x_row are loaded right
+    // behind the first step's matrix loads, so that their latency overlaps the gathers
+    const bool diag = !std::is_same<MV, double>::value && a.sdiag != nullptr && row < a.n;
+    for (int32_t e = 0; e < width; e += U) {
+      int32_t c[U];
+      MV v[U];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
+      for (int q = 0; q < U; ++q) {
         if (e + q < width) {
           c[q] = ld_stream(cp + 32 * (e + q));
           v[q] = ld_stream(vp + 32 * (e + q));
         }
       }
-      VT xv[8];
+      if (e == 0 && diag) {
+        dg = (VT)ld_stream(a.sdiag + row);
+        xr = __ldg(a.x + row);
+      }
+      VT xv[U];
 #pragma unroll
-      for (int q = 0; q < 8; ++q)
+      for (int q = 0; q < U; ++q)
         if (e + q < width) xv[q] = __ldg(a.x + c[q]);
 #pragma unroll
-      for (int q = 0; q < 8; ++q)
+      for (int q = 0; q < U; ++q)
         if (e + q < width) y += to_acc(v[q], VT(0)) * xv[q];
     }
-    const int32_t row = sl * 32 + lane;
+    if (diag) {
+      if (width == 0) {  // a row without off-diagonal entries
+        dg = (VT)a.sdiag[row];
+        xr = a.x[row];
+      }
+      y += dg * xr;
+    }
     if (row < a.n) {
-      if (a.sdiag) y += (VT)a.sdiag[row] * a.x[row];
       VT o;
       if (EPI == E_Y) o = y;
       else if (EPI == E_RESID) o = a.rhs[row] - y;
@@ -156,7 +178,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_sell(SellArgs<VT> a) {
       else
         o = a.xin[row] + (a.dinv[row] * y + a.dinv[row] * (a.coef[3 * row] * a.res[row]));
       a.out[row] = o;
-      if (a.ndot) {
+      if (DOTS && a.ndot) {
         const double ox = (double)a.x[row], oy = (double)o, o1 = a.u1 ? (double)a.u1[row] : 0.0,
                      o2 = a.u2 ? (double)a.u2[row] : 0.0;
         acc0 += dot_operand(a.dop[0][0], ox, oy, o1, o2) * dot_operand(a.dop[0][1], ox, oy, o1, o2);
@@ -165,7 +187,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_sell(SellArgs<VT> a) {
       }
     }
   }
-  if (a.ndot) block_store_dots3(acc0, acc1, acc2, a.ndot, a.partials);
+  if (DOTS && a.ndot) block_store_dots3(acc0, acc1, acc2, a.ndot, a.partials);
 }
 
 // out = wd * rhs: damped Jacobi from a zero initial guess
@@ -891,11 +913,16 @@ inline int ew_grid(int64_t n) { return grid_for(n, kThreads, kRedBlocks); }
 void prepare_batched(Hierarchy &h, cudaStream_t s);
 template <class MV, class VT>
 void autotune_t(Hierarchy &h, cudaStream_t s);
-// k_sell keeps 4 blocks of 256 threads resident per SM (64 registers): one wave
-// by default; the autotuner may choose another grid (at most kRedBlocks, the
-// capacity of the partial-sum buffers)
-inline int default_sell_grid(const Level &L) { return grid_for((int64_t)L.nslices, kWarps, 4 * 152); }
-inline int sell_grid(const Level &L) { return L.sell_blocks > 0 ? L.sell_blocks : default_sell_grid(L); }
+// Grid of a level's SpMV launches: one wave of resident blocks (6 per SM with
+// FP32 vectors, 4 with FP64) unless the autotuner chose another size (at most
+// kRedBlocks, the capacity of the partial-sum buffers).  The FP64 products of the
+// outer iteration on level 0 use the FP64 kernel's wave whatever the precision.
+template <class VT>
+inline int default_sell_grid(const Level &L) {
+  return grid_for((int64_t)L.nslices, kWarps, sell_min_blocks<VT>() * 152);
+}
+inline int sell_grid(const Level &L) { return L.sell_blocks; }
+inline int outer_grid(const Level &L0) { return default_sell_grid<double>(L0); }
 
 template <class MV, class VT>
 struct Engine {
@@ -931,7 +958,18 @@ struct Engine {
 
   template <int EPI>
   void sell(const SellArgs<VT> &a, int k) {
-    klaunch(k_sell<MV, VT, EPI>, sell_grid(h.lev[k]), kThreads, s, a);
+    // fused inner products: after the plain product (Alg. 5) and on the last
+    // post-smoothing step of level 0 (z^T q of the outer flexible CG)
+    if constexpr (EPI == E_Y || EPI == E_POST || EPI == E_HORNER_LAST) {
+      if (a.ndot) {
+        klaunch(k_sell<MV, VT, EPI, true>, sell_grid(h.lev[k]), kThreads, s, a);
+        check();
+        return;
+      }
+    } else {
+      if (a.ndot) throw Error{AMG_ERR_UNSUPPORTED, "SpMV epilogue without fused inner products was given some"};
+    }
+    klaunch(k_sell<MV, VT, EPI, false>, sell_grid(h.lev[k]), kThreads, s, a);
     check();
   }
 
@@ -1180,7 +1218,7 @@ struct Engine {
       a.sval = L0.sval64;
       a.x = h.pdir;
       a.out = h.q;
-      klaunch(k_sell<double, double, E_Y>, sell_grid(L0), kThreads, s, a);
+      klaunch(k_sell<double, double, E_Y, false>, outer_grid(L0), kThreads, s, a);
     }
     launches += 3;
     e64.launches = 0;
@@ -1201,8 +1239,8 @@ struct Engine {
     Level &L0 = h.lev[0];
     double *part = L0.partials;
     const int ng = ew_grid(L0.n);
-    const int nsg = sell_grid(L0);
-    const int nzq = (std::is_same<VT, double>::value && h.L > 1) ? nsg : ng;
+    const int nsg = outer_grid(L0);  // FP64 q = A p and its two inner products
+    const int nzq = (std::is_same<VT, double>::value && h.L > 1) ? sell_grid(L0) : ng;  // z^T q of the cycle
     // z = M r (+ z^T q partials)
     precond(h.r, h.z, active, true);
     // p = z + beta p
@@ -1223,7 +1261,7 @@ struct Engine {
       a.dop[1][0] = OP_X; a.dop[1][1] = OP_U1;
       a.partials = part + 5 * kRedBlocks;
       a.pred = active;
-      klaunch(k_sell<double, double, E_Y>, nsg, kThreads, s, a);
+      klaunch(k_sell<double, double, E_Y, true>, nsg, kThreads, s, a);
       check();
     }
     // x, r update (+ the next preconditioner input in reduced precision)
@@ -1255,7 +1293,7 @@ void alloc_level_vectors(Hierarchy &h, Level &L, int k) {
     L.d = vec();
     L.w = vec();
   }
-  if (L.sell_blocks <= 0) L.sell_blocks = default_sell_grid(L);
+  if (L.sell_blocks <= 0) L.sell_blocks = default_sell_grid<VT>(L);
   L.slots = h.arena.get<double>(kNumSlots);
   L.flag = h.arena.get<int>(4);
   L.partials = h.arena.get<double>((size_t)kRedBlocks * 8);
@@ -1383,7 +1421,7 @@ void copy_out(double *dst, const double *src_dev, int32_t n, cudaStream_t s) {
 // ||b - A x||^2 into slots[dst] (FP64)
 void true_residual(Hierarchy &h, int dst, cudaStream_t s, int64_t &launches) {
   Level &L0 = h.lev[0];
-  const int nsg = sell_grid(L0);
+  const int nsg = outer_grid(L0);
   klaunch(k_residual64, nsg, kThreads, s, L0.n, L0.nslices, L0.sptr64, L0.scol64, L0.sval64, h.x, h.b, h.r,
                                         L0.partials + 7 * kRedBlocks);
   klaunch(k_store_sum, 1, kThreads, s, L0.partials + 7 * kRedBlocks, nsg, L0.slots + dst);
@@ -1563,7 +1601,7 @@ int run_fgmres_t(Hierarchy &h, const double *b, double *x, double tol, int32_t *
         a.x = zj;
         a.out = w;
         a.pred = active;
-        klaunch(k_sell<double, double, E_Y>, sell_grid(L0), kThreads, s, a);
+        klaunch(k_sell<double, double, E_Y, false>, outer_grid(L0), kThreads, s, a);
         eng.check();
       }
       for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
@@ -1668,7 +1706,7 @@ int run_solve_batch_t(Hierarchy &h, const double *b, double *x, double tol, int3
   copy_in(h.x, x, n, s);
   e64.segdot(0, 1, h.b, h.b, nullptr, nullptr, nullptr, nullptr, S_NB2, nullptr);
   klaunch(k_fix_zero_norm, grid_for(ns, kThreads, 152), kThreads, s, ns, L0.bslots);
-  klaunch(k_residual64, sell_grid(L0), kThreads, s, n, L0.nslices, (const int64_t *)L0.sptr64,
+  klaunch(k_residual64, outer_grid(L0), kThreads, s, n, L0.nslices, (const int64_t *)L0.sptr64,
           (const int32_t *)L0.scol64, (const double *)L0.sval64, (const double *)h.x, (const double *)h.b, h.r,
           L0.partials + 7 * kRedBlocks);
   e64.segdot(0, 1, h.r, h.r, nullptr, nullptr, nullptr, nullptr, S_RR, nullptr);
@@ -1707,7 +1745,7 @@ int run_solve_batch_t(Hierarchy &h, const double *b, double *x, double tol, int3
       continue;
     }
     // every system stopped: check the true residuals, restart those that miss tol
-    klaunch(k_residual64, sell_grid(L0), kThreads, s, n, L0.nslices, (const int64_t *)L0.sptr64,
+    klaunch(k_residual64, outer_grid(L0), kThreads, s, n, L0.nslices, (const int64_t *)L0.sptr64,
             (const int32_t *)L0.scol64, (const double *)L0.sval64, (const double *)h.x, (const double *)h.b, h.r,
             L0.partials + 7 * kRedBlocks);
     e64.segdot(0, 1, h.r, h.r, nullptr, nullptr, nullptr, nullptr, S_TRUE_RR, nullptr);
