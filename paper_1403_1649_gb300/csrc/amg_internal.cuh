@@ -115,6 +115,7 @@ struct Level {
   int32_t n = 0, nc = 0, mis_rounds = 0;
   int64_t nnz = 0;
   double omega = 0.0;
+  double *omega_dev = nullptr;  // the estimated weight on the device (omega_mode 0)
   // setup CSR (FP64, exact)
   int32_t *rp = nullptr, *ci = nullptr;
   double *val = nullptr;

@@ -377,6 +377,8 @@ __global__ void k_interp(int32_t nc, const int32_t *__restrict__ aptr, const int
 // ascending order; for each it sums P_iI * A_ij * P_jJ over the run in order,
 // one term at a time, so every coarse value is the sequential sum.
 constexpr int kGalWarps = 8;   // warps per block of k_galerkin
+constexpr int32_t kGalCapMax = 4096;         // longest run staged by k_galerkin_smem
+constexpr size_t kGalSmemBudget = 200 << 10;  // its dynamic shared memory per block
 constexpr int kGalCap = 320;   // entries of one coarse row staged in shared memory
 
 template <bool FILL>
@@ -384,13 +386,15 @@ __global__ void __launch_bounds__(kGalWarps * 32) k_galerkin(
     int32_t nc, const int32_t *__restrict__ aptr, const int32_t *__restrict__ amem,
     const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ val,
     const int32_t *__restrict__ agg, const double *__restrict__ pw, int32_t *__restrict__ ccount,
-    const int32_t *__restrict__ crp, int32_t *__restrict__ cci, double *__restrict__ cval) {
+    const int32_t *__restrict__ crp, int32_t *__restrict__ cci, double *__restrict__ cval, bool marked_only) {
   __shared__ int32_t sJ[kGalWarps][kGalCap];
+  __shared__ int32_t sK[kGalWarps][kGalCap];  // distinct coarse columns of the run
   __shared__ double sV[FILL ? kGalWarps : 1][FILL ? kGalCap : 1];
   const int lane = threadIdx.x & 31;
   const int wid = threadIdx.x >> 5;
   const int wpb = blockDim.x >> 5;
   for (int32_t I = blockIdx.x * wpb + wid; I < nc; I += gridDim.x * wpb) {
+    if (marked_only && ccount[I] != -1) continue;  // done by k_galerkin_smem
     const int32_t m0 = aptr[I], m1 = aptr[I + 1];
     // length of the run of keys (I, *): all entries of the member rows
     int32_t total = 0;
@@ -426,40 +430,62 @@ __global__ void __launch_bounds__(kGalWarps * 32) k_galerkin(
         base += __shfl_sync(0xffffffffu, incl, 31);
       }
       __syncwarp();
-      // walk the distinct coarse columns in ascending order; sum each in run order
-      int32_t cur = -1, out = 0;
-      for (;;) {
-        int32_t next = INT_MAX;
-        double sum = 0.0;
-        bool have = false;
-        for (int32_t e0 = 0; e0 < total; e0 += 32) {
-          const int32_t e = e0 + lane;
-          const int32_t J = e < total ? sJ[wid][e] : INT_MAX;
-          if (J > cur && J < next) next = J;
-          if (FILL) {
-            unsigned mask = __ballot_sync(0xffffffffu, J == cur);
-            const double v = (J == cur) ? sV[wid][e] : 0.0;
-            while (mask) {
-              const int src = __ffs(mask) - 1;
-              const double t = __shfl_sync(0xffffffffu, v, src);
-              sum = have ? __dadd_rn(sum, t) : t;
-              have = true;
-              mask &= mask - 1;
+      // distinct coarse columns of the run, in order of first occurrence
+      int32_t d = 0;
+      for (int32_t e0 = 0; e0 < total; e0 += 32) {
+        const int32_t e = e0 + lane;
+        bool first = false;
+        int32_t J = 0;
+        if (e < total) {
+          J = sJ[wid][e];
+          first = true;
+          for (int32_t t = 0; t < e; ++t)
+            if (sJ[wid][t] == J) {
+              first = false;
+              break;
             }
-          }
         }
-        next = __reduce_min_sync(0xffffffffu, next);
-        if (cur >= 0) {
-          if (FILL && lane == 0) {
-            cci[crp[I] + out] = cur;
-            cval[crp[I] + out] = sum;
-          }
-          out++;
-        }
-        if (next == INT_MAX) break;
-        cur = next;
+        const unsigned b = __ballot_sync(0xffffffffu, first);
+        if (first) sK[wid][d + __popc(b & ((1u << lane) - 1u))] = J;
+        d += __popc(b);
       }
-      if (ccount && lane == 0) ccount[I] = out;
+      __syncwarp();
+      // ascending order: the rank of a column is the number of smaller ones
+      int32_t kk[kGalCap / 32], rk[kGalCap / 32];
+#pragma unroll
+      for (int t = 0; t < kGalCap / 32; ++t) {
+        const int32_t q = lane + 32 * t;
+        kk[t] = q < d ? sK[wid][q] : INT_MAX;
+        rk[t] = 0;
+        if (q < d)
+          for (int32_t u = 0; u < d; ++u) rk[t] += sK[wid][u] < kk[t] ? 1 : 0;
+      }
+      __syncwarp();
+#pragma unroll
+      for (int t = 0; t < kGalCap / 32; ++t)
+        if (lane + 32 * t < d) sK[wid][rk[t]] = kk[t];
+      __syncwarp();
+      // each lane sums its columns' terms in run order, starting from the first
+      if (FILL) {
+#pragma unroll
+        for (int t = 0; t < kGalCap / 32; ++t) {
+          const int32_t q = lane + 32 * t;
+          if (32 * t >= d) break;
+          if (q < d) {
+            const int32_t J = sK[wid][q];
+            double sum = 0.0;
+            bool have = false;
+            for (int32_t e = 0; e < total; ++e)
+              if (sJ[wid][e] == J) {
+                sum = have ? __dadd_rn(sum, sV[wid][e]) : sV[wid][e];
+                have = true;
+              }
+            cci[crp[I] + q] = J;
+            cval[crp[I] + q] = sum;
+          }
+        }
+      }
+      if (ccount && lane == 0) ccount[I] = d;
       __syncwarp();
       continue;
     }
@@ -513,11 +539,165 @@ __global__ void __launch_bounds__(kGalWarps * 32) k_galerkin(
 // entries of the run of keys (I, *): the summed lengths of the member rows,
 // an upper bound on the number of coarse nonzeros of row I
 __global__ void k_run_length(int32_t nc, const int32_t *__restrict__ aptr, const int32_t *__restrict__ amem,
-                             const int32_t *__restrict__ rp, int32_t *__restrict__ len) {
+                             const int32_t *__restrict__ rp, int32_t *__restrict__ len, int32_t *__restrict__ maxlen) {
+  int32_t mx = 0;
   for (int32_t I = blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += gridDim.x * blockDim.x) {
     int32_t t = 0;
     for (int32_t m = aptr[I]; m < aptr[I + 1]; ++m) t += rp[amem[m] + 1] - rp[amem[m]];
     len[I] = t;
+    mx = max(mx, t);
+  }
+  mx = __reduce_max_sync(0xffffffffu, mx);
+  if ((threadIdx.x & 31) == 0) atomicMax(maxlen, mx);
+}
+
+// Galerkin keyed sum (Sec. 3.1), one coarse row I per warp, its run staged in
+// shared memory (at most `cap` entries; longer runs are marked ccount[I] = -1 and
+// left to k_galerkin).  Per row:
+//  1. stage (J, (P_iI * A_ij) * P_jJ) in run order, one lane per entry;
+//  2. the distinct columns J through an open-addressing hash table, ranked
+//     ascending by counting;
+//  3. a stable counting scatter of the terms by column: chunks of 32 entries in
+//     run order, lanes of equal column ordered by lane (__match_any_sync), so
+//     every column's terms end up contiguous and in run order;
+//  4. one lane per column adds its terms in that order, starting from the first:
+//     the order of the sequential keyed sum, bit for bit.
+// Output goes to the row's upper-bound slot crp[I]; ccount[I] = number of columns.
+__global__ void __launch_bounds__(256) k_galerkin_smem(
+    int32_t nc, int32_t cap, int32_t hbits, const int32_t *__restrict__ aptr, const int32_t *__restrict__ amem,
+    const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ val,
+    const int32_t *__restrict__ agg, const double *__restrict__ pw, int32_t *__restrict__ ccount,
+    const int32_t *__restrict__ crp, int32_t *__restrict__ cci, double *__restrict__ cval) {
+  extern __shared__ __align__(16) unsigned char gal_sm[];
+  const int lane = threadIdx.x & 31;
+  const int wid = threadIdx.x >> 5;
+  const int wpb = blockDim.x >> 5;
+  const int32_t hsize = 1 << hbits, hmask = hsize - 1;
+  const unsigned lt = (1u << lane) - 1u;
+  const size_t per = (size_t)cap * 32 + (size_t)hsize * 8;
+  double *sV = reinterpret_cast<double *>(gal_sm + per * wid);  // staged terms
+  double *sW = sV + cap;                                       // terms grouped by column
+  int32_t *sJ = reinterpret_cast<int32_t *>(sW + cap);          // column of each term, then its rank
+  int32_t *sKey = sJ + cap;                                     // distinct columns, table order
+  int32_t *sCnt = sKey + cap;                                   // per rank: count, then segment end
+  int32_t *sAux = sCnt + cap;                                   // member offsets, then sorted columns
+  int32_t *hK = sAux + cap;
+  int32_t *hR = hK + hsize;
+  auto slot_of = [&](int32_t J) {
+    uint32_t hh = ((uint32_t)J * 2654435761u) >> (32 - hbits);
+    while (hK[hh] != J) hh = (hh + 1) & hmask;
+    return hh;
+  };
+  for (int32_t I = blockIdx.x * wpb + wid; I < nc; I += gridDim.x * wpb) {
+    const int32_t m0 = aptr[I], m1 = aptr[I + 1], nm = m1 - m0;
+    // run offsets of the member rows (warp prefix sums over chunks of 32 members)
+    int32_t total = 0;
+    for (int32_t mb = m0; mb < m1; mb += 32) {
+      const int32_t m = mb + lane;
+      int32_t len = 0;
+      if (m < m1) {
+        const int32_t i = amem[m];
+        len = rp[i + 1] - rp[i];
+      }
+      int32_t incl = len;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      if (m < m1 && total + incl - len < cap) sAux[m - m0] = total + incl - len;
+      total += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (total > cap || nm > cap) {
+      if (lane == 0) ccount[I] = -1;  // left to the global-memory kernel
+      continue;
+    }
+    __syncwarp();
+    // 1. stage the terms in run order, one lane per entry
+    for (int32_t e = lane; e < total; e += 32) {
+      int32_t lo = 0, hi = nm - 1;
+      while (lo < hi) {  // the member whose run segment holds e
+        const int32_t mid = (lo + hi + 1) >> 1;
+        if (sAux[mid] <= e) lo = mid; else hi = mid - 1;
+      }
+      const int32_t i = amem[m0 + lo];
+      const int32_t p = rp[i] + (e - sAux[lo]);
+      const int32_t j = ci[p];
+      sJ[e] = agg[j];
+      sV[e] = __dmul_rn(__dmul_rn(pw[i], val[p]), pw[j]);
+    }
+    for (int32_t t = lane; t < hsize; t += 32) hK[t] = -1;
+    __syncwarp();
+    // 2. distinct columns: hash insertion, compaction, ranks by counting
+    for (int32_t e = lane; e < total; e += 32) {
+      const int32_t J = sJ[e];
+      uint32_t hh = ((uint32_t)J * 2654435761u) >> (32 - hbits);
+      for (;;) {
+        const int32_t prev = atomicCAS(&hK[hh], -1, J);
+        if (prev == -1 || prev == J) break;
+        hh = (hh + 1) & hmask;
+      }
+    }
+    __syncwarp();
+    int32_t d = 0;
+    for (int32_t t0 = 0; t0 < hsize; t0 += 32) {
+      const int32_t k = hK[t0 + lane];
+      const unsigned b = __ballot_sync(0xffffffffu, k != -1);
+      if (k != -1) sKey[d + __popc(b & lt)] = k;
+      d += __popc(b);
+    }
+    __syncwarp();
+    for (int32_t q = lane; q < d; q += 32) {
+      const int32_t K = sKey[q];
+      int32_t r = 0;
+      for (int32_t u = 0; u < d; ++u) r += sKey[u] < K ? 1 : 0;
+      hR[slot_of(K)] = r;
+      sAux[r] = K;  // sorted columns (the member offsets are no longer needed)
+      sCnt[q] = 0;
+    }
+    __syncwarp();
+    // 3. counts per column in run order, then segment starts, then the stable scatter
+    for (int32_t e0 = 0; e0 < total; e0 += 32) {
+      const int32_t e = e0 + lane;
+      const int32_t r = e < total ? hR[slot_of(sJ[e])] : -1;
+      if (e < total) sJ[e] = r;
+      const unsigned grp = __match_any_sync(0xffffffffu, r);
+      if (r >= 0 && (grp & lt) == 0) sCnt[r] += __popc(grp);
+      __syncwarp();
+    }
+    {  // exclusive prefix over the d counts
+      int32_t run = 0;
+      for (int32_t q0 = 0; q0 < d; q0 += 32) {
+        const int32_t q = q0 + lane;
+        const int32_t c = q < d ? sCnt[q] : 0;
+        int32_t incl = c;
+        for (int o = 1; o < 32; o <<= 1) {
+          const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += y;
+        }
+        if (q < d) sCnt[q] = run + incl - c;
+        run += __shfl_sync(0xffffffffu, incl, 31);
+      }
+    }
+    __syncwarp();
+    for (int32_t e0 = 0; e0 < total; e0 += 32) {
+      const int32_t e = e0 + lane;
+      const int32_t r = e < total ? sJ[e] : -1;
+      const unsigned grp = __match_any_sync(0xffffffffu, r);
+      if (r >= 0) sW[sCnt[r] + __popc(grp & lt)] = sV[e];
+      __syncwarp();
+      if (r >= 0 && (grp & lt) == 0) sCnt[r] += __popc(grp);
+      __syncwarp();
+    }
+    // 4. one lane per column: its terms in run order (sCnt[r] is now its segment end)
+    for (int32_t q = lane; q < d; q += 32) {
+      const int32_t a = q == 0 ? 0 : sCnt[q - 1], b = sCnt[q];
+      double sum = sW[a];
+      for (int32_t t = a + 1; t < b; ++t) sum = __dadd_rn(sum, sW[t]);
+      cci[crp[I] + q] = sAux[q];
+      cval[crp[I] + q] = sum;
+    }
+    if (lane == 0) ccount[I] = d;
+    __syncwarp();
   }
 }
 
@@ -616,68 +796,159 @@ __global__ void k_build_sell(int32_t n, int32_t nslices, const int32_t *__restri
 }
 
 // ============================================================== Arnoldi omega
-__global__ void k_arnoldi_start(int32_t n, uint64_t seed, int32_t level, const double *__restrict__ diag,
-                                double *__restrict__ q, double *__restrict__ dh) {
-  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const uint64_t z = splitmix64(~seed ^ ((uint64_t)(uint32_t)level << 40) ^ (uint64_t)(uint32_t)i);
-  q[i] = 2.0 * ((double)(z >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
-  dh[i] = 1.0 / sqrt(fabs(diag[i]));
+// ---- Arnoldi on M = |D|^-1/2 A |D|^-1/2 with three kernels per step --------
+// Every kernel ends with a last-block reduction: blocks publish their partial
+// sums, take a ticket, and the block that finishes last sums the partials of
+// all blocks in block order (deterministic) and writes the scalars.
+constexpr int kArnSlots = 8;
+
+__device__ __forceinline__ bool arn_last_block(unsigned *ticket) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  return last;
 }
 
-// w = D^-1/2 A D^-1/2 q  (CSR, FP64, one thread per row)
-__global__ void k_scaled_spmv(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                              const double *__restrict__ val, const double *__restrict__ dh,
-                              const double *__restrict__ q, double *__restrict__ w) {
+// block partials of up to kArnSlots sums -> part[slot * gridDim.x + block]
+__device__ __forceinline__ void arn_block_partials(const double (&v)[kArnSlots], int ns, double *part) {
+  __shared__ double sh[kArnSlots][8];
+#pragma unroll
+  for (int k = 0; k < kArnSlots; ++k) {
+    if (k < ns) {
+      const double w = warp_sum(v[k]);
+      if ((threadIdx.x & 31) == 0) sh[k][threadIdx.x >> 5] = w;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < (unsigned)ns) {
+    double a = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) a += sh[threadIdx.x][q];
+    part[threadIdx.x * gridDim.x + blockIdx.x] = a;
+  }
+}
+
+// sums of slots 0..ns-1 over all blocks, computed by the whole last block in a
+// fixed order (thread t takes blocks t, t + 256, ..., then a fixed tree)
+__device__ void arn_totals(const double *part, int ns, double *out_sh) {
+  __shared__ double sh[8];
+  for (int k = 0; k < ns; ++k) {
+    double a = 0.0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) a += __ldcg(part + k * gridDim.x + b);
+    a = warp_sum(a);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[q];
+      out_sh[k] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// start: W = random start vector in [-1, 1), dh = |A_ii|^-1/2; nrm2 = ||W||^2
+__global__ void __launch_bounds__(256) k_arn_start(int32_t n, uint64_t seed, int32_t level,
+                                                   const double *__restrict__ diag, double *__restrict__ W,
+                                                   double *__restrict__ dh, double *part, double *nrm2,
+                                                   unsigned *ticket) {
+  double v[kArnSlots] = {0.0};
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint64_t z = splitmix64(~seed ^ ((uint64_t)(uint32_t)level << 40) ^ (uint64_t)(uint32_t)i);
+    const double q = 2.0 * ((double)(z >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
+    W[i] = q;
+    dh[i] = 1.0 / sqrt(fabs(diag[i]));
+    v[0] += q * q;
+  }
+  arn_block_partials(v, 1, part);
+  if (arn_last_block(ticket)) {
+    __shared__ double tot[kArnSlots];
+    arn_totals(part, 1, tot);
+    if (threadIdx.x == 0) {
+      *nrm2 = tot[0];
+      *ticket = 0;
+    }
+  }
+}
+
+// step j, part 1: q_j = W / ||W||; w = M q_j; h_lj = q_l . w (l <= j), wn_j = ||w||;
+// h_{j,j-1} = ||W|| (j > 0)
+__global__ void __launch_bounds__(256) k_arn_spmv(int32_t n, int j, const int32_t *__restrict__ rp,
+                                                  const int32_t *__restrict__ ci, const double *__restrict__ val,
+                                                  const double *__restrict__ dh, const double *__restrict__ W,
+                                                  double *__restrict__ Q, double *__restrict__ w, double *part,
+                                                  const double *nrm2, double *H, double *wn, unsigned *ticket) {
+  const double h = sqrt(*nrm2), sc = 1.0 / h;
+  double *qj = Q + (size_t)j * n;
+  double v[kArnSlots] = {0.0};
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     double acc = 0.0;
-    for (int32_t p = rp[i]; p < rp[i + 1]; ++p) acc += val[p] * (dh[ci[p]] * q[ci[p]]);
-    w[i] = dh[i] * acc;
+    for (int32_t p = rp[i]; p < rp[i + 1]; ++p) {
+      const int32_t c = ci[p];
+      acc += val[p] * (dh[c] * (sc * W[c]));
+    }
+    const double wi = dh[i] * acc, qi = sc * W[i];
+    qj[i] = qi;
+    w[i] = wi;
+#pragma unroll
+    for (int l = 0; l < kArnSlots; ++l) {  // static indices: the sums stay in registers
+      if (l < j) v[l] += Q[(size_t)l * n + i] * wi;
+      else if (l == j) v[l] += qi * wi;
+      else if (l == j + 1) v[l] += wi * wi;
+    }
+  }
+  arn_block_partials(v, j + 2, part);
+  if (arn_last_block(ticket)) {
+    __shared__ double tot[kArnSlots];
+    arn_totals(part, j + 2, tot);
+    if ((int)threadIdx.x <= j) H[threadIdx.x * 8 + j] = tot[threadIdx.x];
+    if ((int)threadIdx.x == j + 1) wn[j] = sqrt(tot[j + 1]);
+    if (threadIdx.x == 0) {
+      if (j > 0) H[j * 8 + (j - 1)] = h;
+      *ticket = 0;
+    }
   }
 }
 
-// block partial sums of a.b (grid-stride, fixed grid: deterministic)
-__global__ void k_dot_part(int32_t n, const double *__restrict__ a, const double *__restrict__ b,
-                           double *__restrict__ part) {
-  __shared__ double sh[32];
-  double acc = 0.0;
-  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) acc += a[i] * b[i];
-  acc = warp_sum(acc);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double v = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
-    v = warp_sum(v);
-    if (threadIdx.x == 0) part[blockIdx.x] = v;
+// step j, parts 2 and 3 (classical Gram-Schmidt twice): w -= sum_l c_l q_l with
+// c = H[.][j] (pass 0) or the correction corr (pass 1).  Pass 0 ends with
+// corr_l = q_l . w; pass 1 adds corr to H[.][j], writes W = w and nrm2 = ||w||^2.
+__global__ void __launch_bounds__(256) k_arn_orth(int32_t n, int j, int pass, const double *__restrict__ Q,
+                                                  double *__restrict__ w, double *__restrict__ W, double *part,
+                                                  double *H, double *corr, double *nrm2, unsigned *ticket) {
+  double c[kArnSlots];
+#pragma unroll
+  for (int l = 0; l < kArnSlots; ++l) c[l] = l <= j ? (pass == 0 ? H[l * 8 + j] : corr[l]) : 0.0;
+  double v[kArnSlots] = {0.0};
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double wi = w[i];
+#pragma unroll
+    for (int l = 0; l < kArnSlots; ++l)
+      if (l <= j) wi -= c[l] * Q[(size_t)l * n + i];
+    if (pass == 0) {
+      w[i] = wi;
+#pragma unroll
+      for (int l = 0; l < kArnSlots; ++l)
+        if (l <= j) v[l] += Q[(size_t)l * n + i] * wi;
+    } else {
+      W[i] = wi;
+      v[0] += wi * wi;
+    }
   }
-}
-
-// out[slot] = sum of part[0..nb)  (mode 1: sqrt of the sum)
-__global__ void k_fin_sum(const double *__restrict__ part, int nb, double *__restrict__ out, int mode) {
-  __shared__ double sh[32];
-  double acc = 0.0;
-  for (int k = threadIdx.x; k < nb; k += blockDim.x) acc += part[k];
-  acc = warp_sum(acc);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double v = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
-    v = warp_sum(v);
-    if (threadIdx.x == 0) *out = mode == 1 ? sqrt(v) : v;
+  const int ns = pass == 0 ? j + 1 : 1;
+  arn_block_partials(v, ns, part);
+  if (arn_last_block(ticket)) {
+    __shared__ double tot[kArnSlots];
+    arn_totals(part, ns, tot);
+    if (pass == 0) {
+      if ((int)threadIdx.x <= j) corr[threadIdx.x] = tot[threadIdx.x];
+    } else {
+      if ((int)threadIdx.x <= j) H[threadIdx.x * 8 + j] += corr[threadIdx.x];
+      if (threadIdx.x == 0) *nrm2 = tot[0];
+    }
+    if (threadIdx.x == 0) *ticket = 0;
   }
-}
-
-// y -= (*h) x
-__global__ void k_axpy_neg_dev(int32_t n, double *__restrict__ y, const double *__restrict__ x,
-                               const double *__restrict__ h) {
-  const double a = *h;
-  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) y[i] -= a * x[i];
-}
-// y = x / (*nrm)
-__global__ void k_div_dev(int32_t n, double *__restrict__ y, const double *__restrict__ x,
-                          const double *__restrict__ nrm) {
-  const double a = *nrm;
-  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) y[i] = x[i] / a;
 }
 
 // Largest |eigenvalue| of a small symmetric matrix by bisection on the inertia
@@ -739,8 +1010,11 @@ __global__ void k_omega_from_H(const double *__restrict__ H, const double *__res
     g = fmax(g, rs);
   }
   g = g * (1.0 + 1e-12) + 1e-300;
-  double ext[2];
-  for (int side = 0; side < 2; ++side) {
+  double ext[2] = {0.0, 0.0};
+  // no eigenvalue below 0 (the usual case: M is positive definite): rho is the
+  // largest eigenvalue and the smallest one need not be located
+  const int nsides = count_below(T, mm, 0.0) == 0 ? 1 : 2;
+  for (int side = 0; side < nsides; ++side) {
     // side 0: largest eigenvalue = sup{sigma : count_below(sigma) < mm}
     // side 1: smallest eigenvalue = sup{sigma : count_below(sigma) == 0}
     double lo = -g, hi = g;
@@ -1036,39 +1310,27 @@ void build_solve_matrix(Hierarchy &h, Level &L, cudaStream_t s) {
   }
 }
 
-// omega of Eq. (damped Jacobi) from m = 5 Arnoldi steps on D^-1/2 A D^-1/2
-double estimate_omega(Hierarchy &h, int k, const double *diag, cudaStream_t s) {
+// omega of Eq. (damped Jacobi) from m = 5 Arnoldi steps on D^-1/2 A D^-1/2:
+// three kernels per step, the result left in omega_dev (no host round trip)
+void estimate_omega(Hierarchy &h, int k, const double *diag, double *omega_dev, cudaStream_t s) {
   Level &L = h.lev[k];
   const int32_t n = L.n;
-  const int m = n < 5 ? n : 5;
-  DevBuf<double> Q((size_t)n * (m + 1)), w(n), dh(n), part(kRedBlocks), H(9 * 8), wn(8), om(1), tmp(2);
+  const int m = n < kArnoldiMax ? n : kArnoldiMax;
+  const int g = grid_for(n, 256, kRedBlocks);  // a few rows per thread; few partials to reduce
+  DevBuf<double> Q((size_t)n * m), W(n), w(n), dh(n), part((size_t)kArnSlots * g), H(9 * 8), wn(8), corr(8),
+      nrm2(1);
+  DevBuf<unsigned> ticket(1);
   AMG_CUDA(cudaMemsetAsync(H.p, 0, sizeof(double) * 72, s));
-  const unsigned gb = blocks_for(n);
-  const int gr = grid_for(n, 256, kRedBlocks);
-  AMG_COUNT(), k_arnoldi_start<<<gb, 256, 0, s>>>(n, h.p.seed, k, diag, Q.p, dh.p);
-  AMG_COUNT(), k_dot_part<<<gr, 256, 0, s>>>(n, Q.p, Q.p, part.p);
-  AMG_COUNT(), k_fin_sum<<<1, 1024, 0, s>>>(part.p, gr, tmp.p, 1);
-  AMG_COUNT(), k_div_dev<<<grid_for(n, 256), 256, 0, s>>>(n, Q.p, Q.p, tmp.p);
-  AMG_LAUNCH_CHECK();
+  AMG_CUDA(cudaMemsetAsync(ticket.p, 0, sizeof(unsigned), s));
+  AMG_COUNT(), k_arn_start<<<g, 256, 0, s>>>(n, h.p.seed, k, diag, W.p, dh.p, part.p, nrm2.p, ticket.p);
   for (int j = 0; j < m; ++j) {
-    const double *qj = Q.p + (size_t)j * n;
-    AMG_COUNT(), k_scaled_spmv<<<grid_for(n, 256), 256, 0, s>>>(n, L.rp, L.ci, L.val, dh.p, qj, w.p);
-    AMG_COUNT(), k_dot_part<<<gr, 256, 0, s>>>(n, w.p, w.p, part.p);
-    AMG_COUNT(), k_fin_sum<<<1, 1024, 0, s>>>(part.p, gr, wn.p + j, 1);
-    for (int l = 0; l <= j; ++l) {  // modified Gram-Schmidt
-      const double *ql = Q.p + (size_t)l * n;
-      AMG_COUNT(), k_dot_part<<<gr, 256, 0, s>>>(n, ql, w.p, part.p);
-      AMG_COUNT(), k_fin_sum<<<1, 1024, 0, s>>>(part.p, gr, H.p + l * 8 + j, 0);
-      AMG_COUNT(), k_axpy_neg_dev<<<grid_for(n, 256), 256, 0, s>>>(n, w.p, ql, H.p + l * 8 + j);
-    }
-    AMG_COUNT(), k_dot_part<<<gr, 256, 0, s>>>(n, w.p, w.p, part.p);
-    AMG_COUNT(), k_fin_sum<<<1, 1024, 0, s>>>(part.p, gr, H.p + (j + 1) * 8 + j, 1);
-    if (j + 1 < m) AMG_COUNT(), k_div_dev<<<grid_for(n, 256), 256, 0, s>>>(n, Q.p + (size_t)(j + 1) * n, w.p, H.p + (j + 1) * 8 + j);
-    AMG_LAUNCH_CHECK();
+    AMG_COUNT(), k_arn_spmv<<<g, 256, 0, s>>>(n, j, L.rp, L.ci, L.val, dh.p, W.p, Q.p, w.p, part.p, nrm2.p, H.p,
+                                              wn.p, ticket.p);
+    AMG_COUNT(), k_arn_orth<<<g, 256, 0, s>>>(n, j, 0, Q.p, w.p, W.p, part.p, H.p, corr.p, nrm2.p, ticket.p);
+    AMG_COUNT(), k_arn_orth<<<g, 256, 0, s>>>(n, j, 1, Q.p, w.p, W.p, part.p, H.p, corr.p, nrm2.p, ticket.p);
   }
-  AMG_COUNT(), k_omega_from_H<<<1, 32, 0, s>>>(H.p, wn.p, m, om.p);
+  AMG_COUNT(), k_omega_from_H<<<1, 32, 0, s>>>(H.p, wn.p, m, omega_dev);
   AMG_LAUNCH_CHECK();
-  return read_scalar(om.p, s);
 }
 
 }  // namespace
@@ -1213,16 +1475,31 @@ void coarsen_all(Hierarchy &h, cudaStream_t s) {
     // Galerkin keyed sum: count, offsets, fill
     Cl.rp = h.arena.get<int32_t>((size_t)nc + 1);
     {  // one walk per coarse row into upper-bound slots, then compaction
-      DevBuf<int32_t> ccount(nc + 1), rlen(nc + 1), ub(nc + 1);
-      const int gw = grid_for((int64_t)nc * 32, 256, 152 * 64);
-      AMG_COUNT(), k_run_length<<<grid_for(nc, 256), 256, 0, s>>>(nc, L.aptr, L.amem, L.rp, rlen.p);
+      DevBuf<int32_t> ccount(nc + 1), rlen(nc + 1), ub(nc + 1), maxlen(1);
+      AMG_CUDA(cudaMemsetAsync(maxlen.p, 0, sizeof(int32_t), s));
+      AMG_COUNT(), k_run_length<<<grid_for(nc, 256), 256, 0, s>>>(nc, L.aptr, L.amem, L.rp, rlen.p, maxlen.p);
       AMG_LAUNCH_CHECK();
       exclusive_scan<int32_t, int32_t>(rlen.p, ub.p, nc, s);
+      const int32_t mx = read_scalar(maxlen.p, s);
       DevBuf<int32_t> tci(L.nnz + 1);
       DevBuf<double> tval(L.nnz + 1);
-      AMG_COUNT(), k_galerkin<true><<<gw, 256, 0, s>>>(nc, L.aptr, L.amem, L.rp, L.ci, L.val, agg, L.pw64,
-                                                       ccount.p, ub.p, tci.p, tval.p);
+      // shared-memory sort path sized by the longest run (one warp per coarse row)
+      const int32_t cap = std::max<int32_t>(32, std::min<int32_t>(mx, kGalCapMax));
+      int hbits = 1;
+      while ((1 << hbits) < 2 * cap) ++hbits;
+      const size_t per = (size_t)cap * 32 + ((size_t)8 << hbits);
+      const int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, kGalSmemBudget / per));
+      const size_t smem = per * wpb;
+      AMG_CUDA(cudaFuncSetAttribute(k_galerkin_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      AMG_COUNT(), k_galerkin_smem<<<grid_for(nc, wpb, 152 * 64), wpb * 32, smem, s>>>(
+          nc, cap, hbits, L.aptr, L.amem, L.rp, L.ci, L.val, agg, L.pw64, ccount.p, ub.p, tci.p, tval.p);
       AMG_LAUNCH_CHECK();
+      if (mx > cap) {  // runs longer than the cap: walked from global memory
+        const int gw = grid_for((int64_t)nc * 32, 256, 152 * 64);
+        AMG_COUNT(), k_galerkin<true><<<gw, 256, 0, s>>>(nc, L.aptr, L.amem, L.rp, L.ci, L.val, agg, L.pw64,
+                                                         ccount.p, ub.p, tci.p, tval.p, true);
+        AMG_LAUNCH_CHECK();
+      }
       int32_t cnnz = 0;
       exclusive_scan<int32_t, int32_t>(ccount.p, Cl.rp, nc, s, &cnnz);
       Cl.nnz = cnnz;
@@ -1242,8 +1519,20 @@ void coarsen_all(Hierarchy &h, cudaStream_t s) {
     DevBuf<double> diag(L.n);
     AMG_COUNT(), k_diag<<<blocks_for(L.n), 256, 0, s>>>(L.n, L.rp, L.ci, L.val, diag.p);
     AMG_LAUNCH_CHECK();
-    if (q < h.L - 1) L.omega = p.omega_mode == 0 ? estimate_omega(h, q, diag.p, s) : p.omega;
+    L.omega = p.omega;  // omega_mode 1; mode 0 reads the estimate back after the loop
+    if (q < h.L - 1 && p.omega_mode == 0) {
+      L.omega_dev = h.arena.get<double>(1);
+      estimate_omega(h, q, diag.p, L.omega_dev, s);
+    }
     make_row_data(h, L, diag.p, s);  // per-row smoother data in the vector type
+  }
+  {  // the estimated weights back to the host, one synchronisation for all levels
+    for (int q = 0; q < h.L - 1; ++q)
+      if (h.lev[q].omega_dev)
+        AMG_CUDA(cudaMemcpyAsync(h.host_pinned + q, h.lev[q].omega_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+    AMG_CUDA(cudaStreamSynchronize(s));
+    for (int q = 0; q < h.L - 1; ++q)
+      if (h.lev[q].omega_dev) h.lev[q].omega = h.host_pinned[q];
   }
 
   // ---- coarsest level: dense factorisation and inverse

@@ -889,10 +889,11 @@ __global__ void k_bfcg_fin(int32_t nsys, double *__restrict__ bslots, int *__res
 #undef BS
 
 template <class VT>
-__global__ void k_convert_row_data(int32_t n, const double *__restrict__ diag, double omega,
-                                   const double *__restrict__ pw64, VT *__restrict__ wd, VT *__restrict__ dinv,
-                                   VT *__restrict__ pw) {
+__global__ void k_convert_row_data(int32_t n, const double *__restrict__ diag, double omega_host,
+                                   const double *__restrict__ omega_dev, const double *__restrict__ pw64,
+                                   VT *__restrict__ wd, VT *__restrict__ dinv, VT *__restrict__ pw) {
   pdl_wait_and_trigger();
+  const double omega = omega_dev ? *omega_dev : omega_host;
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     wd[i] = (VT)(omega / diag[i]);
     dinv[i] = (VT)(1.0 / diag[i]);
@@ -1387,8 +1388,8 @@ void make_row_data_t(Hierarchy &h, Level &L, const double *diag, cudaStream_t s)
   L.wd = h.arena.get<VT>((size_t)L.n + 1);
   L.dinv = h.arena.get<VT>((size_t)L.n + 1);
   L.pw = h.arena.get<VT>((size_t)L.n + 1);
-  klaunch(k_convert_row_data<VT>, ew_grid(L.n), kThreads, s, L.n, diag, L.omega, L.pw64, (VT *)L.wd,
-                                                           (VT *)L.dinv, (VT *)L.pw);
+  klaunch(k_convert_row_data<VT>, ew_grid(L.n), kThreads, s, L.n, diag, L.omega, (const double *)L.omega_dev,
+          L.pw64, (VT *)L.wd, (VT *)L.dinv, (VT *)L.pw);
   AMG_LAUNCH_CHECK();
 }
 
