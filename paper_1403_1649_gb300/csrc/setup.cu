@@ -911,6 +911,55 @@ __global__ void __launch_bounds__(256) k_arn_spmv(int32_t n, int j, const int32_
   }
 }
 
+// step j, part 1 on a level with an FP64 SELL-32 copy of A (one warp per slice,
+// coalesced loads; the same sums in the same order as the CSR kernel above plus
+// zero terms of the padding)
+__global__ void __launch_bounds__(256) k_arn_spmv_sell(int32_t n, int32_t nslices, int j,
+                                                       const int64_t *__restrict__ sptr, const int32_t *__restrict__ scol,
+                                                       const double *__restrict__ sval, const double *__restrict__ dh,
+                                                       const double *__restrict__ W, double *__restrict__ Q,
+                                                       double *__restrict__ w, double *part, const double *nrm2,
+                                                       double *H, double *wn, unsigned *ticket) {
+  const double h = sqrt(*nrm2), sc = 1.0 / h;
+  double *qj = Q + (size_t)j * n;
+  const int lane = threadIdx.x & 31;
+  double v[kArnSlots] = {0.0};
+  for (int32_t sl = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); sl < nslices;
+       sl += gridDim.x * (blockDim.x >> 5)) {
+    const int64_t base = sptr[sl];
+    const int32_t width = (int32_t)((sptr[sl + 1] - base) >> 5);
+    double acc = 0.0;
+    for (int32_t e = 0; e < width; ++e) {
+      const int64_t at = base + 32 * (int64_t)e + lane;
+      const int32_t c = __ldcs(scol + at);
+      acc += __ldcs(sval + at) * (dh[c] * (sc * W[c]));
+    }
+    const int32_t i = sl * 32 + lane;
+    if (i < n) {
+      const double wi = dh[i] * acc, qi = sc * W[i];
+      qj[i] = qi;
+      w[i] = wi;
+#pragma unroll
+      for (int l = 0; l < kArnSlots; ++l) {
+        if (l < j) v[l] += Q[(size_t)l * n + i] * wi;
+        else if (l == j) v[l] += qi * wi;
+        else if (l == j + 1) v[l] += wi * wi;
+      }
+    }
+  }
+  arn_block_partials(v, j + 2, part);
+  if (arn_last_block(ticket)) {
+    __shared__ double tot[kArnSlots];
+    arn_totals(part, j + 2, tot);
+    if ((int)threadIdx.x <= j) H[threadIdx.x * 8 + j] = tot[threadIdx.x];
+    if ((int)threadIdx.x == j + 1) wn[j] = sqrt(tot[j + 1]);
+    if (threadIdx.x == 0) {
+      if (j > 0) H[j * 8 + (j - 1)] = h;
+      *ticket = 0;
+    }
+  }
+}
+
 // step j, parts 2 and 3 (classical Gram-Schmidt twice): w -= sum_l c_l q_l with
 // c = H[.][j] (pass 0) or the correction corr (pass 1).  Pass 0 ends with
 // corr_l = q_l . w; pass 1 adds corr to H[.][j], writes W = w and nrm2 = ||w||^2.
@@ -1317,15 +1366,24 @@ void estimate_omega(Hierarchy &h, int k, const double *diag, double *omega_dev, 
   const int32_t n = L.n;
   const int m = n < kArnoldiMax ? n : kArnoldiMax;
   const int g = grid_for(n, 256, kRedBlocks);  // a few rows per thread; few partials to reduce
-  DevBuf<double> Q((size_t)n * m), W(n), w(n), dh(n), part((size_t)kArnSlots * g), H(9 * 8), wn(8), corr(8),
-      nrm2(1);
+  DevBuf<double> Q((size_t)n * m), W(n), w(n), dh(n), part((size_t)kArnSlots * kRedBlocks), H(9 * 8), wn(8),
+      corr(8), nrm2(1);
+  // an FP64 SELL copy of every entry: level 0 always, every level in FP64 mode
+  const int64_t *sp64 = k == 0 ? L.sptr64 : (h.p.precision == AMG_PREC_F64 ? L.sptr : nullptr);
+  const int32_t *sc64 = k == 0 ? L.scol64 : L.scol;
+  const double *sv64 = k == 0 ? L.sval64 : static_cast<const double *>(L.sval);
+  const int gs = grid_for(L.nslices, 8, kRedBlocks);
   DevBuf<unsigned> ticket(1);
   AMG_CUDA(cudaMemsetAsync(H.p, 0, sizeof(double) * 72, s));
   AMG_CUDA(cudaMemsetAsync(ticket.p, 0, sizeof(unsigned), s));
   AMG_COUNT(), k_arn_start<<<g, 256, 0, s>>>(n, h.p.seed, k, diag, W.p, dh.p, part.p, nrm2.p, ticket.p);
   for (int j = 0; j < m; ++j) {
-    AMG_COUNT(), k_arn_spmv<<<g, 256, 0, s>>>(n, j, L.rp, L.ci, L.val, dh.p, W.p, Q.p, w.p, part.p, nrm2.p, H.p,
-                                              wn.p, ticket.p);
+    if (sp64)
+      AMG_COUNT(), k_arn_spmv_sell<<<gs, 256, 0, s>>>(n, L.nslices, j, sp64, sc64, sv64, dh.p, W.p, Q.p, w.p, part.p,
+                                                      nrm2.p, H.p, wn.p, ticket.p);
+    else
+      AMG_COUNT(), k_arn_spmv<<<g, 256, 0, s>>>(n, j, L.rp, L.ci, L.val, dh.p, W.p, Q.p, w.p, part.p, nrm2.p, H.p,
+                                                wn.p, ticket.p);
     AMG_COUNT(), k_arn_orth<<<g, 256, 0, s>>>(n, j, 0, Q.p, w.p, W.p, part.p, H.p, corr.p, nrm2.p, ticket.p);
     AMG_COUNT(), k_arn_orth<<<g, 256, 0, s>>>(n, j, 1, Q.p, w.p, W.p, part.p, H.p, corr.p, nrm2.p, ticket.p);
   }
