@@ -165,6 +165,23 @@ int amg_setup_batch(int32_t nsys, const amg_csr *As, const amg_params *params, v
 int amg_solve_batch(amg_hierarchy *h, const double *b, double *x, double tol, int32_t *iters, double *relres,
                     void *stream);
 
+/* Values-only re-setup (Sec. 3.1: the pattern of the hierarchy depends only on
+ * the aggregates and the pattern of A_0, so the Galerkin products can be
+ * repeated from stored summation plans, as between Newton steps).
+ * val: the nnz new values of A_0 (host or device), in the CSR order of the
+ * matrix given to amg_setup (for a batch: the systems' values concatenated in
+ * system order); the sparsity pattern must be unchanged.  The aggregates, P and
+ * every coarse pattern are kept; the coarse values are recomputed from the
+ * plans, bit-identical to a full setup that finds the same aggregates; then
+ * omega, the smoother data and the coarsest factorisation are refilled in
+ * place (captured solves stay valid).  Polynomial coefficients set with
+ * amg_set_poly or amg_apply_learned_smoother are kept: apply them again to
+ * follow the new values.  The device time is reported as setup_ms.
+ * Errors: AMG_ERR_BAD_INPUT (zero diagonal or non-finite value);
+ * AMG_ERR_UNSUPPORTED (a level whose aggregate runs exceeded 4096 terms has no
+ * plan); AMG_ERR_SETUP (coarsest matrix not positive definite). */
+int amg_resetup_values(amg_hierarchy *h, const double *val, void *stream);
+
 /* One application of the preconditioner, x = M b (Alg. 5 at level 0 from a
  * zero initial guess).  b, x: n doubles, host or device. */
 int amg_precond(amg_hierarchy *h, const double *b, double *x, void *stream);

@@ -78,6 +78,7 @@ def lib() -> C.CDLL:
         L.amg_setup.argtypes = [C.POINTER(amg_csr), C.POINTER(amg_params), vp, C.POINTER(vp)]
         L.amg_solve.argtypes = [vp, vp, vp, dbl, C.POINTER(i32), vp, vp]
         L.amg_precond.argtypes = [vp, vp, vp, vp]
+        L.amg_resetup_values.argtypes = [vp, vp, vp]
         L.amg_spmv.argtypes = [vp, i32, vp, vp, vp]
         L.amg_set_poly.argtypes = [vp, i32, vp, vp]
         L.amg_hierarchy_info.argtypes = [vp, vp, i32, C.POINTER(i32)]
@@ -102,7 +103,7 @@ def lib() -> C.CDLL:
         L.amg_validate_hierarchy.argtypes = [vp]
         L.amg_validate_hierarchy.restype = C.c_int
         L.amg_solve_batch.restype = C.c_int
-        for name in ("amg_setup", "amg_solve", "amg_precond", "amg_spmv", "amg_set_poly", "amg_hierarchy_info",
+        for name in ("amg_setup", "amg_solve", "amg_precond", "amg_resetup_values", "amg_spmv", "amg_set_poly", "amg_hierarchy_info",
                      "amg_export_level", "amg_last_solve_info", "amg_features", "amg_mlp_forward",
                      "amg_mlp_backward", "amg_twogrid_loss", "amg_train_smoother", "amg_apply_learned_smoother"):
             getattr(L, name).restype = C.c_int
@@ -209,6 +210,13 @@ def amg_solve(h, b, x, tol: float, max_iter: int | None = None, stream=None, all
                          stream if stream is not None else _stream(b, x))
     _check(rc, allow)
     return rc, it.value, hist[:it.value + 1].copy()
+
+
+def amg_resetup_values(h, val, stream=None) -> None:
+    """Values-only re-setup with new values of A_0 (same pattern, CSR order)."""
+    if isinstance(val, np.ndarray):
+        val = np.ascontiguousarray(val, np.float64)
+    _check(lib().amg_resetup_values(h, _ptr(val), stream if stream is not None else _stream(val)))
 
 
 def amg_precond(h, b, x, stream=None) -> None:

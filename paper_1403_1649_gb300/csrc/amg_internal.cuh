@@ -123,6 +123,11 @@ struct Level {
   // transfer
   int32_t *agg = nullptr, *aptr = nullptr, *amem = nullptr;
   double *pw64 = nullptr;  // P weights in FP64 (exported)
+  // summation plan of the Galerkin product into level k+1 (Sec. 3.1): coarse
+  // nonzero q sums the terms gptr[q] .. gptr[q+1]-1, term t being
+  // (P_i * A_ij) * P_j with fine CSR position gpos[t] and fine row i = grow[t]
+  bool plan = false;
+  int32_t *gpos = nullptr, *grow = nullptr, *gptr = nullptr;
   // solve-phase matrix (SELL-32).  FP64: every entry of A.  FP32 / BF16: the
   // off-diagonal entries only, rounded, with the diagonal in sdiag (FP32) as
   // a_ii plus the rounding errors of the row's off-diagonals, so that row sums
@@ -232,6 +237,8 @@ PtrKind pointer_kind(const void *p);
 void build_hierarchy(Hierarchy &h, const amg_csr &A, cudaStream_t s);
 void build_hierarchy_batch(Hierarchy &h, int32_t nsys, const amg_csr *As, cudaStream_t s);
 void coarsen_all(Hierarchy &h, cudaStream_t s);
+void finish_levels(Hierarchy &h, cudaStream_t s, bool fresh);
+void resetup_values(Hierarchy &h, const double *val0, cudaStream_t s);
 // solve.cu: per-row smoother data (omega/A_ii, 1/A_ii, P weights) in the vector type
 void make_row_data(Hierarchy &h, Level &L, const double *diag, cudaStream_t s);
 // solve.cu

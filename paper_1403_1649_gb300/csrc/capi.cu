@@ -274,6 +274,25 @@ int amg_solve_batch(amg_hierarchy *H, const double *b, double *x, double tol, in
   });
 }
 
+int amg_resetup_values(amg_hierarchy *H, const double *val, void *stream) {
+  if (!H || !val) {
+    amg::set_last_error("amg_resetup_values: null argument");
+    return AMG_ERR_BAD_INPUT;
+  }
+  return guarded([&]() {
+    enter(H, stream);
+    AMG_CUDA(cudaEventRecord(H->t0, H->stream));
+    amg::resetup_values(H->h, val, H->stream);
+    AMG_CUDA(cudaEventRecord(H->t1, H->stream));
+    AMG_CUDA(cudaEventSynchronize(H->t1));
+    float ms = 0.f;
+    AMG_CUDA(cudaEventElapsedTime(&ms, H->t0, H->t1));
+    H->h.info.setup_ms = ms;
+    leave(H, stream);
+    return AMG_OK;
+  });
+}
+
 int amg_precond(amg_hierarchy *H, const double *b, double *x, void *stream) {
   if (!H || !b || !x) return AMG_ERR_BAD_INPUT;
   return guarded([&]() {

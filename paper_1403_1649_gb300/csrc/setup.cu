@@ -567,21 +567,24 @@ __global__ void __launch_bounds__(256) k_galerkin_smem(
     int32_t nc, int32_t cap, int32_t hbits, const int32_t *__restrict__ aptr, const int32_t *__restrict__ amem,
     const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ val,
     const int32_t *__restrict__ agg, const double *__restrict__ pw, int32_t *__restrict__ ccount,
-    const int32_t *__restrict__ crp, int32_t *__restrict__ cci, double *__restrict__ cval) {
+    const int32_t *__restrict__ crp, int32_t *__restrict__ cci, double *__restrict__ cval,
+    int32_t *__restrict__ gpos, int32_t *__restrict__ grow, int32_t *__restrict__ gseg) {
   extern __shared__ __align__(16) unsigned char gal_sm[];
   const int lane = threadIdx.x & 31;
   const int wid = threadIdx.x >> 5;
   const int wpb = blockDim.x >> 5;
   const int32_t hsize = 1 << hbits, hmask = hsize - 1;
   const unsigned lt = (1u << lane) - 1u;
-  const size_t per = (size_t)cap * 32 + (size_t)hsize * 8;
+  const size_t per = (size_t)cap * 40 + (size_t)hsize * 8;
   double *sV = reinterpret_cast<double *>(gal_sm + per * wid);  // staged terms
   double *sW = sV + cap;                                       // terms grouped by column
   int32_t *sJ = reinterpret_cast<int32_t *>(sW + cap);          // column of each term, then its rank
   int32_t *sKey = sJ + cap;                                     // distinct columns, table order
   int32_t *sCnt = sKey + cap;                                   // per rank: count, then segment end
   int32_t *sAux = sCnt + cap;                                   // member offsets, then sorted columns
-  int32_t *hK = sAux + cap;
+  int32_t *sPos = sAux + cap;                                   // fine CSR position of each staged term
+  int32_t *sMem = sPos + cap;                                   // member (run-local) of each staged term
+  int32_t *hK = sMem + cap;
   int32_t *hR = hK + hsize;
   auto slot_of = [&](int32_t J) {
     uint32_t hh = ((uint32_t)J * 2654435761u) >> (32 - hbits);
@@ -624,6 +627,8 @@ __global__ void __launch_bounds__(256) k_galerkin_smem(
       const int32_t j = ci[p];
       sJ[e] = agg[j];
       sV[e] = __dmul_rn(__dmul_rn(pw[i], val[p]), pw[j]);
+      sPos[e] = p;
+      sMem[e] = i;
     }
     for (int32_t t = lane; t < hsize; t += 32) hK[t] = -1;
     __syncwarp();
@@ -683,7 +688,14 @@ __global__ void __launch_bounds__(256) k_galerkin_smem(
       const int32_t e = e0 + lane;
       const int32_t r = e < total ? sJ[e] : -1;
       const unsigned grp = __match_any_sync(0xffffffffu, r);
-      if (r >= 0) sW[sCnt[r] + __popc(grp & lt)] = sV[e];
+      if (r >= 0) {
+        const int32_t t = sCnt[r] + __popc(grp & lt);
+        sW[t] = sV[e];
+        if (gpos) {  // the summation plan: term t of the row's run, in sorted order
+          gpos[crp[I] + t] = sPos[e];
+          grow[crp[I] + t] = sMem[e];
+        }
+      }
       __syncwarp();
       if (r >= 0 && (grp & lt) == 0) sCnt[r] += __popc(grp);
       __syncwarp();
@@ -695,6 +707,7 @@ __global__ void __launch_bounds__(256) k_galerkin_smem(
       for (int32_t t = a + 1; t < b; ++t) sum = __dadd_rn(sum, sW[t]);
       cci[crp[I] + q] = sAux[q];
       cval[crp[I] + q] = sum;
+      if (gseg) gseg[crp[I] + q] = crp[I] + a;  // first term of this coarse entry in the plan
     }
     if (lane == 0) ccount[I] = d;
     __syncwarp();
@@ -711,6 +724,36 @@ __global__ void k_compact_rows(int32_t nc, const int32_t *__restrict__ ub, const
       cci[crp[I] + t] = tci[ub[I] + t];
       cval[crp[I] + t] = tval[ub[I] + t];
     }
+  }
+}
+
+// plan: segment start of row I's coarse entries, from upper-bound slots to
+// compact positions; gptr[cnnz] = number of fine nonzeros
+__global__ void k_compact_plan(int32_t nc, const int32_t *__restrict__ ub, const int32_t *__restrict__ crp,
+                               const int32_t *__restrict__ tseg, int32_t *__restrict__ gptr, int32_t nnz_fine) {
+  for (int32_t I = blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += gridDim.x * blockDim.x) {
+    const int32_t len = crp[I + 1] - crp[I];
+    for (int32_t t = 0; t < len; ++t) gptr[crp[I] + t] = tseg[ub[I] + t];
+    if (I == nc - 1) gptr[crp[nc]] = nnz_fine;
+  }
+}
+
+// values-only Galerkin product from the plan: the same terms in the same order
+// as the full product, so the coarse values are bit-identical to a full setup
+// that finds the same aggregates
+__global__ void k_galerkin_values(int32_t cnnz, const int32_t *__restrict__ gptr, const int32_t *__restrict__ gpos,
+                                  const int32_t *__restrict__ grow, const int32_t *__restrict__ ci,
+                                  const double *__restrict__ val, const double *__restrict__ pw,
+                                  double *__restrict__ cval) {
+  for (int32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < cnnz; q += gridDim.x * blockDim.x) {
+    const int32_t a = gptr[q], b = gptr[q + 1];
+    double sum = 0.0;
+    for (int32_t t = a; t < b; ++t) {
+      const int32_t pp = gpos[t];
+      const double term = __dmul_rn(__dmul_rn(pw[grow[t]], val[pp]), pw[ci[pp]]);
+      sum = t == a ? term : __dadd_rn(sum, term);
+    }
+    cval[q] = sum;
   }
 }
 
@@ -1311,7 +1354,9 @@ Coarsening coarsen_level(Hierarchy &h, int k, cudaStream_t s, int32_t *agg_out, 
 
 // SELL-32 of level L: the preconditioner's matrix in its precision and, on
 // level 0, every entry in FP64 for the outer iteration
-void build_solve_matrix(Hierarchy &h, Level &L, cudaStream_t s) {
+// fresh: lay out and allocate; otherwise refill the values of the existing
+// layout (values-only re-setup, same pattern)
+void build_solve_matrix(Hierarchy &h, Level &L, cudaStream_t s, bool fresh) {
   const int32_t n = L.n;
   L.nslices = (n + kSlice - 1) / kSlice;
   const unsigned g = blocks_for((int64_t)L.nslices * 32);
@@ -1324,30 +1369,32 @@ void build_solve_matrix(Hierarchy &h, Level &L, cudaStream_t s) {
     scol = h.arena.get<int32_t>(entries);
   };
   const bool split = h.p.precision != AMG_PREC_F64;
-  layout(split, L.sptr, L.scol, L.sell_entries);
+  if (fresh) layout(split, L.sptr, L.scol, L.sell_entries);
   const int64_t entries = L.sell_entries;
-  if (split) L.sdiag = h.arena.get<float>(n);
+  if (fresh && split) L.sdiag = h.arena.get<float>(n);
   switch (h.p.precision) {
     case AMG_PREC_F64:
-      L.sval = h.arena.get<double>(entries);
+      if (fresh) L.sval = h.arena.get<double>(entries);
       AMG_COUNT(), k_build_sell<double><<<g, 256, 0, s>>>(n, L.nslices, L.rp, L.ci, L.val, L.sptr, L.scol,
                                                           (double *)L.sval, nullptr);
       break;
     case AMG_PREC_F32:
-      L.sval = h.arena.get<float>(entries);
+      if (fresh) L.sval = h.arena.get<float>(entries);
       AMG_COUNT(), k_build_sell<float><<<g, 256, 0, s>>>(n, L.nslices, L.rp, L.ci, L.val, L.sptr, L.scol,
                                                          (float *)L.sval, L.sdiag);
       break;
     default:
-      L.sval = h.arena.get<__nv_bfloat16>(entries);
+      if (fresh) L.sval = h.arena.get<__nv_bfloat16>(entries);
       AMG_COUNT(), k_build_sell<__nv_bfloat16><<<g, 256, 0, s>>>(n, L.nslices, L.rp, L.ci, L.val, L.sptr, L.scol,
                                                                  (__nv_bfloat16 *)L.sval, L.sdiag);
   }
   AMG_LAUNCH_CHECK();
   if (&L != &h.lev[0]) return;
   if (split) {
-    layout(false, L.sptr64, L.scol64, L.sell64_entries);
-    L.sval64 = h.arena.get<double>(L.sell64_entries);
+    if (fresh) {
+      layout(false, L.sptr64, L.scol64, L.sell64_entries);
+      L.sval64 = h.arena.get<double>(L.sell64_entries);
+    }
     AMG_COUNT(), k_build_sell<double><<<g, 256, 0, s>>>(n, L.nslices, L.rp, L.ci, L.val, L.sptr64, L.scol64,
                                                         L.sval64, nullptr);
     AMG_LAUNCH_CHECK();
@@ -1545,12 +1592,21 @@ void coarsen_all(Hierarchy &h, cudaStream_t s) {
       const int32_t cap = std::max<int32_t>(32, std::min<int32_t>(mx, kGalCapMax));
       int hbits = 1;
       while ((1 << hbits) < 2 * cap) ++hbits;
-      const size_t per = (size_t)cap * 32 + ((size_t)8 << hbits);
+      const size_t per = (size_t)cap * 40 + ((size_t)8 << hbits);
       const int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, kGalSmemBudget / per));
       const size_t smem = per * wpb;
       AMG_CUDA(cudaFuncSetAttribute(k_galerkin_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      // the summation plan for values-only re-setup (Sec. 3.1): recorded when every
+      // run fits the shared-memory path
+      L.plan = mx <= cap;
+      DevBuf<int32_t> tseg(L.plan ? L.nnz + 1 : 1);
+      if (L.plan) {
+        L.gpos = h.arena.get<int32_t>((size_t)L.nnz);
+        L.grow = h.arena.get<int32_t>((size_t)L.nnz);
+      }
       AMG_COUNT(), k_galerkin_smem<<<grid_for(nc, wpb, 152 * 64), wpb * 32, smem, s>>>(
-          nc, cap, hbits, L.aptr, L.amem, L.rp, L.ci, L.val, agg, L.pw64, ccount.p, ub.p, tci.p, tval.p);
+          nc, cap, hbits, L.aptr, L.amem, L.rp, L.ci, L.val, agg, L.pw64, ccount.p, ub.p, tci.p, tval.p,
+          L.plan ? L.gpos : nullptr, L.plan ? L.grow : nullptr, L.plan ? tseg.p : nullptr);
       AMG_LAUNCH_CHECK();
       if (mx > cap) {  // runs longer than the cap: walked from global memory
         const int gw = grid_for((int64_t)nc * 32, 256, 152 * 64);
@@ -1565,21 +1621,34 @@ void coarsen_all(Hierarchy &h, cudaStream_t s) {
       Cl.val = h.arena.get<double>(cnnz);
       AMG_COUNT(), k_compact_rows<<<grid_for(nc, 256), 256, 0, s>>>(nc, ub.p, Cl.rp, tci.p, tval.p, Cl.ci, Cl.val);
       AMG_LAUNCH_CHECK();
+      if (L.plan) {
+        L.gptr = h.arena.get<int32_t>((size_t)cnnz + 1);
+        AMG_COUNT(), k_compact_plan<<<grid_for(nc, 256), 256, 0, s>>>(nc, ub.p, Cl.rp, tseg.p, L.gptr,
+                                                                      (int32_t)L.nnz);
+        AMG_LAUNCH_CHECK();
+      }
     }
     ++k;
   }
   h.L = k + 1;
 
-  // ---- solve-phase data of every level
+  finish_levels(h, s, true);
+}
+
+// Solve-phase data of every level (SELL values, diagonal, omega, per-row data)
+// and the coarsest factorisation.  fresh = false refills the existing buffers in
+// place (values-only re-setup): captured solve graphs stay valid.
+void finish_levels(Hierarchy &h, cudaStream_t s, bool fresh) {
+  const amg_params &p = h.p;
   for (int q = 0; q < h.L; ++q) {
     Level &L = h.lev[q];
-    build_solve_matrix(h, L, s);
+    build_solve_matrix(h, L, s, fresh);
     DevBuf<double> diag(L.n);
     AMG_COUNT(), k_diag<<<blocks_for(L.n), 256, 0, s>>>(L.n, L.rp, L.ci, L.val, diag.p);
     AMG_LAUNCH_CHECK();
     L.omega = p.omega;  // omega_mode 1; mode 0 reads the estimate back after the loop
     if (q < h.L - 1 && p.omega_mode == 0) {
-      L.omega_dev = h.arena.get<double>(1);
+      if (!L.omega_dev) L.omega_dev = h.arena.get<double>(1);
       estimate_omega(h, q, diag.p, L.omega_dev, s);
     }
     make_row_data(h, L, diag.p, s);  // per-row smoother data in the vector type
@@ -1607,8 +1676,10 @@ void coarsen_all(Hierarchy &h, cudaStream_t s) {
       throw Error{AMG_ERR_SETUP, "a system's coarsest level has " + std::to_string(bmax) + " unknowns"};
     h.bmax = bmax;
     h.nL = Lc.n;
-    h.binv = h.arena.get<double>((size_t)boff[h.nsys]);
-    h.binv_off = h.arena.get<int64_t>(h.nsys + 1);
+    if (fresh) {
+      h.binv = h.arena.get<double>((size_t)boff[h.nsys]);
+      h.binv_off = h.arena.get<int64_t>(h.nsys + 1);
+    }
     AMG_CUDA(cudaMemcpyAsync(h.binv_off, boff.data(), sizeof(int64_t) * (h.nsys + 1), cudaMemcpyHostToDevice, s));
     DevBuf<double> dense((size_t)boff[h.nsys]);
     DevBuf<int> err(1);
@@ -1625,7 +1696,7 @@ void coarsen_all(Hierarchy &h, cudaStream_t s) {
     throw Error{AMG_ERR_SETUP, "coarsest level has " + std::to_string(Lc.n) + " unknowns (limit " +
                                    std::to_string(kMaxDense) + "); coarsening stalled"};
   h.nL = Lc.n;
-  h.coarse_inv = h.arena.get<double>((size_t)Lc.n * Lc.n);
+  if (fresh) h.coarse_inv = h.arena.get<double>((size_t)Lc.n * Lc.n);
   {
     DevBuf<double> dense((size_t)Lc.n * Lc.n);
     DevBuf<int> err(1);
@@ -1636,6 +1707,34 @@ void coarsen_all(Hierarchy &h, cudaStream_t s) {
     AMG_LAUNCH_CHECK();
     if (read_scalar(err.p, s)) throw Error{AMG_ERR_SETUP, "coarsest level matrix is not positive definite"};
   }
+}
+
+// Values-only re-setup (Sec. 3.1): A_0 keeps its pattern and takes new values;
+// the aggregates and P are kept (P depends on the near-null vector only), the
+// coarse values come from the stored summation plans, then every level's solve
+// data and the coarsest factorisation are refilled in place.
+void resetup_values(Hierarchy &h, const double *val0, cudaStream_t s) {
+  for (int k = 0; k + 1 < h.L; ++k)
+    if (!h.lev[k].plan)
+      throw Error{AMG_ERR_UNSUPPORTED, "level " + std::to_string(k) +
+                                           " has aggregate runs too long for a stored Galerkin plan"};
+  Level &L0 = h.lev[0];
+  const cudaMemcpyKind kind = pointer_kind(val0) == PTR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  AMG_CUDA(cudaMemcpyAsync(L0.val, val0, sizeof(double) * (size_t)L0.nnz, kind, s));
+  {
+    DevBuf<int> err(1);
+    AMG_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+    AMG_COUNT(), k_check_csr<<<blocks_for(L0.n), 256, 0, s>>>(L0.n, L0.nnz, L0.rp, L0.ci, L0.val, err.p);
+    AMG_LAUNCH_CHECK();
+    if (read_scalar(err.p, s)) throw Error{AMG_ERR_BAD_INPUT, "new values: zero diagonal or non-finite value"};
+  }
+  for (int k = 0; k + 1 < h.L; ++k) {
+    Level &L = h.lev[k], &C = h.lev[k + 1];
+    AMG_COUNT(), k_galerkin_values<<<grid_for(C.nnz, 256, 152 * 32), 256, 0, s>>>(
+        (int32_t)C.nnz, L.gptr, L.gpos, L.grow, L.ci, L.val, L.pw64, C.val);
+    AMG_LAUNCH_CHECK();
+  }
+  finish_levels(h, s, false);
 }
 
 }  // namespace amg

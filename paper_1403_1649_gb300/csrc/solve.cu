@@ -1385,9 +1385,11 @@ void prepare_t(Hierarchy &h, cudaStream_t s) {
 
 template <class VT>
 void make_row_data_t(Hierarchy &h, Level &L, const double *diag, cudaStream_t s) {
-  L.wd = h.arena.get<VT>((size_t)L.n + 1);
-  L.dinv = h.arena.get<VT>((size_t)L.n + 1);
-  L.pw = h.arena.get<VT>((size_t)L.n + 1);
+  if (!L.wd) {  // refilled in place by a values-only re-setup
+    L.wd = h.arena.get<VT>((size_t)L.n + 1);
+    L.dinv = h.arena.get<VT>((size_t)L.n + 1);
+    L.pw = h.arena.get<VT>((size_t)L.n + 1);
+  }
   klaunch(k_convert_row_data<VT>, ew_grid(L.n), kThreads, s, L.n, diag, L.omega, (const double *)L.omega_dev,
           L.pw64, (VT *)L.wd, (VT *)L.dinv, (VT *)L.pw);
   AMG_LAUNCH_CHECK();
