@@ -198,6 +198,7 @@ int amg_spmv(amg_hierarchy *h, int32_t level, const void *x, void *y, void *stre
  * host or device doubles): the smoother applies
  * x += sum_q diag(c_q) (D^-1 A)^q D^-1 r before the coarse correction and the
  * transposed polynomial after it.  Takes effect when params.smoother == 1.
+ * coef = NULL returns the level to damped Jacobi.
  * The paper lists polynomial smoothers as future work (Sec. 5). */
 int amg_set_poly(amg_hierarchy *h, int32_t level, const double *coef, void *stream);
 
@@ -263,9 +264,13 @@ int amg_twogrid_loss(amg_hierarchy *h, const double *coef, int32_t nvec, uint64_
 int amg_train_smoother(amg_hierarchy *const *hs, int32_t nh, int32_t steps, double lr, int32_t nvec,
                        uint64_t seed, float *w, double *loss_hist, void *stream);
 
-/* Evaluate the MLP (binary16 weights w16, host or device) on every level but
- * the coarsest and install the resulting per-row coefficients; turns the
- * polynomial smoother on. */
+/* Evaluate the MLP (binary16 weights w16, host or device) on the rows of
+ * level 0, the level whose two-grid factor the network is trained on, and
+ * install the resulting per-row coefficients there; turns the polynomial
+ * smoother on.  The coarser levels keep damped Jacobi (measured: on the
+ * FEM and batched variable-coefficient problems the network applied to coarse
+ * levels costs more SpMVs per cycle and needs as many or more iterations);
+ * amg_features + amg_mlp_forward + amg_set_poly install it on any level. */
 int amg_apply_learned_smoother(amg_hierarchy *h, const uint16_t *w16, void *stream);
 
 /* Sizes per level.  levels (host, capacity cap) may be NULL to query *nlevels. */

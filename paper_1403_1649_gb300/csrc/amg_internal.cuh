@@ -148,6 +148,7 @@ struct Level {
   int64_t sell64_entries = 0;
   // solve-phase vectors and per-row data in the vector type
   void *wd = nullptr, *dinv = nullptr, *pw = nullptr, *poly = nullptr;
+  bool poly_off = false;  // the level's polynomial was cleared: damped Jacobi
   void *r = nullptr, *bc = nullptr, *xc = nullptr, *c = nullptr, *v = nullptr, *rt = nullptr,
        *d = nullptr, *w = nullptr, *tmp = nullptr, *u0 = nullptr, *u1 = nullptr;
   double *slots = nullptr;    // kNumSlots doubles
@@ -156,6 +157,7 @@ struct Level {
   // batched systems (block-diagonal hierarchy): system s owns rows
   // [sys_off[s], sys_off[s+1]) on every level; row tiles never cross systems
   int32_t *sys_off = nullptr, *sys_of = nullptr;
+  unsigned char *slive = nullptr;  // per slice: some system in it still iterates
   std::vector<int32_t> sys_off_host;
   int32_t ntiles = 0;
   int32_t *tile_row = nullptr, *sys_tile = nullptr;  // ntiles+1 row starts; nsys+1 first tiles

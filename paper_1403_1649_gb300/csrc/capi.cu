@@ -327,8 +327,8 @@ int amg_spmv(amg_hierarchy *H, int32_t level, const void *x, void *y, void *stre
 }
 
 int amg_set_poly(amg_hierarchy *H, int32_t level, const double *coef, void *stream) {
-  if (!H || !coef || level < 0 || level >= H->h.L - 1) {
-    amg::set_last_error("amg_set_poly: bad level (the coarsest level has no smoother) or null pointer");
+  if (!H || level < 0 || level >= H->h.L - 1) {
+    amg::set_last_error("amg_set_poly: bad level (the coarsest level has no smoother) or null hierarchy");
     return AMG_ERR_BAD_INPUT;
   }
   return guarded([&]() {

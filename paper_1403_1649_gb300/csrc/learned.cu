@@ -466,8 +466,10 @@ void mlp_backward_fixed(int32_t n, const float *w, const float *feat, const floa
   AMG_LAUNCH_CHECK();
 }
 
+// The network is trained on the two-grid factor of level 0 and installed there;
+// coarser levels keep damped Jacobi.
 void apply_learned(Hierarchy &h, const uint16_t *w16_dev, cudaStream_t s) {
-  for (int k = 0; k < h.L - 1; ++k) {
+  for (int k = 0; k < std::min(h.L - 1, 1); ++k) {
     Level &L = h.lev[k];
     DevBuf<float> feat((size_t)L.n * NF), out((size_t)L.n * NO);
     DevBuf<double> coef((size_t)L.n * 3);

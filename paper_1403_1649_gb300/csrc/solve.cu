@@ -36,6 +36,7 @@ struct SellArgs {
   const int32_t *scol;
   const void *sval;
   const float *sdiag;  // split diagonal (reduced precision), else null
+  const unsigned char *live;  // batch: 0 for slices whose systems all stopped (skipped); else null
   const VT *x;    // SpMV input
   VT *out;        // output vector
   const VT *rhs;  // right-hand side (residual / smoothing epilogues)
@@ -106,6 +107,23 @@ __device__ __forceinline__ double dot_operand(int op, double x, double y, double
   return op == OP_X ? x : (op == OP_Y ? y : (op == OP_U1 ? u1 : u2));
 }
 
+// batch: live[sl] = 1 when some system with rows in slice sl still iterates.
+// Rows of a stopped system are only ever read by that system, so its work can
+// be skipped; a restarted system starts again from its recomputed residual.
+__global__ void k_slice_live(int32_t n, int32_t nslices, const int32_t *__restrict__ sys,
+                             const int *__restrict__ bact, unsigned char *__restrict__ live) {
+  pdl_wait_and_trigger();
+  for (int32_t sl = blockIdx.x * blockDim.x + threadIdx.x; sl < nslices; sl += gridDim.x * blockDim.x) {
+    unsigned char v = 0;
+    for (int32_t q = sys[sl * 32]; q <= sys[min(sl * 32 + 31, n - 1)]; ++q)
+      if (bact[q]) {
+        v = 1;
+        break;
+      }
+    live[sl] = v;
+  }
+}
+
 // Resident blocks per SM of k_sell: FP32 vectors fit in 40 registers (6 blocks
 // of 256 threads), FP64 vectors need 64 (4 blocks).
 template <class VT>
@@ -113,7 +131,9 @@ constexpr int sell_min_blocks() { return sizeof(VT) == 4 ? 6 : 4; }
 
 // DOTS: the launch fuses inner products (compiled only where used, so that the
 // plain SpMV does not hold their accumulators in registers)
-template <class MV, class VT, int EPI, bool DOTS>
+// GATE: a batch's launch, skipping slices whose systems have all stopped
+// (compiled only into the batch instantiations)
+template <class MV, class VT, int EPI, bool DOTS, bool GATE>
 __global__ void __launch_bounds__(kThreads, sell_min_blocks<VT>()) k_sell(SellArgs<VT> a) {
   pdl_wait_and_trigger();
   if (a.pred && *a.pred == 0) return;
@@ -124,6 +144,7 @@ __global__ void __launch_bounds__(kThreads, sell_min_blocks<VT>()) k_sell(SellAr
   // split-off diagonal in one step, at 40 registers), 8 with FP64
   constexpr int U = sizeof(VT) == 4 ? 6 : 8;
   for (int32_t sl = blockIdx.x * kWarps + (threadIdx.x >> 5); sl < a.nslices; sl += gridDim.x * kWarps) {
+    if (GATE && !a.live[sl]) continue;
     const int32_t row = sl * 32 + lane;
     const int64_t base = a.sptr[sl];
     const int32_t width = (int32_t)((a.sptr[sl + 1] - base) >> 5);
@@ -193,10 +214,11 @@ __global__ void __launch_bounds__(kThreads, sell_min_blocks<VT>()) k_sell(SellAr
 // out = wd * rhs: damped Jacobi from a zero initial guess
 template <class VT>
 __global__ void k_scale(int32_t n, VT *__restrict__ out, const VT *__restrict__ wd, const VT *__restrict__ rhs,
-                        const int *pred) {
+                        const int *pred, const int32_t *sys, const int *bact) {
   pdl_wait_and_trigger();
   if (pred && *pred == 0) return;
-  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = wd[i] * rhs[i];
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    if (!bact || bact[sys[i]]) out[i] = wd[i] * rhs[i];
 }
 
 // r_{k+1}(I) = sum_{i in G_I} P(i, I) r_k(i) in ascending fine index; also the
@@ -204,10 +226,12 @@ __global__ void k_scale(int32_t n, VT *__restrict__ out, const VT *__restrict__ 
 template <class VT>
 __global__ void k_restrict(int32_t nc, const int32_t *__restrict__ aptr, const int32_t *__restrict__ amem,
                            const VT *__restrict__ pw, const VT *__restrict__ r, VT *__restrict__ bc,
-                           const VT *__restrict__ wdc, VT *__restrict__ x0c, const int *pred) {
+                           const VT *__restrict__ wdc, VT *__restrict__ x0c, const int *pred,
+                           const int32_t *sysc, const int *bact) {
   pdl_wait_and_trigger();
   if (pred && *pred == 0) return;
   for (int32_t I = blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += gridDim.x * blockDim.x) {
+    if (bact && !bact[sysc[I]]) continue;
     VT s = VT(0);
     for (int32_t m = aptr[I]; m < aptr[I + 1]; ++m) {
       const int32_t i = amem[m];
@@ -221,11 +245,12 @@ __global__ void k_restrict(int32_t nc, const int32_t *__restrict__ aptr, const i
 // x_k += P_k x_{k+1}: a gather through the aggregate map
 template <class VT>
 __global__ void k_prolong(int32_t n, const int32_t *__restrict__ agg, const VT *__restrict__ pw,
-                          const VT *__restrict__ xc, VT *__restrict__ x, const int *pred) {
+                          const VT *__restrict__ xc, VT *__restrict__ x, const int *pred, const int32_t *sys,
+                          const int *bact) {
   pdl_wait_and_trigger();
   if (pred && *pred == 0) return;
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    x[i] += pw[i] * xc[agg[i]];
+    if (!bact || bact[sys[i]]) x[i] += pw[i] * xc[agg[i]];
 }
 
 // exact coarsest solve x = A_L^-1 b (one warp per row, FP64 accumulation)
@@ -935,6 +960,9 @@ struct Engine {
   Engine(Hierarchy &hh, cudaStream_t ss) : h(hh), s(ss) { gmres_variant = h.p.outer == 1; }
 
   VT *V(void *p) { return static_cast<VT *>(p); }
+  // batch: the system map of a level and the systems still iterating (null otherwise)
+  const int32_t *bsys(const Level &L) const { return h.batched ? L.sys_of : nullptr; }
+  const int *bact() const { return h.batched ? h.bactive : nullptr; }
 
   void check() {
     ++launches;
@@ -950,6 +978,7 @@ struct Engine {
     a.scol = L.scol;
     a.sval = L.sval;
     a.sdiag = L.sdiag;
+    if (h.batched) a.live = L.slive;
     a.x = x;
     a.out = out;
     a.pred = pred;
@@ -961,16 +990,22 @@ struct Engine {
   void sell(const SellArgs<VT> &a, int k) {
     // fused inner products: after the plain product (Alg. 5) and on the last
     // post-smoothing step of level 0 (z^T q of the outer flexible CG)
+    if (h.batched) {  // no fused inner products in a batch: they are per system (segdot)
+      if (a.ndot) throw Error{AMG_ERR_UNSUPPORTED, "batched SpMV was given fused inner products"};
+      klaunch(k_sell<MV, VT, EPI, false, true>, sell_grid(h.lev[k]), kThreads, s, a);
+      check();
+      return;
+    }
     if constexpr (EPI == E_Y || EPI == E_POST || EPI == E_HORNER_LAST) {
       if (a.ndot) {
-        klaunch(k_sell<MV, VT, EPI, true>, sell_grid(h.lev[k]), kThreads, s, a);
+        klaunch(k_sell<MV, VT, EPI, true, false>, sell_grid(h.lev[k]), kThreads, s, a);
         check();
         return;
       }
     } else {
       if (a.ndot) throw Error{AMG_ERR_UNSUPPORTED, "SpMV epilogue without fused inner products was given some"};
     }
-    klaunch(k_sell<MV, VT, EPI, false>, sell_grid(h.lev[k]), kThreads, s, a);
+    klaunch(k_sell<MV, VT, EPI, false, false>, sell_grid(h.lev[k]), kThreads, s, a);
     check();
   }
 
@@ -989,9 +1024,9 @@ struct Engine {
     }
     Level &C = h.lev[k + 1];
     VT *tmp = V(L.tmp);
-    const bool poly = h.p.smoother == 1 && L.poly != nullptr;
+    const bool poly = h.p.smoother == 1 && L.poly != nullptr && !L.poly_off;
     if (poly) {  // x = sum_q diag(c_q) (D^-1 A)^q D^-1 b
-      klaunch(k_scale<VT>, ew_grid(L.n), kThreads, s, L.n, V(L.u0), V(L.dinv), rhs, pred);
+      klaunch(k_scale<VT>, ew_grid(L.n), kThreads, s, L.n, V(L.u0), V(L.dinv), rhs, pred, bsys(L), bact());
       check();
       SellArgs<VT> a = sell_args(k, V(L.u0), V(L.u1), pred);
       a.dinv = V(L.dinv);
@@ -1003,7 +1038,7 @@ struct Engine {
       a.p1 = V(L.u1);
       sell<E_POLYPRE>(a, k);
     } else if (!x0_ready) {
-      klaunch(k_scale<VT>, ew_grid(L.n), kThreads, s, L.n, tmp, V(L.wd), rhs, pred);  // pre-smoothing
+      klaunch(k_scale<VT>, ew_grid(L.n), kThreads, s, L.n, tmp, V(L.wd), rhs, pred, bsys(L), bact());  // pre-smoothing
       check();
     }
     {  // r_k = b_k - A_k x_k
@@ -1015,7 +1050,7 @@ struct Engine {
     const bool tail = (k + 1 == h.tail_t);
     // r_{k+1} = R_k r_k  (and x0 of level k+1 when it smooths)
     klaunch(k_restrict<VT>, ew_grid(L.nc), kThreads, s, L.nc, L.aptr, L.amem, V(L.pw), V(L.r), V(C.bc),
-                                                      (coarse_is_last || tail) ? nullptr : V(C.wd), V(C.tmp), pred);
+            (coarse_is_last || tail) ? nullptr : V(C.wd), V(C.tmp), pred, bsys(C), bact());
     check();
     if (tail) {  // levels k+1..L-1 in one cluster launch
       TailArgs ta{};
@@ -1038,7 +1073,7 @@ struct Engine {
       cycle(k + 1, V(C.bc), V(C.xc), true, pred);  // Alg. 4 recursion
     }
     // x_k += P_k x_{k+1}
-    klaunch(k_prolong<VT>, ew_grid(L.n), kThreads, s, L.n, L.agg, V(L.pw), V(C.xc), tmp, pred);
+    klaunch(k_prolong<VT>, ew_grid(L.n), kThreads, s, L.n, L.agg, V(L.pw), V(C.xc), tmp, pred, bsys(L), bact());
     check();
     // r_k = b_k - A_k x_k;  x_k += omega D^-1 r_k  (or the transposed polynomial)
     SellArgs<VT> a = sell_args(k, tmp, out, pred);
@@ -1202,6 +1237,12 @@ struct Engine {
     const int32_t ns = h.nsys, n = L0.n;
     const int ng = ew_grid(n);
     int *bact = h.bactive, *brs = h.bactive + ns + 1;
+    for (int k = 0; k < h.L; ++k) {  // slices of the systems still iterating
+      Level &L = h.lev[k];
+      klaunch(k_slice_live, grid_for(L.nslices, kThreads, 152 * 4), kThreads, s, L.n, L.nslices,
+              (const int32_t *)L.sys_of, (const int *)bact, L.slive);
+      ++launches;
+    }
     // z = M r
     precond(h.r, h.z, nullptr, false);
     Engine<double, double> e64(h, s);
@@ -1219,7 +1260,8 @@ struct Engine {
       a.sval = L0.sval64;
       a.x = h.pdir;
       a.out = h.q;
-      klaunch(k_sell<double, double, E_Y, false>, outer_grid(L0), kThreads, s, a);
+      a.live = L0.slive;
+      klaunch(k_sell<double, double, E_Y, false, true>, outer_grid(L0), kThreads, s, a);
     }
     launches += 3;
     e64.launches = 0;
@@ -1262,7 +1304,7 @@ struct Engine {
       a.dop[1][0] = OP_X; a.dop[1][1] = OP_U1;
       a.partials = part + 5 * kRedBlocks;
       a.pred = active;
-      klaunch(k_sell<double, double, E_Y, true>, nsg, kThreads, s, a);
+      klaunch(k_sell<double, double, E_Y, true, false>, nsg, kThreads, s, a);
       check();
     }
     // x, r update (+ the next preconditioner input in reduced precision)
@@ -1313,7 +1355,7 @@ void configure_tail(Hierarchy &h, cudaStream_t s) {
     if (h.lev[t].n > kTailMaxRows) continue;
     bool ok = true;
     for (int k = t; k <= h.L - 3; ++k) ok = ok && k >= h.p.kcycle_levels;
-    for (int k = t; k < h.L - 1; ++k) ok = ok && !(h.p.smoother == 1 && h.lev[k].poly);
+    for (int k = t; k < h.L - 1; ++k) ok = ok && !(h.p.smoother == 1 && h.lev[k].poly && !h.lev[k].poly_off);
     if (ok) {
       h.tail_t = t;
       break;
@@ -1604,7 +1646,7 @@ int run_fgmres_t(Hierarchy &h, const double *b, double *x, double tol, int32_t *
         a.x = zj;
         a.out = w;
         a.pred = active;
-        klaunch(k_sell<double, double, E_Y, false>, outer_grid(L0), kThreads, s, a);
+        klaunch(k_sell<double, double, E_Y, false, false>, outer_grid(L0), kThreads, s, a);
         eng.check();
       }
       for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
@@ -1812,6 +1854,8 @@ void prepare_batched(Hierarchy &h, cudaStream_t s) {
     Level &L = h.lev[k];
     L.sys_of = h.arena.get<int32_t>((size_t)L.n + 1);
     klaunch(k_sys_of, ew_grid(L.n), kThreads, s, L.n, ns, (const int32_t *)L.sys_off, L.sys_of);
+    L.slive = h.arena.get<unsigned char>((size_t)L.nslices + 1);
+    AMG_CUDA(cudaMemsetAsync(L.slive, 1, (size_t)L.nslices + 1, s));
     build_tiles(h, L, kTile, s);
     L.bslots = h.arena.get<double>((size_t)kNumSlots * ns);
     L.bflag = h.arena.get<int>((size_t)ns + 1);
@@ -1916,6 +1960,13 @@ void run_spmv_t(Hierarchy &h, int k, const void *x, void *y, cudaStream_t s) {
 
 void set_poly(Hierarchy &h, int level, const double *coef, cudaStream_t s) {
   Level &L = h.lev[level];
+  if (!coef) {  // back to damped Jacobi on this level (the buffer stays for a later set)
+    L.poly_off = true;
+    configure_tail(h, s);
+    h.graph_kind = -1;
+    return;
+  }
+  L.poly_off = false;
   const size_t cnt = (size_t)L.n * 3;
   DevBuf<double> tmp(cnt);
   const cudaMemcpyKind kind = pointer_kind(coef) == PTR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;

@@ -193,6 +193,13 @@ def test_polynomial_smoother_reduces_to_jacobi(gpu, orc):
         L = g.level(k)
         gpu.amg_set_poly(g.h, k, np.tile([L["omega"], 0.0, 0.0], (L["n"], 1)))
     assert np.allclose(g.precond(b), z_j, rtol=1e-12, atol=1e-14 * np.abs(z_j).max())
+    # a cleared level runs damped Jacobi again: bit-identical to never having set it
+    for k in range(g.nlevels - 1):
+        gpu.amg_set_poly(g.h, k, np.tile([0.3, 0.1, 0.05], (g.level(k)["n"], 1)))
+    assert not np.array_equal(g.precond(b), z_j)
+    for k in range(g.nlevels - 1):
+        gpu.amg_set_poly(g.h, k, None)
+    assert np.array_equal(g.precond(b), z_j)
 
 
 @pytest.mark.parametrize("tail", [1, 2])
