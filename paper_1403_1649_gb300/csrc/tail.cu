@@ -162,6 +162,7 @@ __device__ void tail_vcycle(TailCtx &c, const TailArgs &a, const VT *rhs_t, VT *
 
 template <class MV, class VT, int CL>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kTailThreads, 1) k_tail(TailArgs a) {
+  pdl_wait_and_trigger();  // launched like the other solve kernels (programmatic dependent launch)
   if (a.pred && *a.pred == 0) return;  // uniform: every block reads the same flag
   TailCtx c{cg::this_cluster()};
   c.nblocks = CL;
@@ -251,9 +252,9 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kTailThreads, 1) k_
 template <class MV, class VT>
 void tail_launch(const TailArgs &a, int blocks, cudaStream_t s) {
   if (blocks == 1)
-    k_tail<MV, VT, 1><<<1, kTailThreads, 0, s>>>(a);
+    klaunch(k_tail<MV, VT, 1>, 1, kTailThreads, s, a);
   else
-    k_tail<MV, VT, 8><<<8, kTailThreads, 0, s>>>(a);
+    klaunch(k_tail<MV, VT, 8>, 8, kTailThreads, s, a);
   AMG_LAUNCH_CHECK();
 }
 
