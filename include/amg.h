@@ -89,6 +89,11 @@ typedef struct amg_params {
                             (and, for a batch, the row tile of the per-system inner
                             products) and keep the fastest; the choice is reported in
                             amg_level_info.  Changes rounding order only                  */
+  int32_t symmetric;     /* 1: A is symmetric (omega from the symmetric part of the
+                            Arnoldi matrix, Cholesky coarsest factor).  0: nonsymmetric
+                            (omega from the eigenvalues of the Arnoldi Hessenberg matrix,
+                            LU coarsest factor); needs outer = 1 (FGMRES, Sec. 2.2) and
+                            a single system                                                */
 } amg_params;
 
 typedef struct amg_level_info {
@@ -117,7 +122,7 @@ typedef struct amg_hierarchy amg_hierarchy;
 /* Fill *p with the defaults: alpha 0.25, seed 0, coarse_max 64, max_levels 25,
  * kcycle_levels 2, kcycle_t 0.25, omega_mode 0, omega 2/3, precision F64,
  * outer FCG, restart 30, max_iter 500, use_graph 1, smoother 0, tail 0, pdl 1,
- * autotune 0. */
+ * autotune 0, symmetric 1. */
 void amg_default_params(amg_params *p);
 
 /* Alg. 1: build the hierarchy of A on the GPU.

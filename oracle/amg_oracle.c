@@ -18,6 +18,8 @@
  */
 #include "amg_oracle.h"
 
+#include <complex.h>
+#undef I /* the oracle uses I for coarse indices */
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -376,8 +378,62 @@ void or_sym_eig(int32_t m, const double *a_in, double *w) {
 /* which is similar to D^-1 A and symmetric for symmetric A; the estimate is */
 /* the largest |eigenvalue| of the symmetric part of the m x m Hessenberg.   */
 /* ------------------------------------------------------------------------- */
+/* Shifted QR algorithm for the eigenvalues of an upper Hessenberg matrix, in
+ * complex arithmetic (Golub & Van Loan, Sec. 7.5): on the active leading block,
+ * H - mu I = Q R by Givens rotations, H <- R Q + mu I, with the Wilkinson shift
+ * mu (the eigenvalue of the trailing 2 x 2 block nearer to its last diagonal
+ * entry); the last row deflates once |h_{n,n-1}| <= 1e-14 (|h_nn| + |h_{n-1,n-1}|)
+ * (or after 200 steps).  Returns the largest modulus. */
+double or_hess_rho(int32_t m, const double *Hin) {
+  double complex a[8][8];
+  for (int32_t i = 0; i < m; ++i)
+    for (int32_t j = 0; j < m; ++j) a[i][j] = Hin[i * m + j];
+  double rho = 0.0;
+  int32_t n = m, iter = 0;
+  while (n > 0) {
+    if (n == 1) {
+      if (cabs(a[0][0]) > rho) rho = cabs(a[0][0]);
+      break;
+    }
+    const double sc = cabs(a[n - 1][n - 1]) + cabs(a[n - 2][n - 2]);
+    if (cabs(a[n - 1][n - 2]) <= 1e-14 * sc || iter >= 200) {
+      if (cabs(a[n - 1][n - 1]) > rho) rho = cabs(a[n - 1][n - 1]);
+      n = n - 1;
+      iter = 0;
+      continue;
+    }
+    const double complex p = a[n - 2][n - 2], q = a[n - 2][n - 1], r = a[n - 1][n - 2], t = a[n - 1][n - 1];
+    const double complex half = (p + t) / 2.0;
+    const double complex disc = csqrt(half * half - (p * t - q * r));
+    const double complex l1 = half + disc, l2 = half - disc;
+    const double complex mu = cabs(l1 - t) < cabs(l2 - t) ? l1 : l2;
+    double complex cs[8], sn[8];
+    for (int32_t i = 0; i < n; ++i) a[i][i] = a[i][i] - mu;
+    for (int32_t k = 0; k + 1 < n; ++k) { /* left rotations: R = G_{n-2} ... G_0 (H - mu I) */
+      const double complex x = a[k][k], y = a[k + 1][k];
+      const double nrm = sqrt(cabs(x) * cabs(x) + cabs(y) * cabs(y));
+      cs[k] = nrm > 0.0 ? x / nrm : 1.0;
+      sn[k] = nrm > 0.0 ? y / nrm : 0.0;
+      for (int32_t j = k; j < n; ++j) {
+        const double complex u = a[k][j], v = a[k + 1][j];
+        a[k][j] = conj(cs[k]) * u + conj(sn[k]) * v;
+        a[k + 1][j] = -sn[k] * u + cs[k] * v;
+      }
+    }
+    for (int32_t k = 0; k + 1 < n; ++k) /* right rotations: R Q */
+      for (int32_t i = 0; i <= k + 1; ++i) {
+        const double complex u = a[i][k], v = a[i][k + 1];
+        a[i][k] = u * cs[k] + v * sn[k];
+        a[i][k + 1] = -u * conj(sn[k]) + v * conj(cs[k]);
+      }
+    for (int32_t i = 0; i < n; ++i) a[i][i] = a[i][i] + mu;
+    iter = iter + 1;
+  }
+  return rho;
+}
+
 double or_rho_estimate(int32_t n, const int32_t *rp, const int32_t *ci, const double *val,
-                       uint64_t seed, int32_t level, int32_t m, double *H_out) {
+                       uint64_t seed, int32_t level, int32_t m, double *H_out, int32_t symmetric) {
   if (m > n) m = n;
   if (m > 8) m = 8;
   double *dh = (double *)malloc(sizeof(double) * (size_t)n);
@@ -433,12 +489,59 @@ double or_rho_estimate(int32_t n, const int32_t *rp, const int32_t *ci, const do
   if (H_out)
     for (int32_t a = 0; a < mm; ++a)
       for (int32_t b = 0; b < mm; ++b) H_out[a * mm + b] = H[a * 8 + b];
-  or_sym_eig(mm, T, ev);
-  double rho = fabs(ev[0]) > fabs(ev[mm - 1]) ? fabs(ev[0]) : fabs(ev[mm - 1]);
+  double rho;
+  if (symmetric) {
+    or_sym_eig(mm, T, ev);
+    rho = fabs(ev[0]) > fabs(ev[mm - 1]) ? fabs(ev[0]) : fabs(ev[mm - 1]);
+  } else {
+    for (int32_t a = 0; a < mm; ++a)
+      for (int32_t b = 0; b < mm; ++b) T[a * mm + b] = H[a * 8 + b];
+    rho = or_hess_rho(mm, T);
+  }
   free(dh);
   free(Q);
   free(w);
   return rho;
+}
+
+/* ------------------------------------------------------------------------- */
+/* dense LU with partial pivoting for a nonsymmetric coarsest level          */
+/* ------------------------------------------------------------------------- */
+int32_t or_lu(int32_t n, double *a, int32_t *piv) {
+  for (int32_t j = 0; j < n; ++j) {
+    int32_t pr = j; /* the largest |a_ij| below the diagonal, first index on ties */
+    for (int32_t i = j + 1; i < n; ++i)
+      if (fabs(a[(size_t)i * n + j]) > fabs(a[(size_t)pr * n + j])) pr = i;
+    piv[j] = pr;
+    if (!(fabs(a[(size_t)pr * n + j]) > 0.0)) return -1;
+    if (pr != j)
+      for (int32_t k = 0; k < n; ++k) {
+        const double t = a[(size_t)j * n + k];
+        a[(size_t)j * n + k] = a[(size_t)pr * n + k];
+        a[(size_t)pr * n + k] = t;
+      }
+    for (int32_t i = j + 1; i < n; ++i) {
+      const double l = a[(size_t)i * n + j] / a[(size_t)j * n + j];
+      a[(size_t)i * n + j] = l;
+      for (int32_t k = j + 1; k < n; ++k) a[(size_t)i * n + k] = a[(size_t)i * n + k] - l * a[(size_t)j * n + k];
+    }
+  }
+  return 0;
+}
+
+void or_lu_solve(int32_t n, const double *lu, const int32_t *piv, double *b) {
+  for (int32_t j = 0; j < n; ++j) /* the row interchanges, then L y = b, U x = y */
+    if (piv[j] != j) {
+      const double t = b[j];
+      b[j] = b[piv[j]];
+      b[piv[j]] = t;
+    }
+  for (int32_t i = 0; i < n; ++i)
+    for (int32_t k = 0; k < i; ++k) b[i] = b[i] - lu[(size_t)i * n + k] * b[k];
+  for (int32_t i = n - 1; i >= 0; --i) {
+    for (int32_t k = i + 1; k < n; ++k) b[i] = b[i] - lu[(size_t)i * n + k] * b[k];
+    b[i] = b[i] / lu[(size_t)i * n + i];
+  }
 }
 
 /* ------------------------------------------------------------------------- */
@@ -497,7 +600,8 @@ struct or_hier {
   or_params p;
   int32_t L;
   or_level lev[OR_MAX_LEVELS];
-  double *chol; /* dense Cholesky factor of A_{L-1} */
+  double *chol; /* dense Cholesky (symmetric) or LU (nonsymmetric) factor of A_{L-1} */
+  int32_t *piv; /* LU row interchanges */
 };
 
 void or_default_params(or_params *p) {
@@ -512,6 +616,7 @@ void or_default_params(or_params *p) {
   p->outer = 0;
   p->restart = 30;
   p->smoother = 0;
+  p->symmetric = 1;
 }
 
 static double *dalloc(size_t n) { return (double *)calloc(n + 1, sizeof(double)); }
@@ -543,6 +648,7 @@ void or_free(or_hier *h) {
   if (!h) return;
   for (int32_t k = 0; k < h->L; ++k) level_free(&h->lev[k]);
   free(h->chol);
+  free(h->piv);
   free(h);
 }
 
@@ -634,7 +740,7 @@ or_hier *or_setup(int32_t n, const int32_t *rp, const int32_t *ci, const double 
         if (L->ci[pp] == i) L->dinv[i] = 1.0 / L->val[pp];
     if (q < h->L - 1) {
       L->omega = p->omega_mode == 0
-                     ? (4.0 / 3.0) / or_rho_estimate(L->n, L->rp, L->ci, L->val, p->seed, q, 5, NULL)
+                     ? (4.0 / 3.0) / or_rho_estimate(L->n, L->rp, L->ci, L->val, p->seed, q, 5, NULL, p->symmetric)
                      : p->omega;
       for (int32_t i = 0; i < L->n; ++i) {
         double aii = 1.0 / L->dinv[i];
@@ -654,7 +760,8 @@ or_hier *or_setup(int32_t n, const int32_t *rp, const int32_t *ci, const double 
   for (int32_t i = 0; i < Lc->n; ++i)
     for (int32_t pp = Lc->rp[i]; pp < Lc->rp[i + 1]; ++pp)
       h->chol[(size_t)i * Lc->n + Lc->ci[pp]] = Lc->val[pp];
-  if (or_cholesky(Lc->n, h->chol)) {
+  if (p->symmetric ? or_cholesky(Lc->n, h->chol)
+                   : or_lu(Lc->n, h->chol, h->piv = (int32_t *)malloc(sizeof(int32_t) * (size_t)(Lc->n + 1)))) {
     *err = -7;
     or_free(h);
     return NULL;
@@ -751,7 +858,10 @@ static void smooth_post(or_hier *h, int32_t k, const double *b, double *x) {
 static void coarsest_solve(or_hier *h, const double *b, double *x) {
   int32_t n = h->lev[h->L - 1].n;
   for (int32_t i = 0; i < n; ++i) x[i] = b[i];
-  or_chol_solve(n, h->chol, x);
+  if (h->piv)
+    or_lu_solve(n, h->chol, h->piv, x);
+  else
+    or_chol_solve(n, h->chol, x);
 }
 
 static void cycle(or_hier *h, int32_t k, const double *b, double *x);

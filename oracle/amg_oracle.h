@@ -37,6 +37,9 @@ typedef struct or_params {
   int32_t restart;     /* FGMRES restart length                                    */
   int32_t smoother;    /* 0: damped Jacobi; 1: per-row polynomial (coefficients
                           supplied per level through or_set_poly)                  */
+  int32_t symmetric;   /* 1: A symmetric (rho from the symmetric part of H, Cholesky
+                          coarsest factor); 0: nonsymmetric (rho from the
+                          eigenvalues of H, LU coarsest factor; use FGMRES)        */
 } or_params;
 
 /* ---- individual setup steps (used directly by the pin tests) ---- */
@@ -70,8 +73,18 @@ int64_t or_galerkin(int32_t n, const int32_t *rp, const int32_t *ci, const doubl
                     int32_t nc, const int32_t *agg, const double *P, int32_t *crp,
                     int32_t *cci, double *cval, int64_t cap);
 /* Eq. (damped Jacobi): spectral-radius estimate of D^-1 A from m Arnoldi steps. */
+/* largest |eigenvalue| of an upper Hessenberg m x m matrix (m <= 8, row major)
+ * by the shifted QR algorithm in complex arithmetic */
+double or_hess_rho(int32_t m, const double *H);
+/* LU factorisation with partial pivoting (row interchanges piv), and solve */
+int32_t or_lu(int32_t n, double *a, int32_t *piv);
+void or_lu_solve(int32_t n, const double *lu, const int32_t *piv, double *b);
+/* rho(D^-1 A) from m Arnoldi steps on |D|^-1/2 A |D|^-1/2 (Eq. damped Jacobi):
+ * symmetric = 1: the largest |eigenvalue| of the symmetric part of H_m (equal to
+ * H_m for symmetric A); 0: the largest |eigenvalue| of H_m itself */
 double or_rho_estimate(int32_t n, const int32_t *rp, const int32_t *ci, const double *val,
-                       uint64_t seed, int32_t level, int32_t m, double *H_out /* m*m or NULL */);
+                       uint64_t seed, int32_t level, int32_t m, double *H_out /* m*m or NULL */,
+                       int32_t symmetric);
 /* eigenvalues of a symmetric m x m matrix (cyclic Jacobi), ascending */
 void or_sym_eig(int32_t m, const double *a, double *w);
 /* dense Cholesky in place (lower triangle); returns 0 or -1 if not SPD */

@@ -39,6 +39,7 @@ class ORParams(C.Structure):
         ("outer", C.c_int32),
         ("restart", C.c_int32),
         ("smoother", C.c_int32),
+        ("symmetric", C.c_int32),
     ]
 
 
@@ -80,7 +81,12 @@ def lib():
                                   C.c_void_p, C.c_void_p, C.c_int64]
         L.or_galerkin.restype = C.c_int64
         L.or_rho_estimate.argtypes = [C.c_int32, _i32p, _i32p, _f64p, C.c_uint64, C.c_int32, C.c_int32,
-                                      C.c_void_p]
+                                      C.c_void_p, C.c_int32]
+        L.or_hess_rho.argtypes = [C.c_int32, _f64p]
+        L.or_hess_rho.restype = C.c_double
+        L.or_lu.argtypes = [C.c_int32, _f64p, _i32p]
+        L.or_lu.restype = C.c_int32
+        L.or_lu_solve.argtypes = [C.c_int32, _f64p, _i32p, _f64p]
         L.or_rho_estimate.restype = C.c_double
         L.or_sym_eig.argtypes = [C.c_int32, _f64p, _f64p]
         L.or_cholesky.argtypes = [C.c_int32, _f64p]
@@ -194,10 +200,10 @@ def galerkin(A, agg, nc: int, P=None):
     return CSR(nc, crp, cci[:cn], cval[:cn])
 
 
-def rho_estimate(A, seed: int = 0, level: int = 0, m: int = 5):
+def rho_estimate(A, seed: int = 0, level: int = 0, m: int = 5, symmetric: bool = True):
     n, rp, ci, v = _csr_args(A)
     H = np.zeros(64)
-    rho = lib().or_rho_estimate(n, rp, ci, v, seed, level, m, H.ctypes.data)
+    rho = lib().or_rho_estimate(n, rp, ci, v, seed, level, m, H.ctypes.data, 1 if symmetric else 0)
     mm = min(m, n)
     return rho, H[:mm * mm].reshape(mm, mm)
 
@@ -213,6 +219,26 @@ def cholesky(a: np.ndarray):
     L = np.ascontiguousarray(a, np.float64).copy()
     rc = lib().or_cholesky(L.shape[0], L.reshape(-1))
     return (L if rc == 0 else None)
+
+
+def hess_rho(H: np.ndarray) -> float:
+    """Largest |eigenvalue| of an upper Hessenberg matrix (shifted complex QR)."""
+    H = np.ascontiguousarray(H, np.float64)
+    return lib().or_hess_rho(H.shape[0], H.reshape(-1).copy())
+
+
+def lu(a: np.ndarray):
+    """In-place LU with partial pivoting: (LU, piv) or None if singular."""
+    LU = np.ascontiguousarray(a, np.float64).copy()
+    piv = np.zeros(LU.shape[0], np.int32)
+    rc = lib().or_lu(LU.shape[0], LU.reshape(-1), piv)
+    return (LU, piv) if rc == 0 else None
+
+
+def lu_solve(LU: np.ndarray, piv: np.ndarray, b: np.ndarray) -> np.ndarray:
+    x = np.ascontiguousarray(b, np.float64).copy()
+    lib().or_lu_solve(LU.shape[0], np.ascontiguousarray(LU).reshape(-1), piv, x)
+    return x
 
 
 def chol_solve(L: np.ndarray, b: np.ndarray) -> np.ndarray:

@@ -96,7 +96,7 @@ int check_params(const amg_params *p) {
   if (!(p->alpha >= 0.0 && p->alpha < 1.0) || p->coarse_max < 1 || p->max_levels < 1 || p->kcycle_levels < 0 ||
       p->precision < 0 || p->precision > 2 || p->outer < 0 || p->outer > 1 || p->max_iter < 1 ||
       p->restart < 1 || p->omega_mode < 0 || p->omega_mode > 1 || p->smoother < 0 || p->smoother > 1 ||
-      p->tail < 0 || p->tail > 2 || p->autotune < 0 || p->autotune > 1) {
+      p->tail < 0 || p->tail > 2 || p->autotune < 0 || p->autotune > 1 || p->symmetric < 0 || p->symmetric > 1) {
     amg::set_last_error("invalid amg_params");
     return AMG_ERR_BAD_INPUT;
   }
@@ -137,6 +137,7 @@ void amg_default_params(amg_params *p) {
   p->tail = 0;
   p->pdl = 1;
   p->autotune = 0;
+  p->symmetric = 1;
 }
 
 int amg_setup(const amg_csr *A, const amg_params *params, void *stream, amg_hierarchy **out) {
@@ -147,6 +148,10 @@ int amg_setup(const amg_csr *A, const amg_params *params, void *stream, amg_hier
   }
   int rc = check_params(params);
   if (rc) return rc;
+  if (params->symmetric == 0 && params->outer != 1) {
+    amg::set_last_error("amg_setup: a nonsymmetric system needs FGMRES (outer = 1)");
+    return AMG_ERR_BAD_INPUT;
+  }
   if (params->outer == 1 && params->restart > 32) {
     amg::set_last_error("amg_setup: FGMRES restart length is limited to 32");
     return AMG_ERR_BAD_INPUT;
@@ -218,8 +223,8 @@ int amg_setup_batch(int32_t nsys, const amg_csr *As, const amg_params *params, v
     }
   int rc = check_params(params);
   if (rc) return rc;
-  if (params->outer != 0) {
-    amg::set_last_error("amg_setup_batch: batches use flexible CG (outer = 0)");
+  if (params->outer != 0 || params->symmetric != 1) {
+    amg::set_last_error("amg_setup_batch: batches are symmetric systems solved by flexible CG (outer = 0)");
     return AMG_ERR_UNSUPPORTED;
   }
   *out = nullptr;

@@ -1079,7 +1079,83 @@ __device__ int count_below(const double (&T)[kArnoldiMax][kArnoldiMax], int m, d
 // steps), symmetrises the leading block and sets omega = (4/3)/rho.  One warp:
 // multisection, every lane tests one of 32 points of the current interval, so
 // each round narrows it 33-fold (12 rounds reach double precision).
-__global__ void k_omega_from_H(const double *__restrict__ H, const double *__restrict__ wn, int m,
+// ---- eigenvalues of a small nonsymmetric Hessenberg matrix ---------------
+// complex arithmetic written from the definitions
+struct cx {
+  double re, im;
+};
+__device__ __forceinline__ cx c_add(cx a, cx b) { return {a.re + b.re, a.im + b.im}; }
+__device__ __forceinline__ cx c_sub(cx a, cx b) { return {a.re - b.re, a.im - b.im}; }
+__device__ __forceinline__ cx c_mul(cx a, cx b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+__device__ __forceinline__ cx c_conj(cx a) { return {a.re, -a.im}; }
+__device__ __forceinline__ double c_abs(cx a) { return hypot(a.re, a.im); }
+__device__ __forceinline__ cx c_scale(cx a, double f) { return {a.re * f, a.im * f}; }
+// principal square root: with r = |z|, sqrt(z) = s + i im/(2 s), s = sqrt((r + re)/2)
+// (re >= 0); else |im|/(2 s) + i sign(im) s with s = sqrt((r - re)/2)
+__device__ cx c_sqrt(cx z) {
+  const double r = c_abs(z);
+  if (r == 0.0) return {0.0, 0.0};
+  if (z.re >= 0.0) {
+    const double sq = sqrt(0.5 * (r + z.re));
+    return {sq, z.im / (2.0 * sq)};
+  }
+  const double sq = sqrt(0.5 * (r - z.re));
+  return {fabs(z.im) / (2.0 * sq), copysign(sq, z.im)};
+}
+
+// largest |eigenvalue| of the leading m x m block of H (row stride 8) by the
+// shifted QR algorithm in complex arithmetic: H - mu I = Q R by Givens rotations,
+// H <- R Q + mu I, Wilkinson shift from the trailing 2 x 2 block, deflation once
+// |h_{n,n-1}| <= 1e-14 (|h_nn| + |h_{n-1,n-1}|) or after 200 steps
+__device__ double hess_rho(int m, const double *H) {
+  cx a[kArnoldiMax][kArnoldiMax];
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) a[i][j] = {H[i * 8 + j], 0.0};
+  double rho = 0.0;
+  int n = m, iter = 0;
+  while (n > 0) {
+    if (n == 1) {
+      rho = fmax(rho, c_abs(a[0][0]));
+      break;
+    }
+    const double sc = c_abs(a[n - 1][n - 1]) + c_abs(a[n - 2][n - 2]);
+    if (c_abs(a[n - 1][n - 2]) <= 1e-14 * sc || iter >= 200) {
+      rho = fmax(rho, c_abs(a[n - 1][n - 1]));
+      --n;
+      iter = 0;
+      continue;
+    }
+    const cx p = a[n - 2][n - 2], q = a[n - 2][n - 1], r = a[n - 1][n - 2], t = a[n - 1][n - 1];
+    const cx half = c_scale(c_add(p, t), 0.5);
+    const cx disc = c_sqrt(c_sub(c_mul(half, half), c_sub(c_mul(p, t), c_mul(q, r))));
+    const cx l1 = c_add(half, disc), l2 = c_sub(half, disc);
+    const cx mu = c_abs(c_sub(l1, t)) < c_abs(c_sub(l2, t)) ? l1 : l2;
+    cx cs[kArnoldiMax], sn[kArnoldiMax];
+    for (int i = 0; i < n; ++i) a[i][i] = c_sub(a[i][i], mu);
+    for (int k = 0; k + 1 < n; ++k) {
+      const cx x = a[k][k], y = a[k + 1][k];
+      const double nrm = sqrt(c_abs(x) * c_abs(x) + c_abs(y) * c_abs(y));
+      cs[k] = nrm > 0.0 ? cx{x.re / nrm, x.im / nrm} : cx{1.0, 0.0};
+      sn[k] = nrm > 0.0 ? cx{y.re / nrm, y.im / nrm} : cx{0.0, 0.0};
+      for (int j = k; j < n; ++j) {
+        const cx u = a[k][j], v = a[k + 1][j];
+        a[k][j] = c_add(c_mul(c_conj(cs[k]), u), c_mul(c_conj(sn[k]), v));
+        a[k + 1][j] = c_add(c_mul(cx{-sn[k].re, -sn[k].im}, u), c_mul(cs[k], v));
+      }
+    }
+    for (int k = 0; k + 1 < n; ++k)
+      for (int i = 0; i <= k + 1; ++i) {
+        const cx u = a[i][k], v = a[i][k + 1];
+        a[i][k] = c_add(c_mul(u, cs[k]), c_mul(v, sn[k]));
+        a[i][k + 1] = c_add(c_mul(cx{-u.re, -u.im}, c_conj(sn[k])), c_mul(v, c_conj(cs[k])));
+      }
+    for (int i = 0; i < n; ++i) a[i][i] = c_add(a[i][i], mu);
+    ++iter;
+  }
+  return rho;
+}
+
+__global__ void k_omega_from_H(const double *__restrict__ H, const double *__restrict__ wn, int m, int symmetric,
                                double *__restrict__ omega_out) {
   if (blockIdx.x != 0 || threadIdx.x >= 32) return;
   const int lane = threadIdx.x;
@@ -1089,6 +1165,10 @@ __global__ void k_omega_from_H(const double *__restrict__ H, const double *__res
       mm = j + 1;
       break;
     }
+  if (!symmetric) {  // rho from the eigenvalues of the Hessenberg matrix itself
+    if (lane == 0) *omega_out = (4.0 / 3.0) / hess_rho(mm, H);
+    return;
+  }
   double T[kArnoldiMax][kArnoldiMax];
   double g = 0.0;
 #pragma unroll
@@ -1131,6 +1211,83 @@ __global__ void k_omega_from_H(const double *__restrict__ H, const double *__res
 }
 
 // ============================================================== coarsest level
+// Gauss-Jordan inverse with partial pivoting (the largest |a_ij| on or below the
+// diagonal, the first index on ties) of a nonsymmetric n x n matrix, one block:
+// A (destroyed) -> Ainv.  fac: n doubles of scratch.
+__global__ void k_lu_inverse(int32_t n, double *__restrict__ A, double *__restrict__ Ainv, double *__restrict__ fac,
+                             int *__restrict__ err) {
+  __shared__ double bv_s[32];
+  __shared__ int bi_s[32];
+  __shared__ int piv;
+  __shared__ double pinv;
+  for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += blockDim.x) Ainv[t] = (t / n == t % n) ? 1.0 : 0.0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int32_t j = 0; j < n; ++j) {
+    double bv = -1.0;
+    int bi = n;
+    for (int32_t i = j + threadIdx.x; i < n; i += blockDim.x) {
+      const double v = fabs(A[(int64_t)i * n + j]);
+      if (v > bv || (v == bv && i < bi)) {
+        bv = v;
+        bi = i;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi < bi)) {
+        bv = ov;
+        bi = oi;
+      }
+    }
+    if (lane == 0) {
+      bv_s[wid] = bv;
+      bi_s[wid] = bi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double v = bv_s[0];
+      int i0 = bi_s[0];
+      for (int q = 1; q < nw; ++q)
+        if (bv_s[q] > v || (bv_s[q] == v && bi_s[q] < i0)) {
+          v = bv_s[q];
+          i0 = bi_s[q];
+        }
+      piv = i0;
+      if (!(v > 0.0)) *err = 1;
+    }
+    __syncthreads();
+    if (*err) return;
+    const int32_t pr = piv;
+    if (pr != j)
+      for (int32_t k = threadIdx.x; k < n; k += blockDim.x) {
+        double t = A[(int64_t)j * n + k];
+        A[(int64_t)j * n + k] = A[(int64_t)pr * n + k];
+        A[(int64_t)pr * n + k] = t;
+        t = Ainv[(int64_t)j * n + k];
+        Ainv[(int64_t)j * n + k] = Ainv[(int64_t)pr * n + k];
+        Ainv[(int64_t)pr * n + k] = t;
+      }
+    __syncthreads();
+    if (threadIdx.x == 0) pinv = 1.0 / A[(int64_t)j * n + j];
+    __syncthreads();
+    for (int32_t k = threadIdx.x; k < n; k += blockDim.x) {
+      A[(int64_t)j * n + k] *= pinv;
+      Ainv[(int64_t)j * n + k] *= pinv;
+    }
+    for (int32_t i = threadIdx.x; i < n; i += blockDim.x) fac[i] = i == j ? 0.0 : A[(int64_t)i * n + j];
+    __syncthreads();
+    for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += blockDim.x) {
+      const int32_t i = (int32_t)(t / n), k = (int32_t)(t % n);
+      if (i == j) continue;
+      A[t] -= fac[i] * A[(int64_t)j * n + k];
+      Ainv[t] -= fac[i] * Ainv[(int64_t)j * n + k];
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void k_dense_from_csr(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                                  const double *__restrict__ val, double *__restrict__ A) {
   int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1434,7 +1591,7 @@ void estimate_omega(Hierarchy &h, int k, const double *diag, double *omega_dev, 
     AMG_COUNT(), k_arn_orth<<<g, 256, 0, s>>>(n, j, 0, Q.p, w.p, W.p, part.p, H.p, corr.p, nrm2.p, ticket.p);
     AMG_COUNT(), k_arn_orth<<<g, 256, 0, s>>>(n, j, 1, Q.p, w.p, W.p, part.p, H.p, corr.p, nrm2.p, ticket.p);
   }
-  AMG_COUNT(), k_omega_from_H<<<1, 32, 0, s>>>(H.p, wn.p, m, omega_dev);
+  AMG_COUNT(), k_omega_from_H<<<1, 32, 0, s>>>(H.p, wn.p, m, h.p.symmetric, omega_dev);
   AMG_LAUNCH_CHECK();
 }
 
@@ -1703,9 +1860,16 @@ void finish_levels(Hierarchy &h, cudaStream_t s, bool fresh) {
     AMG_CUDA(cudaMemsetAsync(dense.p, 0, sizeof(double) * (size_t)Lc.n * Lc.n, s));
     AMG_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
     AMG_COUNT(), k_dense_from_csr<<<blocks_for(Lc.n), 256, 0, s>>>(Lc.n, Lc.rp, Lc.ci, Lc.val, dense.p);
-    AMG_COUNT(), k_cholesky_inverse<<<1, 1024, 0, s>>>(Lc.n, dense.p, h.coarse_inv, err.p);
+    if (p.symmetric) {
+      AMG_COUNT(), k_cholesky_inverse<<<1, 1024, 0, s>>>(Lc.n, dense.p, h.coarse_inv, err.p);
+    } else {
+      DevBuf<double> fac(Lc.n);
+      AMG_COUNT(), k_lu_inverse<<<1, 1024, 0, s>>>(Lc.n, dense.p, h.coarse_inv, fac.p, err.p);
+    }
     AMG_LAUNCH_CHECK();
-    if (read_scalar(err.p, s)) throw Error{AMG_ERR_SETUP, "coarsest level matrix is not positive definite"};
+    if (read_scalar(err.p, s))
+      throw Error{AMG_ERR_SETUP, p.symmetric ? "coarsest level matrix is not positive definite"
+                                             : "coarsest level matrix is singular"};
   }
 }
 

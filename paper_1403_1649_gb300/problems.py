@@ -234,6 +234,32 @@ def varcoef3d(m: int = 160, seed: int = 2, block: int = 8, lo: float = -3.0, hi:
     return _stencil_csr((m, m, m), face, bface)
 
 
+def convdiff2d(m: int, seed: int, pe: float = 2.0) -> CSR:
+    """Upwind finite differences for -Laplace(u) + b . grad(u) on an m^2 interior
+    grid, Dirichlet eliminated, scaled by h^2: b = pe (cos t, sin t), t uniform
+    on [0, 2 pi) from the seed, pe the cell Peclet number.  Neighbour entries are
+    -1 - max(+-b_x, 0) (west / east) and -1 - max(+-b_y, 0) (south / north), the
+    diagonal 4 + |b_x| + |b_y|: a nonsymmetric M-matrix."""
+    t = 2.0 * np.pi * float(uniform01(seed, STREAM_COEF, 1)[0])
+    bx, by = pe * np.cos(t), pe * np.sin(t)
+    w, e = -1.0 - max(bx, 0.0), -1.0 - max(-bx, 0.0)
+    so, no = -1.0 - max(by, 0.0), -1.0 - max(-by, 0.0)
+    d = 4.0 + abs(bx) + abs(by)
+    n = m * m
+    idx = np.arange(n)
+    x, y = idx % m, idx // m
+    cols, vals = [], []
+    for dc, v, ok in ((-m, so, y > 0), (-1, w, x > 0), (0, d, np.ones(n, bool)), (1, e, x < m - 1),
+                      (m, no, y < m - 1)):
+        cols.append(np.where(ok, idx + dc, -1))
+        vals.append(np.where(ok, v, 0.0))
+    C = np.stack(cols, 1)
+    V = np.stack(vals, 1)
+    keep = C >= 0
+    rowptr = np.concatenate([[0], np.cumsum(keep.sum(1))]).astype(np.int32)
+    return CSR(n, rowptr, C[keep].astype(np.int32), V[keep].astype(np.float64))
+
+
 def varcoef2d(m: int, seed: int, lo: float = -2.0, hi: float = 2.0) -> CSR:
     """Finite-volume 5-point -div(k grad u) on an m^2 cell grid, k log-uniform per cell."""
     u = uniform01(seed, STREAM_COEF, m * m).reshape(m, m)  # [y, x]

@@ -603,3 +603,51 @@ def test_twogrid_loss_against_dense_and_fd(oracle_mod):
     om = levs[0].omega
     LJ, _ = H.twogrid_loss(np.column_stack([np.full(A.n, om), np.zeros(A.n), np.zeros(A.n)]), 3, 7, False)
     assert LJ < L0
+
+
+# ------------------------------------------------------------ nonsymmetric systems
+def test_hess_rho_against_lapack(oracle_mod):
+    """The shifted complex QR's largest modulus equals LAPACK's, also for
+    Hessenberg matrices with complex conjugate eigenvalue pairs."""
+    rng = np.random.default_rng(7)
+    for m in (1, 2, 3, 5, 8):
+        for _ in range(6):
+            H = np.triu(rng.normal(size=(m, m)), -1)
+            ev = np.linalg.eigvals(H)
+            assert oracle_mod.hess_rho(H) == pytest.approx(np.abs(ev).max(), rel=1e-12)
+    R = np.array([[0.0, -2.0], [2.0, 0.0]])  # a pure rotation: eigenvalues +-2i
+    assert oracle_mod.hess_rho(R) == pytest.approx(2.0, rel=1e-14)
+
+
+def test_lu_solve_against_lapack(oracle_mod):
+    rng = np.random.default_rng(8)
+    for n in (1, 4, 17, 40):
+        A = rng.normal(size=(n, n))
+        b = rng.normal(size=n)
+        LU, piv = oracle_mod.lu(A)
+        assert np.allclose(oracle_mod.lu_solve(LU, piv, b), np.linalg.solve(A, b), rtol=1e-11, atol=1e-11)
+    assert oracle_mod.lu(np.zeros((3, 3))) is None
+
+
+def test_rho_estimate_nonsymmetric_full_krylov_space(oracle_mod):
+    """With m = n Arnoldi steps the Hessenberg matrix is similar to
+    |D|^-1/2 A |D|^-1/2: rho equals its spectral radius."""
+    A = P.convdiff2d(2, 3, pe=3.0)  # 4 x 4, nonsymmetric
+    D = A.to_dense()
+    dh = 1.0 / np.sqrt(np.abs(np.diag(D)))
+    M = dh[:, None] * D * dh[None, :]
+    rho, _ = oracle_mod.rho_estimate(A, seed=1, level=0, m=A.n, symmetric=False)
+    assert rho == pytest.approx(np.abs(np.linalg.eigvals(M)).max(), rel=1e-12)
+    rho_sym, _ = oracle_mod.rho_estimate(A, seed=1, level=0, m=A.n, symmetric=True)
+    assert rho_sym != pytest.approx(rho, rel=1e-6)  # the symmetric part's estimate differs
+
+
+def test_fgmres_nonsymmetric_manufactured(oracle_mod):
+    A = P.convdiff2d(30, 5, pe=2.0)
+    xs = np.sin(np.arange(A.n) * 0.07)
+    b = A.matvec(xs)
+    H = oracle_mod.Hierarchy(A, coarse_max=16, outer=1, restart=10, symmetric=0)
+    x, info = H.solve(b, tol=1e-10, max_iter=300)
+    assert info["status"] == 0 and info["relres"] <= 1e-10
+    assert np.linalg.norm(b - A.matvec(x)) <= 1e-10 * np.linalg.norm(b) * (1 + 1e-6)
+    assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= np.linalg.cond(A.to_dense()) * 1e-10
