@@ -593,21 +593,31 @@ __global__ void __launch_bounds__(256) k_galerkin_smem(
   };
   for (int32_t I = blockIdx.x * wpb + wid; I < nc; I += gridDim.x * wpb) {
     const int32_t m0 = aptr[I], m1 = aptr[I + 1], nm = m1 - m0;
-    // run offsets of the member rows (warp prefix sums over chunks of 32 members)
+    // run offsets of the member rows (warp prefix sums over chunks of 32 members);
+    // each member's row, first CSR position and weight go to shared memory
+    // (sKey, sCnt and sW are free until step 2)
     int32_t total = 0;
     for (int32_t mb = m0; mb < m1; mb += 32) {
       const int32_t m = mb + lane;
-      int32_t len = 0;
+      int32_t len = 0, i = 0, p0 = 0;
+      double pwi = 0.0;
       if (m < m1) {
-        const int32_t i = amem[m];
-        len = rp[i + 1] - rp[i];
+        i = amem[m];
+        p0 = rp[i];
+        pwi = pw[i];
+        len = rp[i + 1] - p0;
       }
       int32_t incl = len;
       for (int o = 1; o < 32; o <<= 1) {
         const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += y;
       }
-      if (m < m1 && total + incl - len < cap) sAux[m - m0] = total + incl - len;
+      if (m < m1 && m - m0 < cap) {
+        if (total + incl - len < cap) sAux[m - m0] = total + incl - len;
+        sKey[m - m0] = i;
+        sCnt[m - m0] = p0;
+        sW[m - m0] = pwi;
+      }
       total += __shfl_sync(0xffffffffu, incl, 31);
     }
     if (total > cap || nm > cap) {
@@ -615,20 +625,40 @@ __global__ void __launch_bounds__(256) k_galerkin_smem(
       continue;
     }
     __syncwarp();
-    // 1. stage the terms in run order, one lane per entry
-    for (int32_t e = lane; e < total; e += 32) {
-      int32_t lo = 0, hi = nm - 1;
-      while (lo < hi) {  // the member whose run segment holds e
-        const int32_t mid = (lo + hi + 1) >> 1;
-        if (sAux[mid] <= e) lo = mid; else hi = mid - 1;
+    // 1. stage the terms in run order, one lane per entry; four entries a lane
+    // per round, so that their loads are in flight together
+    for (int32_t e0 = 0; e0 < total; e0 += 4 * 32) {
+      int32_t ee[4], pp[4], ii[4], jj[4];
+      double pwi[4], vv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        ee[u] = e0 + u * 32 + lane;
+        if (ee[u] < total) {
+          int32_t lo = 0, hi = nm - 1;
+          while (lo < hi) {  // the member whose run segment holds the entry
+            const int32_t mid = (lo + hi + 1) >> 1;
+            if (sAux[mid] <= ee[u]) lo = mid; else hi = mid - 1;
+          }
+          ii[u] = sKey[lo];
+          pp[u] = sCnt[lo] + (ee[u] - sAux[lo]);
+          pwi[u] = sW[lo];
+        }
       }
-      const int32_t i = amem[m0 + lo];
-      const int32_t p = rp[i] + (e - sAux[lo]);
-      const int32_t j = ci[p];
-      sJ[e] = agg[j];
-      sV[e] = __dmul_rn(__dmul_rn(pw[i], val[p]), pw[j]);
-      sPos[e] = p;
-      sMem[e] = i;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (ee[u] < total) {
+          jj[u] = ci[pp[u]];
+          vv[u] = val[pp[u]];
+        }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (ee[u] < total) {
+          const int32_t j = jj[u];
+          sJ[ee[u]] = agg[j];
+          sV[ee[u]] = __dmul_rn(__dmul_rn(pwi[u], vv[u]), pw[j]);
+          sPos[ee[u]] = pp[u];
+          sMem[ee[u]] = ii[u];
+        }
     }
     for (int32_t t = lane; t < hsize; t += 32) hK[t] = -1;
     __syncwarp();
@@ -844,6 +874,7 @@ __global__ void k_build_sell(int32_t n, int32_t nslices, const int32_t *__restri
 // sums, take a ticket, and the block that finishes last sums the partials of
 // all blocks in block order (deterministic) and writes the scalars.
 constexpr int kArnSlots = 8;
+constexpr int kArnoldiMax = 5;  // Arnoldi steps (m <= 5, Eq. damped Jacobi)
 
 __device__ __forceinline__ bool arn_last_block(unsigned *ticket) {
   __shared__ bool last;
@@ -891,17 +922,24 @@ __device__ void arn_totals(const double *part, int ns, double *out_sh) {
   }
 }
 
-// start: W = random start vector in [-1, 1), dh = |A_ii|^-1/2; nrm2 = ||W||^2
+// The products gather U = dh .* W, the unnormalised basis vector scaled by
+// |D|^-1/2, so that an entry costs one FP64 fused multiply-add: the FP64 pipe
+// of the part, not HBM, bounds three operations an entry.
+//
+// start: W = random start vector in [-1, 1), dh = |A_ii|^-1/2, U = dh .* W;
+// nrm2 = ||W||^2
 __global__ void __launch_bounds__(256) k_arn_start(int32_t n, uint64_t seed, int32_t level,
                                                    const double *__restrict__ diag, double *__restrict__ W,
-                                                   double *__restrict__ dh, double *part, double *nrm2,
-                                                   unsigned *ticket) {
+                                                   double *__restrict__ U, double *__restrict__ dh, double *part,
+                                                   double *nrm2, unsigned *ticket) {
   double v[kArnSlots] = {0.0};
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const uint64_t z = splitmix64(~seed ^ ((uint64_t)(uint32_t)level << 40) ^ (uint64_t)(uint32_t)i);
     const double q = 2.0 * ((double)(z >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
+    const double di = 1.0 / sqrt(fabs(diag[i]));
     W[i] = q;
-    dh[i] = 1.0 / sqrt(fabs(diag[i]));
+    dh[i] = di;
+    U[i] = di * q;
     v[0] += q * q;
   }
   arn_block_partials(v, 1, part);
@@ -915,30 +953,55 @@ __global__ void __launch_bounds__(256) k_arn_start(int32_t n, uint64_t seed, int
   }
 }
 
-// step j, part 1: q_j = W / ||W||; w = M q_j; h_lj = q_l . w (l <= j), wn_j = ||w||;
-// h_{j,j-1} = ||W|| (j > 0)
+// step j, part 1: q_j = W / ||W||; w = M q_j = dh .* (A U) / ||W||;
+// h_lj = q_l . w (l <= j), wn_j = ||w||; h_{j,j-1} = ||W|| (j > 0).  T consecutive lanes share a row: lane t sums the
+// row's entries t, t + T, ... and the T partial sums meet in a fixed shuffle tree,
+// so that the entries of a row are read by neighbouring lanes.
+template <int T>
 __global__ void __launch_bounds__(256) k_arn_spmv(int32_t n, int j, const int32_t *__restrict__ rp,
                                                   const int32_t *__restrict__ ci, const double *__restrict__ val,
                                                   const double *__restrict__ dh, const double *__restrict__ W,
-                                                  double *__restrict__ Q, double *__restrict__ w, double *part,
-                                                  const double *nrm2, double *H, double *wn, unsigned *ticket) {
+                                                  const double *__restrict__ U, double *__restrict__ Q,
+                                                  double *__restrict__ w, double *part, const double *nrm2, double *H,
+                                                  double *wn, unsigned *ticket) {
   const double h = sqrt(*nrm2), sc = 1.0 / h;
   double *qj = Q + (size_t)j * n;
+  const int t = threadIdx.x % T;
   double v[kArnSlots] = {0.0};
-  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  const int32_t groups = (int32_t)(gridDim.x * blockDim.x / T);
+  const int32_t g0 = (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) / T);
+  const int32_t rounds = (n + groups - 1) / groups;  // every lane of a group runs the same rounds
+  for (int32_t r = 0; r < rounds; ++r) {
+    const int32_t i = g0 + r * groups;
     double acc = 0.0;
-    for (int32_t p = rp[i]; p < rp[i + 1]; ++p) {
-      const int32_t c = ci[p];
-      acc += val[p] * (dh[c] * (sc * W[c]));
-    }
-    const double wi = dh[i] * acc, qi = sc * W[i];
-    qj[i] = qi;
-    w[i] = wi;
+    if (i < n) {
+      const int32_t p1 = rp[i + 1];
+      for (int32_t p = rp[i] + t; p < p1; p += 4 * T) {
+        int32_t c[4];
+        double a[4];
 #pragma unroll
-    for (int l = 0; l < kArnSlots; ++l) {  // static indices: the sums stay in registers
-      if (l < j) v[l] += Q[(size_t)l * n + i] * wi;
-      else if (l == j) v[l] += qi * wi;
-      else if (l == j + 1) v[l] += wi * wi;
+        for (int u = 0; u < 4; ++u)
+          if (p + u * T < p1) {
+            c[u] = __ldcs(ci + p + u * T);
+            a[u] = __ldcs(val + p + u * T);
+          }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (p + u * T < p1) acc += a[u] * U[c[u]];
+      }
+    }
+#pragma unroll
+    for (int o = T / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, T);
+    if (i < n && t == 0) {
+      const double wi = dh[i] * (sc * acc), qi = sc * W[i];
+      qj[i] = qi;
+      w[i] = wi;
+#pragma unroll
+      for (int l = 0; l < kArnSlots; ++l) {  // static indices: the sums stay in registers
+        if (l < j) v[l] += Q[(size_t)l * n + i] * wi;
+        else if (l == j) v[l] += qi * wi;
+        else if (l == j + 1) v[l] += wi * wi;
+      }
     }
   }
   arn_block_partials(v, j + 2, part);
@@ -960,7 +1023,8 @@ __global__ void __launch_bounds__(256) k_arn_spmv(int32_t n, int j, const int32_
 __global__ void __launch_bounds__(256) k_arn_spmv_sell(int32_t n, int32_t nslices, int j,
                                                        const int64_t *__restrict__ sptr, const int32_t *__restrict__ scol,
                                                        const double *__restrict__ sval, const double *__restrict__ dh,
-                                                       const double *__restrict__ W, double *__restrict__ Q,
+                                                       const double *__restrict__ W, const double *__restrict__ U,
+                                                       double *__restrict__ Q,
                                                        double *__restrict__ w, double *part, const double *nrm2,
                                                        double *H, double *wn, unsigned *ticket) {
   const double h = sqrt(*nrm2), sc = 1.0 / h;
@@ -972,14 +1036,23 @@ __global__ void __launch_bounds__(256) k_arn_spmv_sell(int32_t n, int32_t nslice
     const int64_t base = sptr[sl];
     const int32_t width = (int32_t)((sptr[sl + 1] - base) >> 5);
     double acc = 0.0;
-    for (int32_t e = 0; e < width; ++e) {
-      const int64_t at = base + 32 * (int64_t)e + lane;
-      const int32_t c = __ldcs(scol + at);
-      acc += __ldcs(sval + at) * (dh[c] * (sc * W[c]));
+    for (int32_t e = 0; e < width; e += 8) {  // eight entries' loads in flight, summed in order
+      int32_t c[8];
+      double a[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (e + u < width) {
+          const int64_t at = base + 32 * (int64_t)(e + u) + lane;
+          c[u] = __ldcs(scol + at);
+          a[u] = __ldcs(sval + at);
+        }
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (e + u < width) acc += a[u] * U[c[u]];
     }
     const int32_t i = sl * 32 + lane;
     if (i < n) {
-      const double wi = dh[i] * acc, qi = sc * W[i];
+      const double wi = dh[i] * (sc * acc), qi = sc * W[i];
       qj[i] = qi;
       w[i] = wi;
 #pragma unroll
@@ -1005,27 +1078,55 @@ __global__ void __launch_bounds__(256) k_arn_spmv_sell(int32_t n, int32_t nslice
 
 // step j, parts 2 and 3 (classical Gram-Schmidt twice): w -= sum_l c_l q_l with
 // c = H[.][j] (pass 0) or the correction corr (pass 1).  Pass 0 ends with
-// corr_l = q_l . w; pass 1 adds corr to H[.][j], writes W = w and nrm2 = ||w||^2.
+// corr_l = q_l . w; pass 1 adds corr to H[.][j], writes W = w, U = dh .* w and
+// nrm2 = ||w||^2.
 __global__ void __launch_bounds__(256) k_arn_orth(int32_t n, int j, int pass, const double *__restrict__ Q,
-                                                  double *__restrict__ w, double *__restrict__ W, double *part,
-                                                  double *H, double *corr, double *nrm2, unsigned *ticket) {
-  double c[kArnSlots];
+                                                  double *__restrict__ w, double *__restrict__ W,
+                                                  double *__restrict__ U, const double *__restrict__ dh,
+                                                  double *part, double *H, double *corr, double *nrm2,
+                                                  unsigned *ticket) {
+  double c[kArnoldiMax];
 #pragma unroll
-  for (int l = 0; l < kArnSlots; ++l) c[l] = l <= j ? (pass == 0 ? H[l * 8 + j] : corr[l]) : 0.0;
+  for (int l = 0; l < kArnoldiMax; ++l) c[l] = l <= j ? (pass == 0 ? H[l * 8 + j] : corr[l]) : 0.0;
   double v[kArnSlots] = {0.0};
-  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    double wi = w[i];
+  // two rows per thread and round (i, i + stride), their loads issued together;
+  // each thread still takes its rows in increasing order
+  const int32_t stride = gridDim.x * blockDim.x;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 2 * stride) {
+    const int32_t i2 = i + stride;
+    const bool two = i2 < n;
+    double q1[kArnoldiMax], q2[kArnoldiMax];
+    double wi = w[i], wi2 = two ? w[i2] : 0.0;
 #pragma unroll
-    for (int l = 0; l < kArnSlots; ++l)
-      if (l <= j) wi -= c[l] * Q[(size_t)l * n + i];
+    for (int l = 0; l < kArnoldiMax; ++l)
+      if (l <= j) {
+        q1[l] = Q[(size_t)l * n + i];
+        q2[l] = two ? Q[(size_t)l * n + i2] : 0.0;
+      }
+#pragma unroll
+    for (int l = 0; l < kArnoldiMax; ++l)
+      if (l <= j) {
+        wi -= c[l] * q1[l];
+        wi2 -= c[l] * q2[l];
+      }
     if (pass == 0) {
       w[i] = wi;
+      if (two) w[i2] = wi2;
 #pragma unroll
-      for (int l = 0; l < kArnSlots; ++l)
-        if (l <= j) v[l] += Q[(size_t)l * n + i] * wi;
+      for (int l = 0; l < kArnoldiMax; ++l)
+        if (l <= j) {
+          v[l] += q1[l] * wi;
+          if (two) v[l] += q2[l] * wi2;
+        }
     } else {
       W[i] = wi;
+      U[i] = dh[i] * wi;
       v[0] += wi * wi;
+      if (two) {
+        W[i2] = wi2;
+        U[i2] = dh[i2] * wi2;
+        v[0] += wi2 * wi2;
+      }
     }
   }
   const int ns = pass == 0 ? j + 1 : 1;
@@ -1046,7 +1147,6 @@ __global__ void __launch_bounds__(256) k_arn_orth(int32_t n, int j, int pass, co
 // Largest |eigenvalue| of a small symmetric matrix by bisection on the inertia
 // of T - sigma I (Sylvester's law: the number of negative pivots of Gaussian
 // elimination without pivoting equals the number of eigenvalues below sigma).
-constexpr int kArnoldiMax = 5;  // Arnoldi steps (m <= 5, Eq. damped Jacobi)
 
 // fully unrolled over the 5 x 5 bound so that the matrix stays in registers;
 // rows and columns beyond m act as an identity block (no negative pivots)
@@ -1570,26 +1670,34 @@ void estimate_omega(Hierarchy &h, int k, const double *diag, double *omega_dev, 
   const int32_t n = L.n;
   const int m = n < kArnoldiMax ? n : kArnoldiMax;
   const int g = grid_for(n, 256, kRedBlocks);  // a few rows per thread; few partials to reduce
-  DevBuf<double> Q((size_t)n * m), W(n), w(n), dh(n), part((size_t)kArnSlots * kRedBlocks), H(9 * 8), wn(8),
+  DevBuf<double> Q((size_t)n * m), W(n), U(n), w(n), dh(n), part((size_t)kArnSlots * kRedBlocks), H(9 * 8), wn(8),
       corr(8), nrm2(1);
   // an FP64 SELL copy of every entry: level 0 always, every level in FP64 mode
   const int64_t *sp64 = k == 0 ? L.sptr64 : (h.p.precision == AMG_PREC_F64 ? L.sptr : nullptr);
   const int32_t *sc64 = k == 0 ? L.scol64 : L.scol;
   const double *sv64 = k == 0 ? L.sval64 : static_cast<const double *>(L.sval);
   const int gs = grid_for(L.nslices, 8, kRedBlocks);
+  // CSR rows: 8 lanes a row from 16 entries a row on average, else 4
+  const bool wide = L.nnz >= 16 * (int64_t)n;
+  const int gc = grid_for((int64_t)n * (wide ? 8 : 4), 256, kRedBlocks);
   DevBuf<unsigned> ticket(1);
   AMG_CUDA(cudaMemsetAsync(H.p, 0, sizeof(double) * 72, s));
   AMG_CUDA(cudaMemsetAsync(ticket.p, 0, sizeof(unsigned), s));
-  AMG_COUNT(), k_arn_start<<<g, 256, 0, s>>>(n, h.p.seed, k, diag, W.p, dh.p, part.p, nrm2.p, ticket.p);
+  AMG_COUNT(), k_arn_start<<<g, 256, 0, s>>>(n, h.p.seed, k, diag, W.p, U.p, dh.p, part.p, nrm2.p, ticket.p);
   for (int j = 0; j < m; ++j) {
     if (sp64)
-      AMG_COUNT(), k_arn_spmv_sell<<<gs, 256, 0, s>>>(n, L.nslices, j, sp64, sc64, sv64, dh.p, W.p, Q.p, w.p, part.p,
-                                                      nrm2.p, H.p, wn.p, ticket.p);
+      AMG_COUNT(), k_arn_spmv_sell<<<gs, 256, 0, s>>>(n, L.nslices, j, sp64, sc64, sv64, dh.p, W.p, U.p, Q.p, w.p,
+                                                      part.p, nrm2.p, H.p, wn.p, ticket.p);
+    else if (wide)
+      AMG_COUNT(), k_arn_spmv<8><<<gc, 256, 0, s>>>(n, j, L.rp, L.ci, L.val, dh.p, W.p, U.p, Q.p, w.p, part.p, nrm2.p,
+                                                    H.p, wn.p, ticket.p);
     else
-      AMG_COUNT(), k_arn_spmv<<<g, 256, 0, s>>>(n, j, L.rp, L.ci, L.val, dh.p, W.p, Q.p, w.p, part.p, nrm2.p, H.p,
-                                                wn.p, ticket.p);
-    AMG_COUNT(), k_arn_orth<<<g, 256, 0, s>>>(n, j, 0, Q.p, w.p, W.p, part.p, H.p, corr.p, nrm2.p, ticket.p);
-    AMG_COUNT(), k_arn_orth<<<g, 256, 0, s>>>(n, j, 1, Q.p, w.p, W.p, part.p, H.p, corr.p, nrm2.p, ticket.p);
+      AMG_COUNT(), k_arn_spmv<4><<<gc, 256, 0, s>>>(n, j, L.rp, L.ci, L.val, dh.p, W.p, U.p, Q.p, w.p, part.p, nrm2.p,
+                                                    H.p, wn.p, ticket.p);
+    AMG_COUNT(), k_arn_orth<<<g, 256, 0, s>>>(n, j, 0, Q.p, w.p, W.p, U.p, dh.p, part.p, H.p, corr.p, nrm2.p,
+                                               ticket.p);
+    AMG_COUNT(), k_arn_orth<<<g, 256, 0, s>>>(n, j, 1, Q.p, w.p, W.p, U.p, dh.p, part.p, H.p, corr.p, nrm2.p,
+                                               ticket.p);
   }
   AMG_COUNT(), k_omega_from_H<<<1, 32, 0, s>>>(H.p, wn.p, m, h.p.symmetric, omega_dev);
   AMG_LAUNCH_CHECK();

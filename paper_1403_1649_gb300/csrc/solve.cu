@@ -133,8 +133,12 @@ constexpr int sell_min_blocks() { return sizeof(VT) == 4 ? 6 : 4; }
 // plain SpMV does not hold their accumulators in registers)
 // GATE: a batch's launch, skipping slices whose systems have all stopped
 // (compiled only into the batch instantiations)
-template <class MV, class VT, int EPI, bool DOTS, bool GATE>
-__global__ void __launch_bounds__(kThreads, sell_min_blocks<VT>()) k_sell(SellArgs<VT> a) {
+// UW: entries a row per step on small levels (0: the default below).  A level of
+// a few hundred slices leaves most of the GPU idle and each warp's chain of
+// dependent loads sets the time, so there every load of a coarse row (15-30
+// entries) goes out in one or two steps.
+template <class MV, class VT, int EPI, bool DOTS, bool GATE, int UW = 0>
+__global__ void __launch_bounds__(kThreads, UW ? 1 : sell_min_blocks<VT>()) k_sell(SellArgs<VT> a) {
   pdl_wait_and_trigger();
   if (a.pred && *a.pred == 0) return;
   const int lane = threadIdx.x & 31;
@@ -142,7 +146,7 @@ __global__ void __launch_bounds__(kThreads, sell_min_blocks<VT>()) k_sell(SellAr
   double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
   // U entries of a row per step: 6 with FP32 vectors (a 7-point row without its
   // split-off diagonal in one step, at 40 registers), 8 with FP64
-  constexpr int U = sizeof(VT) == 4 ? 6 : 8;
+  constexpr int U = UW ? UW : (sizeof(VT) == 4 ? 6 : 8);
   for (int32_t sl = blockIdx.x * kWarps + (threadIdx.x >> 5); sl < a.nslices; sl += gridDim.x * kWarps) {
     if (GATE && !a.live[sl]) continue;
     const int32_t row = sl * 32 + lane;
@@ -221,6 +225,18 @@ __global__ void k_scale(int32_t n, VT *__restrict__ out, const VT *__restrict__ 
     if (!bact || bact[sys[i]]) out[i] = wd[i] * rhs[i];
 }
 
+// sum_{i in G_I} P(i, I) r(i) over the members amem[m0..m1) in their (ascending) order
+template <class VT>
+__device__ __forceinline__ VT restrict_row(int32_t m0, int32_t m1, const int32_t *__restrict__ amem,
+                                          const VT *__restrict__ pw, const VT *__restrict__ r) {
+  VT s = VT(0);
+  for (int32_t m = m0; m < m1; ++m) {
+    const int32_t i = amem[m];
+    s += pw[i] * r[i];
+  }
+  return s;
+}
+
 // r_{k+1}(I) = sum_{i in G_I} P(i, I) r_k(i) in ascending fine index; also the
 // next level's smoothing start x0 = wd_{k+1} * r_{k+1} when that level smooths.
 template <class VT>
@@ -232,11 +248,7 @@ __global__ void k_restrict(int32_t nc, const int32_t *__restrict__ aptr, const i
   if (pred && *pred == 0) return;
   for (int32_t I = blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += gridDim.x * blockDim.x) {
     if (bact && !bact[sysc[I]]) continue;
-    VT s = VT(0);
-    for (int32_t m = aptr[I]; m < aptr[I + 1]; ++m) {
-      const int32_t i = amem[m];
-      s += pw[i] * r[i];
-    }
+    const VT s = restrict_row(aptr[I], aptr[I + 1], amem, pw, r);
     bc[I] = s;
     if (wdc) x0c[I] = wdc[I] * s;
   }
@@ -263,6 +275,28 @@ __global__ void k_coarse(int32_t nL, const double *__restrict__ Ainv, const VT *
   for (int32_t i = blockIdx.x * kWarps + (threadIdx.x >> 5); i < nL; i += gridDim.x * kWarps) {
     double s = 0.0;
     for (int32_t j = lane; j < nL; j += 32) s += Ainv[(int64_t)i * nL + j] * (double)b[j];
+    s = warp_sum(s);
+    if (lane == 0) x[i] = (VT)s;
+  }
+}
+
+// restriction to the coarsest level and its exact solve in one launch: every
+// block forms r_L = R r (as k_restrict does) in shared memory, then its warps
+// take rows of x = A_L^-1 r_L (as k_coarse does)
+constexpr int kFusedCoarseMax = 2048;
+template <class VT>
+__global__ void k_restrict_coarse(int32_t nL, const int32_t *__restrict__ aptr, const int32_t *__restrict__ amem,
+                                  const VT *__restrict__ pw, const VT *__restrict__ r, const double *__restrict__ Ainv,
+                                  VT *__restrict__ x, const int *pred) {
+  __shared__ VT bsh[kFusedCoarseMax];
+  pdl_wait_and_trigger();
+  if (pred && *pred == 0) return;
+  for (int32_t I = threadIdx.x; I < nL; I += blockDim.x) bsh[I] = restrict_row(aptr[I], aptr[I + 1], amem, pw, r);
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  for (int32_t i = blockIdx.x * kWarps + (threadIdx.x >> 5); i < nL; i += gridDim.x * kWarps) {
+    double s = 0.0;
+    for (int32_t j = lane; j < nL; j += 32) s += Ainv[(int64_t)i * nL + j] * (double)bsh[j];
     s = warp_sum(s);
     if (lane == 0) x[i] = (VT)s;
   }
@@ -948,6 +982,11 @@ inline int default_sell_grid(const Level &L) {
   return grid_for((int64_t)L.nslices, kWarps, sell_min_blocks<VT>() * 152);
 }
 inline int sell_grid(const Level &L) { return L.sell_blocks; }
+// levels of at most kSmallSlices slices (fewer warps than the GPU holds at a
+// quarter of its occupancy) run the products with kSmallU entries a step, with
+// FP32 vectors (measured: no gain with FP64 vectors)
+constexpr int32_t kSmallSlices = 2048;
+constexpr int kSmallU = 16;
 inline int outer_grid(const Level &L0) { return default_sell_grid<double>(L0); }
 
 template <class MV, class VT>
@@ -996,8 +1035,15 @@ struct Engine {
       check();
       return;
     }
+    const bool small = sizeof(VT) == 4 && h.lev[k].nslices <= kSmallSlices;
     if constexpr (EPI == E_Y || EPI == E_POST || EPI == E_HORNER_LAST) {
       if (a.ndot) {
+        if constexpr (EPI == E_Y)
+          if (small) {
+            klaunch(k_sell<MV, VT, EPI, true, false, kSmallU>, sell_grid(h.lev[k]), kThreads, s, a);
+            check();
+            return;
+          }
         klaunch(k_sell<MV, VT, EPI, true, false>, sell_grid(h.lev[k]), kThreads, s, a);
         check();
         return;
@@ -1005,6 +1051,12 @@ struct Engine {
     } else {
       if (a.ndot) throw Error{AMG_ERR_UNSUPPORTED, "SpMV epilogue without fused inner products was given some"};
     }
+    if constexpr (EPI == E_Y || EPI == E_RESID || EPI == E_POST)
+      if (small) {
+        klaunch(k_sell<MV, VT, EPI, false, false, kSmallU>, sell_grid(h.lev[k]), kThreads, s, a);
+        check();
+        return;
+      }
     klaunch(k_sell<MV, VT, EPI, false, false>, sell_grid(h.lev[k]), kThreads, s, a);
     check();
   }
@@ -1048,10 +1100,18 @@ struct Engine {
     }
     const bool coarse_is_last = (k + 1 == h.L - 1);
     const bool tail = (k + 1 == h.tail_t);
-    // r_{k+1} = R_k r_k  (and x0 of level k+1 when it smooths)
-    klaunch(k_restrict<VT>, ew_grid(L.nc), kThreads, s, L.nc, L.aptr, L.amem, V(L.pw), V(L.r), V(C.bc),
-            (coarse_is_last || tail) ? nullptr : V(C.wd), V(C.tmp), pred, bsys(C), bact());
-    check();
+    // single systems: the restriction to the coarsest level and its solve in one launch
+    const bool fuse_coarse = coarse_is_last && !tail && !h.batched && h.nL <= kFusedCoarseMax;
+    if (fuse_coarse) {
+      klaunch(k_restrict_coarse<VT>, grid_for(h.nL, kWarps, 152), kThreads, s, h.nL, L.aptr, L.amem, V(L.pw),
+              V(L.r), h.coarse_inv, V(C.xc), pred);
+      check();
+    } else {
+      // r_{k+1} = R_k r_k  (and x0 of level k+1 when it smooths)
+      klaunch(k_restrict<VT>, ew_grid(L.nc), kThreads, s, L.nc, L.aptr, L.amem, V(L.pw), V(L.r), V(C.bc),
+              (coarse_is_last || tail) ? nullptr : V(C.wd), V(C.tmp), pred, bsys(C), bact());
+      check();
+    }
     if (tail) {  // levels k+1..L-1 in one cluster launch
       TailArgs ta{};
       ta.t = k + 1;
@@ -1066,7 +1126,7 @@ struct Engine {
       tail_launch<MV, VT>(ta, h.p.tail == 2 ? 1 : 8, s);
       ++launches;
     } else if (coarse_is_last) {
-      cycle(k + 1, V(C.bc), V(C.xc), true, pred);  // exact coarse solve
+      if (!fuse_coarse) cycle(k + 1, V(C.bc), V(C.xc), true, pred);  // exact coarse solve
     } else if (k < h.p.kcycle_levels) {
       krylov2(k + 1, pred);  // Alg. 5 coarse correction
     } else {
@@ -1176,13 +1236,14 @@ struct Engine {
       }
       sell<E_Y>(a, m);
     }
+    // One-block kernels take the scalars: with programmatic dependent launch
+    // their launch costs less than every block of the vector kernel summing the
+    // partials itself.
     klaunch(k_fin_k1, 1, kThreads, s, L.partials, nb, L.slots, pred);
     check();
-    const bool deeper_smooths = true;  // level m is not the coarsest here
-    (void)deeper_smooths;
     const int ng = ew_grid(L.n);
     klaunch(k_axpy_rt<VT>, ng, kThreads, s, L.n, V(L.bc), V(L.v), V(L.rt), V(L.wd), V(L.tmp), L.slots,
-                                          L.partials + 3 * kRedBlocks, pred);
+            L.partials + 3 * kRedBlocks, pred);
     check();
     klaunch(k_decide, 1, kThreads, s, L.partials + 3 * kRedBlocks, ng, L.slots, h.p.kcycle_t, pred, L.flag);
     check();
