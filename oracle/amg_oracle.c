@@ -137,7 +137,7 @@ int64_t or_sym_graph(int32_t n, const int32_t *rp, const int32_t *ci, const uint
 }
 
 /* ------------------------------------------------------------------------- */
-/* Alg. 2: PMIS(2)                                                            */
+/* Alg. 2: PMIS(2), and MIS(k) with k max rounds (Sec. 2.1.2)                 */
 /* ------------------------------------------------------------------------- */
 typedef struct {
   int32_t s;     /* state: 1 MIS, 0 undecided, -1 not MIS */
@@ -154,8 +154,8 @@ static int tuple_greater(tuple_t a, tuple_t b) {
   return a.i > b.i;
 }
 
-int32_t or_pmis2(int32_t n, const int32_t *Sptr, const int32_t *Scol, const int32_t *count,
-                 const uint32_t *h, int8_t *s) {
+int32_t or_pmis(int32_t n, const int32_t *Sptr, const int32_t *Scol, const int32_t *count,
+                const uint32_t *h, int8_t *s, int32_t k) {
   tuple_t *T = (tuple_t *)malloc(sizeof(tuple_t) * (size_t)(n + 1));
   tuple_t *That = (tuple_t *)malloc(sizeof(tuple_t) * (size_t)(n + 1));
   for (int32_t i = 0; i < n; ++i) s[i] = 0; /* every node undecided */
@@ -171,7 +171,7 @@ int32_t or_pmis2(int32_t n, const int32_t *Sptr, const int32_t *Scol, const int3
       T[i].h = h[i];
       T[i].i = i;
     }
-    for (int d = 1; d <= 2; ++d) { /* two rounds of max over the closed neighbourhood */
+    for (int d = 1; d <= k; ++d) { /* k rounds of max over the closed neighbourhood */
       for (int32_t i = 0; i < n; ++i) {
         tuple_t t = T[i];
         for (int32_t q = Sptr[i]; q < Sptr[i + 1]; ++q)
@@ -205,10 +205,11 @@ static int key_greater(int32_t a, int32_t b, const int32_t *count, const uint32_
 /* Sec. 2.1.2: every non-MIS node is aggregated with its nearest MIS node.
  * Reading of the unstated tie-break: among MIS nodes at the same distance the
  * one with the largest priority (v, i) wins.  Pass 1 joins nodes adjacent to
- * a root; pass 2 joins the remaining nodes through a pass-1 neighbour.  Roots
+ * a root; pass d = 2..k joins the remaining nodes through a neighbour assigned
+ * by pass d-1 (for MIS(k) every node is within distance k of a root).  Roots
  * are numbered 0..n_c-1 in ascending fine index. */
 int32_t or_aggregate(int32_t n, const int32_t *Sptr, const int32_t *Scol, const int32_t *count,
-                     const uint32_t *h, const int8_t *s, int32_t *agg) {
+                     const uint32_t *h, const int8_t *s, int32_t *agg, int32_t k) {
   int32_t *r1 = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n + 1));
   int32_t *r2 = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n + 1));
   int32_t *cid = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n + 1));
@@ -222,19 +223,23 @@ int32_t or_aggregate(int32_t n, const int32_t *Sptr, const int32_t *Scol, const 
     }
     r1[i] = best;
   }
-  for (int32_t i = 0; i < n; ++i) r2[i] = r1[i];
-  for (int32_t i = 0; i < n; ++i) {
-    if (r1[i] >= 0) continue;
-    int32_t best = -1;
-    for (int32_t q = Sptr[i]; q < Sptr[i + 1]; ++q) {
-      int32_t j = Scol[q];
-      if (s[j] != 1 && r1[j] >= 0) {
-        int32_t r = r1[j];
-        if (best < 0 || key_greater(r, best, count, h)) best = r;
+  for (int32_t d = 2; d <= k; ++d) { /* r1: passes < d; r2: after pass d */
+    for (int32_t i = 0; i < n; ++i) r2[i] = r1[i];
+    for (int32_t i = 0; i < n; ++i) {
+      if (r1[i] >= 0) continue;
+      int32_t best = -1;
+      for (int32_t q = Sptr[i]; q < Sptr[i + 1]; ++q) {
+        int32_t j = Scol[q];
+        if (s[j] != 1 && r1[j] >= 0) {
+          int32_t r = r1[j];
+          if (best < 0 || key_greater(r, best, count, h)) best = r;
+        }
       }
+      r2[i] = best;
     }
-    r2[i] = best;
+    for (int32_t i = 0; i < n; ++i) r1[i] = r2[i];
   }
+  for (int32_t i = 0; i < n; ++i) r2[i] = r1[i];
   int32_t nc = 0;
   for (int32_t i = 0; i < n; ++i) cid[i] = (s[i] == 1) ? nc++ : -1;
   int32_t ok = 1;
@@ -617,6 +622,7 @@ void or_default_params(or_params *p) {
   p->restart = 30;
   p->smoother = 0;
   p->symmetric = 1;
+  p->mis_k = 2;
 }
 
 static double *dalloc(size_t n) { return (double *)calloc(n + 1, sizeof(double)); }
@@ -672,6 +678,10 @@ or_hier *or_setup(int32_t n, const int32_t *rp, const int32_t *ci, const double 
                   const or_params *p, int32_t *err) {
   *err = check_csr(n, rp, ci, val);
   if (*err) return NULL;
+  if (p->mis_k < 1 || p->mis_k > 8) {
+    *err = -2;
+    return NULL;
+  }
   or_hier *h = (or_hier *)calloc(1, sizeof(or_hier));
   h->p = *p;
   or_level *l0 = &h->lev[0];
@@ -702,8 +712,8 @@ or_hier *or_setup(int32_t n, const int32_t *rp, const int32_t *ci, const double 
     int32_t *Scol = (int32_t *)malloc(sizeof(int32_t) * (size_t)(ns + 1));
     or_sym_graph(nk, L->rp, L->ci, C, Sptr, Scol, ns);
     for (int32_t i = 0; i < nk; ++i) hh[i] = or_mis_hash(p->seed, k, i);
-    L->mis_rounds = or_pmis2(nk, Sptr, Scol, count, hh, s);           /* Agg_k = aggregate(C_k) */
-    int32_t nc = or_aggregate(nk, Sptr, Scol, count, hh, s, agg);
+    L->mis_rounds = or_pmis(nk, Sptr, Scol, count, hh, s, p->mis_k); /* Agg_k = aggregate(C_k) */
+    int32_t nc = or_aggregate(nk, Sptr, Scol, count, hh, s, agg, p->mis_k);
     free(C); free(count); free(Sptr); free(Scol); free(hh); free(s);
     if (nc < 0) {
       free(agg);

@@ -40,6 +40,8 @@ typedef struct or_params {
   int32_t symmetric;   /* 1: A symmetric (rho from the symmetric part of H, Cholesky
                           coarsest factor); 0: nonsymmetric (rho from the
                           eigenvalues of H, LU coarsest factor; use FGMRES)        */
+  int32_t mis_k;       /* roots form an MIS(k) (Sec. 2.1.2: k = 2; k > 2 coarsens
+                          more aggressively); aggregates reach distance k          */
 } or_params;
 
 /* ---- individual setup steps (used directly by the pin tests) ---- */
@@ -57,13 +59,15 @@ int64_t or_sym_graph(int32_t n, const int32_t *rp, const int32_t *ci, const uint
 /* The random part r_i of Alg. 2, as a 32-bit integer (r_i = (h_i + 0.5) / 2^32). */
 uint32_t or_mis_hash(uint64_t seed, int32_t level, int32_t i);
 uint64_t or_splitmix64(uint64_t x);
-/* Alg. 2, PMIS(2).  s[i] = 1 (MIS), -1 (not MIS).  Returns the number of rounds. */
-int32_t or_pmis2(int32_t n, const int32_t *Sptr, const int32_t *Scol, const int32_t *count,
-                 const uint32_t *h, int8_t *s);
-/* Aggregation: every non-MIS node joins its nearest MIS node (Sec. 2.1.2).
- * Returns n_c, or -1 if some node could not be assigned.                   */
+/* Alg. 2 generalised to MIS(k) (Sec. 2.1.2; k = 2 is Alg. 2 as printed): k
+ * rounds of max over the closed neighbourhood per iteration.  s[i] = 1 (MIS),
+ * -1 (not MIS).  Returns the number of iterations. */
+int32_t or_pmis(int32_t n, const int32_t *Sptr, const int32_t *Scol, const int32_t *count,
+                const uint32_t *h, int8_t *s, int32_t k);
+/* Aggregation: every non-MIS node joins its nearest MIS node, at distance at
+ * most k (Sec. 2.1.2).  Returns n_c, or -1 if some node could not be assigned. */
 int32_t or_aggregate(int32_t n, const int32_t *Sptr, const int32_t *Scol, const int32_t *count,
-                     const uint32_t *h, const int8_t *s, int32_t *agg);
+                     const uint32_t *h, const int8_t *s, int32_t *agg, int32_t k);
 /* Alg. 3 interpolation: P[i] = B(i)/B_c(agg(i)), B_c(I) = ||B restricted to G_I||_2. */
 void or_interp(int32_t n, int32_t nc, const int32_t *agg, const double *B, double *P,
                double *Bc);

@@ -40,6 +40,7 @@ class ORParams(C.Structure):
         ("restart", C.c_int32),
         ("smoother", C.c_int32),
         ("symmetric", C.c_int32),
+        ("mis_k", C.c_int32),
     ]
 
 
@@ -72,9 +73,9 @@ def lib():
         L.or_mis_hash.restype = C.c_uint32
         L.or_splitmix64.argtypes = [C.c_uint64]
         L.or_splitmix64.restype = C.c_uint64
-        L.or_pmis2.argtypes = [C.c_int32, _i32p, _i32p, _i32p, _u32p, _i8p]
-        L.or_pmis2.restype = C.c_int32
-        L.or_aggregate.argtypes = [C.c_int32, _i32p, _i32p, _i32p, _u32p, _i8p, _i32p]
+        L.or_pmis.argtypes = [C.c_int32, _i32p, _i32p, _i32p, _u32p, _i8p, C.c_int32]
+        L.or_pmis.restype = C.c_int32
+        L.or_aggregate.argtypes = [C.c_int32, _i32p, _i32p, _i32p, _u32p, _i8p, _i32p, C.c_int32]
         L.or_aggregate.restype = C.c_int32
         L.or_interp.argtypes = [C.c_int32, C.c_int32, _i32p, _f64p, _f64p, _f64p]
         L.or_galerkin.argtypes = [C.c_int32, _i32p, _i32p, _f64p, C.c_int32, _i32p, C.c_void_p, _i32p,
@@ -159,21 +160,26 @@ def splitmix64(x: int) -> int:
     return int(lib().or_splitmix64(x))
 
 
-def pmis2(Sptr, Scol, count, h):
+def pmis(Sptr, Scol, count, h, k: int = 2):
+    """Alg. 2 with k max rounds per iteration: the roots of MIS(k) (Sec. 2.1.2)."""
     n = len(Sptr) - 1
     s = np.zeros(n, np.int8)
     Scol = np.ascontiguousarray(Scol, np.int32) if len(Scol) else np.zeros(1, np.int32)
-    rounds = lib().or_pmis2(n, np.ascontiguousarray(Sptr, np.int32), Scol, np.ascontiguousarray(count, np.int32),
-                            np.ascontiguousarray(h, np.uint32), s)
+    rounds = lib().or_pmis(n, np.ascontiguousarray(Sptr, np.int32), Scol, np.ascontiguousarray(count, np.int32),
+                           np.ascontiguousarray(h, np.uint32), s, k)
     return s, rounds
 
 
-def aggregate(Sptr, Scol, count, h, s):
+def pmis2(Sptr, Scol, count, h):
+    return pmis(Sptr, Scol, count, h, 2)
+
+
+def aggregate(Sptr, Scol, count, h, s, k: int = 2):
     n = len(Sptr) - 1
     agg = np.zeros(n, np.int32)
     Scol = np.ascontiguousarray(Scol, np.int32) if len(Scol) else np.zeros(1, np.int32)
     nc = lib().or_aggregate(n, np.ascontiguousarray(Sptr, np.int32), Scol, np.ascontiguousarray(count, np.int32),
-                            np.ascontiguousarray(h, np.uint32), np.ascontiguousarray(s, np.int8), agg)
+                            np.ascontiguousarray(h, np.uint32), np.ascontiguousarray(s, np.int8), agg, k)
     return agg, nc
 
 

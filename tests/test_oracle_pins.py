@@ -229,6 +229,96 @@ def test_aggregates_on_grid(oracle_mod):
     assert sizes.max() <= 13 and A.n / nc > 3
 
 
+# ----------------------------------------------------------------- MIS(k), k != 2
+def greedy_mis_k(adj, count, h, k):
+    """Sequential greedy MIS on the k-th power of the graph (nodes within distance
+    k are adjacent), nodes in descending (count, h, i)."""
+    n = len(adj)
+    order = sorted(range(n), key=lambda i: (int(count[i]), int(h[i]), i), reverse=True)
+    blocked = np.zeros(n, bool)
+    s = -np.ones(n, np.int8)
+    for i in order:
+        if blocked[i]:
+            continue
+        s[i] = 1
+        for j in bfs_dist(adj, i, k):
+            blocked[j] = True
+    return s
+
+
+@pytest.mark.parametrize("k,seed", [(1, 0), (3, 1), (3, 2), (4, 3)])
+def test_pmis_k_equals_greedy_mis_on_graph_power(oracle_mod, k, seed):
+    n = 300
+    Sptr, Scol, adj = random_sym_graph(n, 4, seed)
+    rng = np.random.default_rng(200 + seed)
+    count = rng.integers(0, 5, n).astype(np.int32)
+    h = oracle_mod.mis_hash(seed, 0, n)
+    s, rounds = oracle_mod.pmis(Sptr, Scol, count, h, k)
+    assert rounds >= 1
+    assert np.array_equal(s, greedy_mis_k(adj, count, h, k))
+
+
+def root_distance(adj, roots):
+    """multi-source breadth-first distance to the nearest root"""
+    d = {int(r): 0 for r in roots}
+    frontier = list(d)
+    while frontier:
+        nxt = []
+        for u in frontier:
+            for v in adj[u]:
+                if v not in d:
+                    d[v] = d[u] + 1
+                    nxt.append(v)
+        frontier = nxt
+    return d
+
+
+def check_aggregates_k(adj, s, agg, nc, count, h, k):
+    """every node joins a nearest root (distance <= k); among the roots reached
+    through neighbours one step nearer, the largest priority (pass d of the
+    aggregation takes the nodes at distance d)"""
+    roots = np.flatnonzero(s == 1)
+    assert nc == len(roots) and agg[roots].tolist() == list(range(nc))
+    assert (agg >= 0).all() and (agg < nc).all()
+    root_of = {int(agg[r]): int(r) for r in roots}
+    key = lambda r: (int(count[r]), int(h[r]), r)
+    rootset = set(roots.tolist())
+    dist = root_distance(adj, roots)
+    assert len(dist) == len(adj) and max(dist.values()) <= k
+    for i in np.flatnonzero(s != 1):
+        i = int(i)
+        r = root_of[int(agg[i])]
+        if dist[i] == 1:
+            expect = max((j for j in adj[i] if j in rootset), key=key)
+        else:
+            expect = max((root_of[int(agg[j])] for j in adj[i] if dist[j] == dist[i] - 1), key=key)
+        assert r == expect
+        assert bfs_dist(adj, i, k).get(r) == dist[i], "member not joined to a nearest root"
+
+
+@pytest.mark.parametrize("k,seed", [(1, 7), (2, 8), (3, 9), (4, 10)])
+def test_aggregate_k_nearest_root_rule(oracle_mod, k, seed):
+    n = 400
+    Sptr, Scol, adj = random_sym_graph(n, 3, seed)
+    count = np.array([len(a) for a in adj], np.int32)
+    h = oracle_mod.mis_hash(seed, 1, n)
+    s, _ = oracle_mod.pmis(Sptr, Scol, count, h, k)
+    agg, nc = oracle_mod.aggregate(Sptr, Scol, count, h, s, k)
+    check_aggregates_k(adj, s, agg, nc, count, h, k)
+
+
+def test_mis3_coarsens_more_and_still_converges(oracle_mod):
+    A = P.poisson2d(40)
+    b = P.rhs_uniform(A.n, 4)
+    n1 = {}
+    for k in (2, 3):
+        H = oracle_mod.Hierarchy(A, alpha=0.25, seed=1, mis_k=k)
+        n1[k] = H.level(1).n
+        x, info = H.solve(b, tol=1e-8, max_iter=200)
+        assert info["status"] == 0 and np.linalg.norm(b - A.matvec(x)) <= 1e-8 * np.linalg.norm(b) * (1 + 1e-6)
+    assert n1[3] < n1[2] / 1.5
+
+
 # ----------------------------------------------------------------- interpolation
 def test_interp_orthonormal_and_reproduces_B(oracle_mod):
     rng = np.random.default_rng(0)
