@@ -418,18 +418,19 @@ def main():
     xd = torch.zeros_like(bd)
     stream = torch.cuda.current_stream(dev)
 
-    def params(prec):
-        return amg.amg_default_params(alpha=ALPHA, seed=SEED, precision=PREC[prec], max_iter=500)
+    def params(prec, **kw):
+        return amg.amg_default_params(alpha=ALPHA, seed=SEED, precision=PREC[prec], max_iter=500, **kw)
 
     stats = {}
 
-    def step(prec):
-        h = amg.amg_setup(rp, ci, va, params(prec), stream.cuda_stream)
+    def step(prec, tag=None, **kw):
+        h = amg.amg_setup(rp, ci, va, params(prec, **kw), stream.cuda_stream)
         xd.zero_()
         rc, it, _ = amg.amg_solve(h, bd, xd, TOL, 500, stream.cuda_stream)
         info = amg.amg_last_solve_info(h)
+        info["levels"] = [lv["n"] for lv in amg.amg_hierarchy_info(h)]
         amg.amg_free(h)
-        stats.setdefault(prec, []).append(info)
+        stats.setdefault(tag or prec, []).append(info)
         return info
 
     prec = args.precision
@@ -465,6 +466,14 @@ def main():
             extra[cmp] = {"setup_ms": inf["setup_ms"], "solve_ms": inf["solve_ms"], "iters": inf["iters"],
                           "final_relres": inf["final_relres"],
                           "solve_dof_per_s": n / (inf["solve_ms"] / 1e3)}
+        # aggressive coarsening: MIS(3) roots and distance-3 aggregates (Sec. 2.1.2)
+        for _ in range(3):
+            inf = step(prec, tag="mis3", mis_k=3)
+        assert inf["status"] == 0 and inf["final_relres"] <= TOL, inf
+        extra["mis3_" + prec] = {"setup_ms": inf["setup_ms"], "solve_ms": inf["solve_ms"], "iters": inf["iters"],
+                                 "final_relres": inf["final_relres"], "levels": inf["levels"],
+                                 "dof_per_s": n / ((inf["setup_ms"] + inf["solve_ms"]) / 1e3)}
+        extra["levels_" + prec] = infos[-1]["levels"]
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     hb = np.ascontiguousarray(b)

@@ -94,13 +94,16 @@ typedef struct amg_params {
                             (omega from the eigenvalues of the Arnoldi Hessenberg matrix,
                             LU coarsest factor); needs outer = 1 (FGMRES, Sec. 2.2) and
                             a single system                                                */
+  int32_t mis_k;         /* aggregate roots form an MIS(k), 1..8: 2 is the paper's PMIS(2)
+                            (Alg. 2); k > 2 coarsens more aggressively (Sec. 2.1.2): k max
+                            rounds per PMIS iteration, aggregates reach distance k        */
 } amg_params;
 
 typedef struct amg_level_info {
   int32_t n;          /* unknowns on this level                             */
   int64_t nnz;        /* nonzeros of A_k                                    */
   int32_t n_coarse;   /* n_{k+1} (0 on the coarsest level)                  */
-  int32_t mis_rounds; /* PMIS(2) rounds used to coarsen this level          */
+  int32_t mis_rounds; /* PMIS iterations (k max rounds each) of this level  */
   double omega;       /* damped-Jacobi weight of this level                 */
   int32_t spmv_blocks; /* thread blocks of this level's SpMV launches          */
   int32_t seg_tile;    /* rows per tile of the per-system inner products of a

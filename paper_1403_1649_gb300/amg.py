@@ -41,7 +41,7 @@ class amg_params(C.Structure):
                 ("omega_mode", C.c_int32), ("omega", C.c_double), ("precision", C.c_int32),
                 ("outer", C.c_int32), ("restart", C.c_int32), ("max_iter", C.c_int32),
                 ("use_graph", C.c_int32), ("smoother", C.c_int32), ("tail", C.c_int32), ("pdl", C.c_int32),
-                ("autotune", C.c_int32), ("symmetric", C.c_int32)]
+                ("autotune", C.c_int32), ("symmetric", C.c_int32), ("mis_k", C.c_int32)]
 
 
 class amg_level_info(C.Structure):

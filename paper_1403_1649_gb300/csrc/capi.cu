@@ -96,7 +96,8 @@ int check_params(const amg_params *p) {
   if (!(p->alpha >= 0.0 && p->alpha < 1.0) || p->coarse_max < 1 || p->max_levels < 1 || p->kcycle_levels < 0 ||
       p->precision < 0 || p->precision > 2 || p->outer < 0 || p->outer > 1 || p->max_iter < 1 ||
       p->restart < 1 || p->omega_mode < 0 || p->omega_mode > 1 || p->smoother < 0 || p->smoother > 1 ||
-      p->tail < 0 || p->tail > 2 || p->autotune < 0 || p->autotune > 1 || p->symmetric < 0 || p->symmetric > 1) {
+      p->tail < 0 || p->tail > 2 || p->autotune < 0 || p->autotune > 1 || p->symmetric < 0 || p->symmetric > 1 ||
+      p->mis_k < 1 || p->mis_k > 8) {
     amg::set_last_error("invalid amg_params");
     return AMG_ERR_BAD_INPUT;
   }
@@ -138,6 +139,7 @@ void amg_default_params(amg_params *p) {
   p->pdl = 1;
   p->autotune = 0;
   p->symmetric = 1;
+  p->mis_k = 2;
 }
 
 int amg_setup(const amg_csr *A, const amg_params *params, void *stream, amg_hierarchy **out) {

@@ -242,14 +242,12 @@ __global__ void k_pmis_max1(int32_t n, const int32_t *__restrict__ Sptr, const i
   }
 }
 
-// second max round, then the decision of Alg. 2 for undecided nodes
-__global__ void k_pmis_max2_decide(int32_t n, const int32_t *__restrict__ Sptr,
-                                   const int32_t *__restrict__ Scol, const uint64_t *__restrict__ Tw,
-                                   const int32_t *__restrict__ Ti, int8_t *__restrict__ s,
-                                   int32_t *__restrict__ undecided) {
-  int32_t local = 0;
+// a middle max round of MIS(k), k > 2: (Tw, Ti) -> (Tw2, Ti2) over the closed
+// neighbourhood
+__global__ void k_pmis_maxk(int32_t n, const int32_t *__restrict__ Sptr, const int32_t *__restrict__ Scol,
+                            const uint64_t *__restrict__ Tw, const int32_t *__restrict__ Ti,
+                            uint64_t *__restrict__ Tw2, int32_t *__restrict__ Ti2) {
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    if (s[i] != 0) continue;
     uint64_t bw = Tw[i];
     int32_t bi = Ti[i];
     for (int32_t q = Sptr[i]; q < Sptr[i + 1]; ++q) {
@@ -261,6 +259,32 @@ __global__ void k_pmis_max2_decide(int32_t n, const int32_t *__restrict__ Sptr,
         bi = wi;
       }
     }
+    Tw2[i] = bw;
+    Ti2[i] = bi;
+  }
+}
+
+// the last max round (none for MIS(1)), then the decision of Alg. 2 for
+// undecided nodes
+__global__ void k_pmis_max2_decide(int32_t n, const int32_t *__restrict__ Sptr,
+                                   const int32_t *__restrict__ Scol, const uint64_t *__restrict__ Tw,
+                                   const int32_t *__restrict__ Ti, int8_t *__restrict__ s,
+                                   int32_t *__restrict__ undecided, bool last_max) {
+  int32_t local = 0;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (s[i] != 0) continue;
+    uint64_t bw = Tw[i];
+    int32_t bi = Ti[i];
+    if (last_max)
+      for (int32_t q = Sptr[i]; q < Sptr[i + 1]; ++q) {
+        const int32_t j = Scol[q];
+        const uint64_t w = Tw[j];
+        const int32_t wi = Ti[j];
+        if (tuple_gt(w, wi, bw, bi)) {
+          bw = w;
+          bi = wi;
+        }
+      }
     if (bi == i)
       s[i] = 1;
     else if ((bw >> 62) == 2)
@@ -281,8 +305,9 @@ __device__ __forceinline__ bool root_gt(int32_t a, int32_t b, const uint64_t *ke
 // roots go to the larger priority (v, i).  Pass 1: roots adjacent to i.
 __global__ void k_agg_pass1(int32_t n, const int32_t *__restrict__ Sptr, const int32_t *__restrict__ Scol,
                             const int8_t *__restrict__ s, const uint64_t *__restrict__ key,
-                            int32_t *__restrict__ r1) {
+                            int32_t *__restrict__ r1, int32_t *__restrict__ is_root) {
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    is_root[i] = (s[i] == 1);
     if (s[i] == 1) {
       r1[i] = i;
       continue;
@@ -296,13 +321,12 @@ __global__ void k_agg_pass1(int32_t n, const int32_t *__restrict__ Sptr, const i
   }
 }
 
-// Pass 2: nodes at distance 2 join through a neighbour assigned in pass 1.
+// Pass d = 2..k: nodes at distance d join through a neighbour assigned by
+// pass d-1 (r1: after pass d-1, r2: after pass d).
 __global__ void k_agg_pass2(int32_t n, const int32_t *__restrict__ Sptr, const int32_t *__restrict__ Scol,
                             const int8_t *__restrict__ s, const uint64_t *__restrict__ key,
-                            const int32_t *__restrict__ r1, int32_t *__restrict__ r2,
-                            int32_t *__restrict__ is_root) {
+                            const int32_t *__restrict__ r1, int32_t *__restrict__ r2) {
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    is_root[i] = (s[i] == 1);
     if (r1[i] >= 0) {
       r2[i] = r1[i];
       continue;
@@ -378,6 +402,7 @@ __global__ void k_interp(int32_t nc, const int32_t *__restrict__ aptr, const int
 // one term at a time, so every coarse value is the sequential sum.
 constexpr int kGalWarps = 8;   // warps per block of k_galerkin
 constexpr int32_t kGalCapMax = 4096;         // longest run staged by k_galerkin_smem
+constexpr int32_t kGalCapFirst = 112;        // run cap of its first pass (five blocks an SM)
 constexpr size_t kGalSmemBudget = 200 << 10;  // its dynamic shared memory per block
 constexpr int kGalCap = 320;   // entries of one coarse row staged in shared memory
 
@@ -563,8 +588,10 @@ __global__ void k_run_length(int32_t nc, const int32_t *__restrict__ aptr, const
 //  4. one lane per column adds its terms in that order, starting from the first:
 //     the order of the sequential keyed sum, bit for bit.
 // Output goes to the row's upper-bound slot crp[I]; ccount[I] = number of columns.
+// marked_only: a second pass with a larger cap over the rows the first left.
 __global__ void __launch_bounds__(256) k_galerkin_smem(
-    int32_t nc, int32_t cap, int32_t hbits, const int32_t *__restrict__ aptr, const int32_t *__restrict__ amem,
+    int32_t nc, int32_t cap, int32_t hbits, bool marked_only, const int32_t *__restrict__ aptr,
+    const int32_t *__restrict__ amem,
     const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ val,
     const int32_t *__restrict__ agg, const double *__restrict__ pw, int32_t *__restrict__ ccount,
     const int32_t *__restrict__ crp, int32_t *__restrict__ cci, double *__restrict__ cval,
@@ -592,6 +619,7 @@ __global__ void __launch_bounds__(256) k_galerkin_smem(
     return hh;
   };
   for (int32_t I = blockIdx.x * wpb + wid; I < nc; I += gridDim.x * wpb) {
+    if (marked_only && ccount[I] != -1) continue;
     const int32_t m0 = aptr[I], m1 = aptr[I + 1], nm = m1 - m0;
     // run offsets of the member rows (warp prefix sums over chunks of 32 members);
     // each member's row, first CSR position and weight go to shared memory
@@ -903,23 +931,26 @@ __device__ __forceinline__ void arn_block_partials(const double (&v)[kArnSlots],
   }
 }
 
-// sums of slots 0..ns-1 over all blocks, computed by the whole last block in a
-// fixed order (thread t takes blocks t, t + 256, ..., then a fixed tree)
+// sums of slots 0..ns-1 over all blocks, computed by the last block in a fixed
+// order: warp k takes slot k (ns <= kArnSlots = the block's warps), lane l the
+// blocks l, l + 32, ... in four interleaved partial sums, then a fixed tree
 __device__ void arn_totals(const double *part, int ns, double *out_sh) {
-  __shared__ double sh[8];
-  for (int k = 0; k < ns; ++k) {
-    double a = 0.0;
-    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) a += __ldcg(part + k * gridDim.x + b);
-    a = warp_sum(a);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = a;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[q];
-      out_sh[k] = t;
+  const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (k < ns) {
+    const double *pk = part + (size_t)k * gridDim.x;
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    unsigned b = lane;
+    for (; b + 96 < gridDim.x; b += 128) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[u] += __ldcg(pk + b + 32 * u);
     }
-    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 3; ++u)
+      if (b + 32 * u < gridDim.x) a[u] += __ldcg(pk + b + 32 * u);
+    const double t = warp_sum((a[0] + a[1]) + (a[2] + a[3]));
+    if (lane == 0) out_sh[k] = t;
   }
+  __syncthreads();
 }
 
 // The products gather U = dh .* W, the unnormalised basis vector scaled by
@@ -936,7 +967,7 @@ __global__ void __launch_bounds__(256) k_arn_start(int32_t n, uint64_t seed, int
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const uint64_t z = splitmix64(~seed ^ ((uint64_t)(uint32_t)level << 40) ^ (uint64_t)(uint32_t)i);
     const double q = 2.0 * ((double)(z >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
-    const double di = 1.0 / sqrt(fabs(diag[i]));
+    const double di = rsqrt(fabs(diag[i]));  // a few ulp from 1 / sqrt, in fewer FP64 operations
     W[i] = q;
     dh[i] = di;
     U[i] = di * q;
@@ -1255,9 +1286,21 @@ __device__ double hess_rho(int m, const double *H) {
   return rho;
 }
 
-__global__ void k_omega_from_H(const double *__restrict__ H, const double *__restrict__ wn, int m, int symmetric,
-                               double *__restrict__ omega_out) {
-  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+// One warp per level (block q: level q), so that the levels' small eigenvalue
+// problems (FP64, a slow pipe on this part) run side by side in one launch.
+struct OmegaJobs {
+  const double *H[kMaxLevels];
+  const double *wn[kMaxLevels];
+  double *out[kMaxLevels];
+  int m[kMaxLevels];
+};
+
+__global__ void k_omega_from_H(OmegaJobs jobs, int symmetric) {
+  if (threadIdx.x >= 32) return;
+  const double *__restrict__ H = jobs.H[blockIdx.x];
+  const double *__restrict__ wn = jobs.wn[blockIdx.x];
+  double *__restrict__ omega_out = jobs.out[blockIdx.x];
+  const int m = jobs.m[blockIdx.x];
   const int lane = threadIdx.x;
   int mm = m;
   for (int j = 0; j < m; ++j)
@@ -1551,9 +1594,10 @@ Coarsening coarsen_level(Hierarchy &h, int k, cudaStream_t s, int32_t *agg_out, 
     }
   }
 
-  // PMIS(2)
-  DevBuf<uint64_t> key(n), Tw(n);
-  DevBuf<int32_t> Ti(n), und(1);
+  // PMIS(k): k max rounds per iteration (k = 2: Alg. 2)
+  const int mk = h.p.mis_k;
+  DevBuf<uint64_t> key(n), Tw(n), Tw2(mk > 2 ? n : 1);
+  DevBuf<int32_t> Ti(n), Ti2(mk > 2 ? n : 1), und(1);
   DevBuf<int8_t> st(n);
   AMG_COUNT(), k_mis_keys<<<gb, 256, 0, s>>>(n, colcnt.p, h.p.seed, k, key.p, st.p);
   AMG_LAUNCH_CHECK();
@@ -1572,8 +1616,15 @@ Coarsening coarsen_level(Hierarchy &h, int k, cudaStream_t s, int32_t *agg_out, 
       const int b = round & 1;
       AMG_CUDA(cudaMemsetAsync(und2.p + b, 0, sizeof(int32_t), s));
       AMG_COUNT(), k_pmis_max1<<<grid_for(n, 256), 256, 0, s>>>(n, Sptr.p, Scol.p, st.p, key.p, Tw.p, Ti.p);
-      AMG_COUNT(), k_pmis_max2_decide<<<grid_for(n, 256), 256, 0, s>>>(n, Sptr.p, Scol.p, Tw.p, Ti.p, st.p,
-                                                                       und2.p + b);
+      uint64_t *tw = Tw.p, *tw2 = Tw2.p;
+      int32_t *ti = Ti.p, *ti2 = Ti2.p;
+      for (int r = 2; r < mk; ++r) {
+        AMG_COUNT(), k_pmis_maxk<<<grid_for(n, 256), 256, 0, s>>>(n, Sptr.p, Scol.p, tw, ti, tw2, ti2);
+        std::swap(tw, tw2);
+        std::swap(ti, ti2);
+      }
+      AMG_COUNT(), k_pmis_max2_decide<<<grid_for(n, 256), 256, 0, s>>>(n, Sptr.p, Scol.p, tw, ti, st.p,
+                                                                       und2.p + b, mk >= 2);
       AMG_LAUNCH_CHECK();
       AMG_CUDA(cudaMemcpyAsync(pin + b, und2.p + b, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
       AMG_CUDA(cudaEventRecord(ev[b], s));
@@ -1593,12 +1644,16 @@ Coarsening coarsen_level(Hierarchy &h, int k, cudaStream_t s, int32_t *agg_out, 
   // aggregation
   DevBuf<int32_t> r1(n), r2(n), isroot(n + 1), cid(n + 1), err(1);
   AMG_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
-  AMG_COUNT(), k_agg_pass1<<<grid_for(n, 256), 256, 0, s>>>(n, Sptr.p, Scol.p, st.p, key.p, r1.p);
-  AMG_COUNT(), k_agg_pass2<<<grid_for(n, 256), 256, 0, s>>>(n, Sptr.p, Scol.p, st.p, key.p, r1.p, r2.p, isroot.p);
+  AMG_COUNT(), k_agg_pass1<<<grid_for(n, 256), 256, 0, s>>>(n, Sptr.p, Scol.p, st.p, key.p, r1.p, isroot.p);
+  int32_t *ra = r1.p, *rb = r2.p;
+  for (int d = 2; d <= mk; ++d) {  // passes 2..k
+    AMG_COUNT(), k_agg_pass2<<<grid_for(n, 256), 256, 0, s>>>(n, Sptr.p, Scol.p, st.p, key.p, ra, rb);
+    std::swap(ra, rb);
+  }
   AMG_LAUNCH_CHECK();
   int32_t nc = 0;
   exclusive_scan<int32_t, int32_t>(isroot.p, cid.p, n, s, &nc);
-  AMG_COUNT(), k_agg_final<<<gb, 256, 0, s>>>(n, r2.p, cid.p, agg_out, err.p);
+  AMG_COUNT(), k_agg_final<<<gb, 256, 0, s>>>(n, ra, cid.p, agg_out, err.p);
   AMG_LAUNCH_CHECK();
   if (next_sys_off) {  // coarse rows of system s start at the number of roots before its first row
     AMG_COUNT(), k_gather_i32<<<blocks_for(h.nsys + 1), 256, 0, s>>>(h.nsys + 1, L.sys_off, cid.p, next_sys_off);
@@ -1663,15 +1718,15 @@ void build_solve_matrix(Hierarchy &h, Level &L, cudaStream_t s, bool fresh) {
   }
 }
 
-// omega of Eq. (damped Jacobi) from m = 5 Arnoldi steps on D^-1/2 A D^-1/2:
-// three kernels per step, the result left in omega_dev (no host round trip)
-void estimate_omega(Hierarchy &h, int k, const double *diag, double *omega_dev, cudaStream_t s) {
+// m = 5 Arnoldi steps on D^-1/2 A D^-1/2 for omega of Eq. (damped Jacobi):
+// three kernels per step; the Hessenberg matrix goes to H (9 x 8) and the
+// norms ||M q_j|| to wn (8), for k_omega_from_H.  Returns m.
+int arnoldi_omega(Hierarchy &h, int k, const double *diag, double *H, double *wn, cudaStream_t s) {
   Level &L = h.lev[k];
   const int32_t n = L.n;
   const int m = n < kArnoldiMax ? n : kArnoldiMax;
   const int g = grid_for(n, 256, kRedBlocks);  // a few rows per thread; few partials to reduce
-  DevBuf<double> Q((size_t)n * m), W(n), U(n), w(n), dh(n), part((size_t)kArnSlots * kRedBlocks), H(9 * 8), wn(8),
-      corr(8), nrm2(1);
+  DevBuf<double> Q((size_t)n * m), W(n), U(n), w(n), dh(n), part((size_t)kArnSlots * kRedBlocks), corr(8), nrm2(1);
   // an FP64 SELL copy of every entry: level 0 always, every level in FP64 mode
   const int64_t *sp64 = k == 0 ? L.sptr64 : (h.p.precision == AMG_PREC_F64 ? L.sptr : nullptr);
   const int32_t *sc64 = k == 0 ? L.scol64 : L.scol;
@@ -1681,32 +1736,31 @@ void estimate_omega(Hierarchy &h, int k, const double *diag, double *omega_dev, 
   const bool wide = L.nnz >= 16 * (int64_t)n;
   const int gc = grid_for((int64_t)n * (wide ? 8 : 4), 256, kRedBlocks);
   DevBuf<unsigned> ticket(1);
-  AMG_CUDA(cudaMemsetAsync(H.p, 0, sizeof(double) * 72, s));
+  AMG_CUDA(cudaMemsetAsync(H, 0, sizeof(double) * 72, s));
   AMG_CUDA(cudaMemsetAsync(ticket.p, 0, sizeof(unsigned), s));
   AMG_COUNT(), k_arn_start<<<g, 256, 0, s>>>(n, h.p.seed, k, diag, W.p, U.p, dh.p, part.p, nrm2.p, ticket.p);
   for (int j = 0; j < m; ++j) {
     if (sp64)
       AMG_COUNT(), k_arn_spmv_sell<<<gs, 256, 0, s>>>(n, L.nslices, j, sp64, sc64, sv64, dh.p, W.p, U.p, Q.p, w.p,
-                                                      part.p, nrm2.p, H.p, wn.p, ticket.p);
+                                                      part.p, nrm2.p, H, wn, ticket.p);
     else if (wide)
       AMG_COUNT(), k_arn_spmv<8><<<gc, 256, 0, s>>>(n, j, L.rp, L.ci, L.val, dh.p, W.p, U.p, Q.p, w.p, part.p, nrm2.p,
-                                                    H.p, wn.p, ticket.p);
+                                                    H, wn, ticket.p);
     else
       AMG_COUNT(), k_arn_spmv<4><<<gc, 256, 0, s>>>(n, j, L.rp, L.ci, L.val, dh.p, W.p, U.p, Q.p, w.p, part.p, nrm2.p,
-                                                    H.p, wn.p, ticket.p);
-    AMG_COUNT(), k_arn_orth<<<g, 256, 0, s>>>(n, j, 0, Q.p, w.p, W.p, U.p, dh.p, part.p, H.p, corr.p, nrm2.p,
+                                                    H, wn, ticket.p);
+    AMG_COUNT(), k_arn_orth<<<g, 256, 0, s>>>(n, j, 0, Q.p, w.p, W.p, U.p, dh.p, part.p, H, corr.p, nrm2.p,
                                                ticket.p);
-    AMG_COUNT(), k_arn_orth<<<g, 256, 0, s>>>(n, j, 1, Q.p, w.p, W.p, U.p, dh.p, part.p, H.p, corr.p, nrm2.p,
+    AMG_COUNT(), k_arn_orth<<<g, 256, 0, s>>>(n, j, 1, Q.p, w.p, W.p, U.p, dh.p, part.p, H, corr.p, nrm2.p,
                                                ticket.p);
   }
-  AMG_COUNT(), k_omega_from_H<<<1, 32, 0, s>>>(H.p, wn.p, m, h.p.symmetric, omega_dev);
   AMG_LAUNCH_CHECK();
+  return m;
 }
 
 }  // namespace
 
 void build_hierarchy(Hierarchy &h, const amg_csr &A, cudaStream_t s) {
-  const amg_params &p = h.p;
   const int32_t n = A.n;
   if (!h.host_pinned) AMG_CUDA(cudaMallocHost(&h.host_pinned, 64 * sizeof(double)));
   // ---- level 0: copy and validate the input
@@ -1853,14 +1907,10 @@ void coarsen_all(Hierarchy &h, cudaStream_t s) {
       const int32_t mx = read_scalar(maxlen.p, s);
       DevBuf<int32_t> tci(L.nnz + 1);
       DevBuf<double> tval(L.nnz + 1);
-      // shared-memory sort path sized by the longest run (one warp per coarse row)
+      // shared-memory sort path sized by the longest run (one warp per coarse row):
+      // a first pass with runs of up to kGalCapFirst entries, at a higher
+      // occupancy, then the longer runs with the full cap
       const int32_t cap = std::max<int32_t>(32, std::min<int32_t>(mx, kGalCapMax));
-      int hbits = 1;
-      while ((1 << hbits) < 2 * cap) ++hbits;
-      const size_t per = (size_t)cap * 40 + ((size_t)8 << hbits);
-      const int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, kGalSmemBudget / per));
-      const size_t smem = per * wpb;
-      AMG_CUDA(cudaFuncSetAttribute(k_galerkin_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       // the summation plan for values-only re-setup (Sec. 3.1): recorded when every
       // run fits the shared-memory path
       L.plan = mx <= cap;
@@ -1869,10 +1919,21 @@ void coarsen_all(Hierarchy &h, cudaStream_t s) {
         L.gpos = h.arena.get<int32_t>((size_t)L.nnz);
         L.grow = h.arena.get<int32_t>((size_t)L.nnz);
       }
-      AMG_COUNT(), k_galerkin_smem<<<grid_for(nc, wpb, 152 * 64), wpb * 32, smem, s>>>(
-          nc, cap, hbits, L.aptr, L.amem, L.rp, L.ci, L.val, agg, L.pw64, ccount.p, ub.p, tci.p, tval.p,
-          L.plan ? L.gpos : nullptr, L.plan ? L.grow : nullptr, L.plan ? tseg.p : nullptr);
-      AMG_LAUNCH_CHECK();
+      auto gal_pass = [&](int32_t pcap, bool marked_only) {
+        int hbits = 1;  // a table larger than the run: at least one free slot
+        while ((1 << hbits) <= pcap) ++hbits;
+        const size_t per = (size_t)pcap * 40 + ((size_t)8 << hbits);
+        const int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, kGalSmemBudget / per));
+        const size_t smem = per * wpb;
+        AMG_CUDA(cudaFuncSetAttribute(k_galerkin_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        AMG_COUNT(), k_galerkin_smem<<<grid_for(nc, wpb, 152 * 64), wpb * 32, smem, s>>>(
+            nc, pcap, hbits, marked_only, L.aptr, L.amem, L.rp, L.ci, L.val, agg, L.pw64, ccount.p, ub.p, tci.p,
+            tval.p, L.plan ? L.gpos : nullptr, L.plan ? L.grow : nullptr, L.plan ? tseg.p : nullptr);
+        AMG_LAUNCH_CHECK();
+      };
+      const int32_t cap1 = std::min(cap, kGalCapFirst);
+      gal_pass(cap1, false);
+      if (mx > cap1) gal_pass(cap, true);
       if (mx > cap) {  // runs longer than the cap: walked from global memory
         const int gw = grid_for((int64_t)nc * 32, 256, 152 * 64);
         AMG_COUNT(), k_galerkin<true><<<gw, 256, 0, s>>>(nc, L.aptr, L.amem, L.rp, L.ci, L.val, agg, L.pw64,
@@ -1905,19 +1966,31 @@ void coarsen_all(Hierarchy &h, cudaStream_t s) {
 // place (values-only re-setup): captured solve graphs stay valid.
 void finish_levels(Hierarchy &h, cudaStream_t s, bool fresh) {
   const amg_params &p = h.p;
+  std::vector<DevBuf<double>> diag(h.L);
+  DevBuf<double> Hs((size_t)kMaxLevels * 72), wns((size_t)kMaxLevels * 8);
+  OmegaJobs jobs{};
+  int nj = 0;
   for (int q = 0; q < h.L; ++q) {
     Level &L = h.lev[q];
     build_solve_matrix(h, L, s, fresh);
-    DevBuf<double> diag(L.n);
-    AMG_COUNT(), k_diag<<<blocks_for(L.n), 256, 0, s>>>(L.n, L.rp, L.ci, L.val, diag.p);
+    diag[q].resize(L.n);
+    AMG_COUNT(), k_diag<<<blocks_for(L.n), 256, 0, s>>>(L.n, L.rp, L.ci, L.val, diag[q].p);
     AMG_LAUNCH_CHECK();
     L.omega = p.omega;  // omega_mode 1; mode 0 reads the estimate back after the loop
     if (q < h.L - 1 && p.omega_mode == 0) {
       if (!L.omega_dev) L.omega_dev = h.arena.get<double>(1);
-      estimate_omega(h, q, diag.p, L.omega_dev, s);
+      jobs.H[nj] = Hs.p + (size_t)nj * 72;
+      jobs.wn[nj] = wns.p + (size_t)nj * 8;
+      jobs.out[nj] = L.omega_dev;
+      jobs.m[nj] = arnoldi_omega(h, q, diag[q].p, Hs.p + (size_t)nj * 72, wns.p + (size_t)nj * 8, s);
+      ++nj;
     }
-    make_row_data(h, L, diag.p, s);  // per-row smoother data in the vector type
   }
+  if (nj) {  // every level's omega = (4/3) / rho in one launch
+    AMG_COUNT(), k_omega_from_H<<<nj, 32, 0, s>>>(jobs, p.symmetric);
+    AMG_LAUNCH_CHECK();
+  }
+  for (int q = 0; q < h.L; ++q) make_row_data(h, h.lev[q], diag[q].p, s);  // per-row smoother data
   {  // the estimated weights back to the host, one synchronisation for all levels
     for (int q = 0; q < h.L - 1; ++q)
       if (h.lev[q].omega_dev)

@@ -35,7 +35,7 @@ def test_default_params_host_only(built):
 def test_struct_layout_matches_header(built):
     # sizes of the ABI structs (x86_64 and aarch64 LP64 agree)
     assert C.sizeof(amg.amg_csr) == 40
-    assert C.sizeof(amg.amg_params) == 96
+    assert C.sizeof(amg.amg_params) == 104
     assert C.sizeof(amg.amg_level_info) == 40
     assert C.sizeof(amg.amg_solve_info) == 48
 
