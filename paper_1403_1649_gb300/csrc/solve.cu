@@ -150,14 +150,32 @@ __global__ void __launch_bounds__(kThreads, UW ? 1 : sell_min_blocks<VT>()) k_se
   for (int32_t sl = blockIdx.x * kWarps + (threadIdx.x >> 5); sl < a.nslices; sl += gridDim.x * kWarps) {
     if (GATE && !a.live[sl]) continue;
     const int32_t row = sl * 32 + lane;
+    VT y = VT(0), dg = VT(0), xr = VT(0);
+    const bool diag = !std::is_same<MV, double>::value && a.sdiag != nullptr && row < a.n;
+    // small levels (UW): the row's own operands (split diagonal, x_row and the
+    // epilogue's rhs, wd, xin) go out before the slice pointers, so that the
+    // warp's chain of dependent loads is the matrix and the gathers only
+    VT pre_rhs = VT(0), pre_wd = VT(0), pre_xin = VT(0);
+    if constexpr (UW != 0) {
+      if (diag) {
+        dg = (VT)ld_stream(a.sdiag + row);
+        xr = __ldg(a.x + row);
+      }
+      if (row < a.n) {
+        if (EPI == E_RESID || EPI == E_POST) pre_rhs = __ldg(a.rhs + row);
+        if (EPI == E_POST) {
+          pre_wd = __ldg(a.wd + row);
+          pre_xin = __ldg(a.xin + row);
+        }
+      }
+    }
     const int64_t base = a.sptr[sl];
     const int32_t width = (int32_t)((a.sptr[sl + 1] - base) >> 5);
     const int32_t *__restrict__ cp = a.scol + base + lane;
     const MV *__restrict__ vp = sval + base + lane;
-    VT y = VT(0), dg = VT(0), xr = VT(0);
-    // the split diagonal (FP32 / BF16 values only) and x_row are loaded right
-    // behind the first step's matrix loads, so that their latency overlaps the gathers
-    const bool diag = !std::is_same<MV, double>::value && a.sdiag != nullptr && row < a.n;
+    // otherwise the split diagonal (FP32 / BF16 values only) and x_row are loaded
+    // right behind the first step's matrix loads, so that their latency overlaps
+    // the gathers
     for (int32_t e = 0; e < width; e += U) {
       int32_t c[U];
       MV v[U];
@@ -168,7 +186,7 @@ __global__ void __launch_bounds__(kThreads, UW ? 1 : sell_min_blocks<VT>()) k_se
           v[q] = ld_stream(vp + 32 * (e + q));
         }
       }
-      if (e == 0 && diag) {
+      if (UW == 0 && e == 0 && diag) {
         dg = (VT)ld_stream(a.sdiag + row);
         xr = __ldg(a.x + row);
       }
@@ -190,8 +208,9 @@ __global__ void __launch_bounds__(kThreads, UW ? 1 : sell_min_blocks<VT>()) k_se
     if (row < a.n) {
       VT o;
       if (EPI == E_Y) o = y;
-      else if (EPI == E_RESID) o = a.rhs[row] - y;
-      else if (EPI == E_POST) o = a.xin[row] + a.wd[row] * (a.rhs[row] - y);
+      else if (EPI == E_RESID) o = (UW ? pre_rhs : a.rhs[row]) - y;
+      else if (EPI == E_POST)
+        o = UW ? pre_xin + pre_wd * (pre_rhs - y) : a.xin[row] + a.wd[row] * (a.rhs[row] - y);
       else if (EPI == E_DSCALE) o = a.dinv[row] * y;
       else if (EPI == E_POLYPRE)
         o = a.coef[3 * row] * a.p0[row] + a.coef[3 * row + 1] * a.p1[row] + a.coef[3 * row + 2] * (a.dinv[row] * y);
@@ -1038,7 +1057,7 @@ struct Engine {
     const bool small = sizeof(VT) == 4 && h.lev[k].nslices <= kSmallSlices;
     if constexpr (EPI == E_Y || EPI == E_POST || EPI == E_HORNER_LAST) {
       if (a.ndot) {
-        if constexpr (EPI == E_Y)
+        if constexpr (EPI == E_Y && sizeof(VT) == 4)
           if (small) {
             klaunch(k_sell<MV, VT, EPI, true, false, kSmallU>, sell_grid(h.lev[k]), kThreads, s, a);
             check();
@@ -1051,7 +1070,7 @@ struct Engine {
     } else {
       if (a.ndot) throw Error{AMG_ERR_UNSUPPORTED, "SpMV epilogue without fused inner products was given some"};
     }
-    if constexpr (EPI == E_Y || EPI == E_RESID || EPI == E_POST)
+    if constexpr ((EPI == E_Y || EPI == E_RESID || EPI == E_POST) && sizeof(VT) == 4)
       if (small) {
         klaunch(k_sell<MV, VT, EPI, false, false, kSmallU>, sell_grid(h.lev[k]), kThreads, s, a);
         check();
