@@ -14,6 +14,7 @@ constexpr int kScanTile = kScanThreads * kScanItems;
 template <class TI, class TO>
 __global__ void k_scan_tiles(const TI *__restrict__ in, TO *__restrict__ out, int64_t n,
                              TO *__restrict__ sums) {
+  pdl_wait_and_trigger();
   __shared__ TO warp_tot[kScanThreads / 32];
   const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
   TO v[kScanItems];
@@ -57,6 +58,7 @@ __global__ void k_scan_tiles(const TI *__restrict__ in, TO *__restrict__ out, in
 
 template <class TO>
 __global__ void k_scan_add(TO *__restrict__ out, int64_t n, const TO *__restrict__ sums) {
+  pdl_wait_and_trigger();
   const TO add = sums[blockIdx.x];
   const int64_t base = (int64_t)blockIdx.x * kScanTile;
   for (int k = threadIdx.x; k < kScanTile; k += blockDim.x) {
@@ -76,12 +78,12 @@ void exclusive_scan(const TI *in, TO *out, int64_t n, cudaStream_t s, TO *total_
     return;
   }
   DevBuf<TO> sums(tiles + 1);
-  AMG_COUNT(), k_scan_tiles<TI, TO><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, n, sums.p);
+  AMG_COUNT(), klaunch_sm(k_scan_tiles<TI, TO>, (unsigned)tiles, kScanThreads, 0, s, in, out, n, sums.p);
   AMG_LAUNCH_CHECK();
   if (tiles > 1) {
     DevBuf<TO> ssc(tiles + 1);
     exclusive_scan<TO, TO>(sums.p, ssc.p, tiles, s, nullptr);
-    AMG_COUNT(), k_scan_add<TO><<<(unsigned)tiles, kScanThreads, 0, s>>>(out, n, ssc.p);
+    AMG_COUNT(), klaunch_sm(k_scan_add<TO>, (unsigned)tiles, kScanThreads, 0, s, out, n, ssc.p);
     AMG_LAUNCH_CHECK();
     // out[n] = last exclusive value + last input = total
     AMG_CUDA(cudaMemcpyAsync(out + n, ssc.p + tiles, sizeof(TO), cudaMemcpyDeviceToDevice, s));

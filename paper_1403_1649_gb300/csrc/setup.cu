@@ -23,6 +23,7 @@ namespace amg {
 __global__ void k_check_csr(int32_t n, int64_t nnz, const int32_t *__restrict__ rp,
                             const int32_t *__restrict__ ci, const double *__restrict__ val,
                             int *__restrict__ err) {
+  pdl_wait_and_trigger();
   int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int e = 0;
@@ -50,6 +51,7 @@ __global__ void k_check_csr(int32_t n, int64_t nnz, const int32_t *__restrict__ 
 __global__ void k_strength(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                            const double *__restrict__ val, double alpha, uint8_t *__restrict__ C,
                            int32_t *__restrict__ rowcnt, int32_t *__restrict__ colcnt) {
+  pdl_wait_and_trigger();
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int32_t p0 = rp[i], p1 = rp[i + 1];
     double aii = 0.0;
@@ -81,6 +83,7 @@ __global__ void k_strength(int32_t n, const int32_t *__restrict__ rp, const int3
 }
 
 __global__ void k_add_i32(int32_t n, const int32_t *a, const int32_t *b, int32_t *c) {
+  pdl_wait_and_trigger();
   int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) c[i] = a[i] + b[i];
 }
@@ -91,6 +94,7 @@ __global__ void k_sym_fill(int32_t n, const int32_t *__restrict__ rp, const int3
                            const uint8_t *__restrict__ C, const int32_t *__restrict__ rowcnt,
                            const int32_t *__restrict__ off, int32_t *__restrict__ cursor,
                            int32_t *__restrict__ tmp) {
+  pdl_wait_and_trigger();
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     int32_t k = 0;
     for (int32_t p = rp[i]; p < rp[i + 1]; ++p) {
@@ -131,6 +135,7 @@ __device__ void sort_segment(int32_t *a, int32_t len) {
 
 __global__ void k_sort_unique(int32_t n, const int32_t *__restrict__ off, int32_t *__restrict__ tmp,
                               int32_t *__restrict__ ucount) {
+  pdl_wait_and_trigger();
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     int32_t *a = tmp + off[i];
     const int32_t len = off[i + 1] - off[i];
@@ -150,6 +155,7 @@ __global__ void k_sort_unique(int32_t n, const int32_t *__restrict__ off, int32_
 __global__ void k_sym_mirror(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                              const uint8_t *__restrict__ C, uint8_t *__restrict__ S, int32_t *__restrict__ scount,
                              int *__restrict__ nonsym) {
+  pdl_wait_and_trigger();
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     int32_t cnt = 0;
     for (int32_t p = rp[i]; p < rp[i + 1]; ++p) {
@@ -180,6 +186,7 @@ __global__ void k_sym_mirror(int32_t n, const int32_t *__restrict__ rp, const in
 __global__ void k_sym_mirror_fill(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                                   const uint8_t *__restrict__ S, const int32_t *__restrict__ Sptr,
                                   int32_t *__restrict__ Scol) {
+  pdl_wait_and_trigger();
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     int32_t k = Sptr[i];
     for (int32_t p = rp[i]; p < rp[i + 1]; ++p)
@@ -189,6 +196,7 @@ __global__ void k_sym_mirror_fill(int32_t n, const int32_t *__restrict__ rp, con
 
 __global__ void k_compact(int32_t n, const int32_t *__restrict__ off, const int32_t *__restrict__ tmp,
                           const int32_t *__restrict__ Sptr, int32_t *__restrict__ Scol) {
+  pdl_wait_and_trigger();
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int32_t len = Sptr[i + 1] - Sptr[i];
     for (int32_t k = 0; k < len; ++k) Scol[Sptr[i] + k] = tmp[off[i] + k];
@@ -207,6 +215,7 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
 // (count_i, h_i), r_i = (h_i + 1/2)/2^32, packed as count << 32 | h.
 __global__ void k_mis_keys(int32_t n, const int32_t *__restrict__ colcnt, uint64_t seed, int32_t level,
                            uint64_t *__restrict__ key, int8_t *__restrict__ s) {
+  pdl_wait_and_trigger();
   int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   uint32_t h = (uint32_t)(splitmix64(seed ^ ((uint64_t)(uint32_t)level << 40) ^ (uint64_t)(uint32_t)i) >> 32);
@@ -226,6 +235,7 @@ __device__ __forceinline__ bool tuple_gt(uint64_t wa, int32_t ia, uint64_t wb, i
 __global__ void k_pmis_max1(int32_t n, const int32_t *__restrict__ Sptr, const int32_t *__restrict__ Scol,
                             const int8_t *__restrict__ s, const uint64_t *__restrict__ key,
                             uint64_t *__restrict__ Tw, int32_t *__restrict__ Ti) {
+  pdl_wait_and_trigger();
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     uint64_t bw = pack_tuple(s[i], key[i]);
     int32_t bi = i;
@@ -247,6 +257,7 @@ __global__ void k_pmis_max1(int32_t n, const int32_t *__restrict__ Sptr, const i
 __global__ void k_pmis_maxk(int32_t n, const int32_t *__restrict__ Sptr, const int32_t *__restrict__ Scol,
                             const uint64_t *__restrict__ Tw, const int32_t *__restrict__ Ti,
                             uint64_t *__restrict__ Tw2, int32_t *__restrict__ Ti2) {
+  pdl_wait_and_trigger();
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     uint64_t bw = Tw[i];
     int32_t bi = Ti[i];
@@ -270,6 +281,7 @@ __global__ void k_pmis_max2_decide(int32_t n, const int32_t *__restrict__ Sptr,
                                    const int32_t *__restrict__ Scol, const uint64_t *__restrict__ Tw,
                                    const int32_t *__restrict__ Ti, int8_t *__restrict__ s,
                                    int32_t *__restrict__ undecided, bool last_max) {
+  pdl_wait_and_trigger();
   int32_t local = 0;
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     if (s[i] != 0) continue;
@@ -306,6 +318,7 @@ __device__ __forceinline__ bool root_gt(int32_t a, int32_t b, const uint64_t *ke
 __global__ void k_agg_pass1(int32_t n, const int32_t *__restrict__ Sptr, const int32_t *__restrict__ Scol,
                             const int8_t *__restrict__ s, const uint64_t *__restrict__ key,
                             int32_t *__restrict__ r1, int32_t *__restrict__ is_root) {
+  pdl_wait_and_trigger();
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     is_root[i] = (s[i] == 1);
     if (s[i] == 1) {
@@ -326,6 +339,7 @@ __global__ void k_agg_pass1(int32_t n, const int32_t *__restrict__ Sptr, const i
 __global__ void k_agg_pass2(int32_t n, const int32_t *__restrict__ Sptr, const int32_t *__restrict__ Scol,
                             const int8_t *__restrict__ s, const uint64_t *__restrict__ key,
                             const int32_t *__restrict__ r1, int32_t *__restrict__ r2) {
+  pdl_wait_and_trigger();
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     if (r1[i] >= 0) {
       r2[i] = r1[i];
@@ -345,6 +359,7 @@ __global__ void k_agg_pass2(int32_t n, const int32_t *__restrict__ Sptr, const i
 
 __global__ void k_agg_final(int32_t n, const int32_t *__restrict__ r2, const int32_t *__restrict__ cid,
                             int32_t *__restrict__ agg, int *__restrict__ err) {
+  pdl_wait_and_trigger();
   int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int32_t r = r2[i];
@@ -359,18 +374,21 @@ __global__ void k_agg_final(int32_t n, const int32_t *__restrict__ r2, const int
 // members of each aggregate, sorted ascending (the summation order of Alg. 3
 // and of the keyed sum)
 __global__ void k_count_members(int32_t n, const int32_t *__restrict__ agg, int32_t *__restrict__ cnt) {
+  pdl_wait_and_trigger();
   int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) atomicAdd(&cnt[agg[i]], 1);
+  if (i < n && agg[i] >= 0) atomicAdd(&cnt[agg[i]], 1);  // -1: unassigned, reported by the host
 }
 __global__ void k_fill_members(int32_t n, const int32_t *__restrict__ agg, const int32_t *__restrict__ aptr,
                                int32_t *__restrict__ cur, int32_t *__restrict__ amem) {
+  pdl_wait_and_trigger();
   int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) {
+  if (i < n && agg[i] >= 0) {
     const int32_t I = agg[i];
     amem[aptr[I] + atomicAdd(&cur[I], 1)] = i;
   }
 }
 __global__ void k_sort_members(int32_t nc, const int32_t *__restrict__ aptr, int32_t *__restrict__ amem) {
+  pdl_wait_and_trigger();
   for (int32_t I = blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += gridDim.x * blockDim.x)
     sort_segment(amem + aptr[I], aptr[I + 1] - aptr[I]);
 }
@@ -380,6 +398,7 @@ __global__ void k_sort_members(int32_t nc, const int32_t *__restrict__ aptr, int
 // index), P(i, I) = B_k(i) / B_{k+1}(I).
 __global__ void k_interp(int32_t nc, const int32_t *__restrict__ aptr, const int32_t *__restrict__ amem,
                          const double *__restrict__ B, double *__restrict__ Bc, double *__restrict__ pw) {
+  pdl_wait_and_trigger();
   for (int32_t I = blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += gridDim.x * blockDim.x) {
     const int32_t m0 = aptr[I], m1 = aptr[I + 1];
     double sum = 0.0;
@@ -412,6 +431,7 @@ __global__ void __launch_bounds__(kGalWarps * 32) k_galerkin(
     const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ val,
     const int32_t *__restrict__ agg, const double *__restrict__ pw, int32_t *__restrict__ ccount,
     const int32_t *__restrict__ crp, int32_t *__restrict__ cci, double *__restrict__ cval, bool marked_only) {
+  pdl_wait_and_trigger();
   __shared__ int32_t sJ[kGalWarps][kGalCap];
   __shared__ int32_t sK[kGalWarps][kGalCap];  // distinct coarse columns of the run
   __shared__ double sV[FILL ? kGalWarps : 1][FILL ? kGalCap : 1];
@@ -565,6 +585,7 @@ __global__ void __launch_bounds__(kGalWarps * 32) k_galerkin(
 // an upper bound on the number of coarse nonzeros of row I
 __global__ void k_run_length(int32_t nc, const int32_t *__restrict__ aptr, const int32_t *__restrict__ amem,
                              const int32_t *__restrict__ rp, int32_t *__restrict__ len, int32_t *__restrict__ maxlen) {
+  pdl_wait_and_trigger();
   int32_t mx = 0;
   for (int32_t I = blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += gridDim.x * blockDim.x) {
     int32_t t = 0;
@@ -596,6 +617,7 @@ __global__ void __launch_bounds__(256) k_galerkin_smem(
     const int32_t *__restrict__ agg, const double *__restrict__ pw, int32_t *__restrict__ ccount,
     const int32_t *__restrict__ crp, int32_t *__restrict__ cci, double *__restrict__ cval,
     int32_t *__restrict__ gpos, int32_t *__restrict__ grow, int32_t *__restrict__ gseg) {
+  pdl_wait_and_trigger();
   extern __shared__ __align__(16) unsigned char gal_sm[];
   const int lane = threadIdx.x & 31;
   const int wid = threadIdx.x >> 5;
@@ -776,6 +798,7 @@ __global__ void __launch_bounds__(256) k_galerkin_smem(
 __global__ void k_compact_rows(int32_t nc, const int32_t *__restrict__ ub, const int32_t *__restrict__ crp,
                                const int32_t *__restrict__ tci, const double *__restrict__ tval,
                                int32_t *__restrict__ cci, double *__restrict__ cval) {
+  pdl_wait_and_trigger();
   for (int32_t I = blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += gridDim.x * blockDim.x) {
     const int32_t len = crp[I + 1] - crp[I];
     for (int32_t t = 0; t < len; ++t) {
@@ -789,6 +812,7 @@ __global__ void k_compact_rows(int32_t nc, const int32_t *__restrict__ ub, const
 // compact positions; gptr[cnnz] = number of fine nonzeros
 __global__ void k_compact_plan(int32_t nc, const int32_t *__restrict__ ub, const int32_t *__restrict__ crp,
                                const int32_t *__restrict__ tseg, int32_t *__restrict__ gptr, int32_t nnz_fine) {
+  pdl_wait_and_trigger();
   for (int32_t I = blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += gridDim.x * blockDim.x) {
     const int32_t len = crp[I + 1] - crp[I];
     for (int32_t t = 0; t < len; ++t) gptr[crp[I] + t] = tseg[ub[I] + t];
@@ -803,6 +827,7 @@ __global__ void k_galerkin_values(int32_t cnnz, const int32_t *__restrict__ gptr
                                   const int32_t *__restrict__ grow, const int32_t *__restrict__ ci,
                                   const double *__restrict__ val, const double *__restrict__ pw,
                                   double *__restrict__ cval) {
+  pdl_wait_and_trigger();
   for (int32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < cnnz; q += gridDim.x * blockDim.x) {
     const int32_t a = gptr[q], b = gptr[q + 1];
     double sum = 0.0;
@@ -818,6 +843,7 @@ __global__ void k_galerkin_values(int32_t cnnz, const int32_t *__restrict__ gptr
 // ============================================================== solve-phase data
 __global__ void k_diag(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                        const double *__restrict__ val, double *__restrict__ diag) {
+  pdl_wait_and_trigger();
   int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double d = 0.0;
@@ -830,6 +856,7 @@ __global__ void k_diag(int32_t n, const int32_t *__restrict__ rp, const int32_t 
 // width of each slice = its longest row (off-diagonal entries only when split)
 __global__ void k_slice_width(int32_t n, int32_t nslices, const int32_t *__restrict__ rp,
                               const int32_t *__restrict__ ci, bool split, int64_t *__restrict__ width32) {
+  pdl_wait_and_trigger();
   const int lane = threadIdx.x & 31;
   const int32_t sl = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (sl >= nslices) return;
@@ -864,6 +891,7 @@ __global__ void k_build_sell(int32_t n, int32_t nslices, const int32_t *__restri
                              const int32_t *__restrict__ ci, const double *__restrict__ val,
                              const int64_t *__restrict__ sptr, int32_t *__restrict__ scol, MV *__restrict__ sval,
                              float *__restrict__ sdiag) {
+  pdl_wait_and_trigger();
   const int lane = threadIdx.x & 31;
   const int32_t sl = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (sl >= nslices) return;
@@ -963,6 +991,7 @@ __global__ void __launch_bounds__(256) k_arn_start(int32_t n, uint64_t seed, int
                                                    const double *__restrict__ diag, double *__restrict__ W,
                                                    double *__restrict__ U, double *__restrict__ dh, double *part,
                                                    double *nrm2, unsigned *ticket) {
+  pdl_wait_and_trigger();
   double v[kArnSlots] = {0.0};
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const uint64_t z = splitmix64(~seed ^ ((uint64_t)(uint32_t)level << 40) ^ (uint64_t)(uint32_t)i);
@@ -995,6 +1024,7 @@ __global__ void __launch_bounds__(256) k_arn_spmv(int32_t n, int j, const int32_
                                                   const double *__restrict__ U, double *__restrict__ Q,
                                                   double *__restrict__ w, double *part, const double *nrm2, double *H,
                                                   double *wn, unsigned *ticket) {
+  pdl_wait_and_trigger();
   const double h = sqrt(*nrm2), sc = 1.0 / h;
   double *qj = Q + (size_t)j * n;
   const int t = threadIdx.x % T;
@@ -1058,6 +1088,7 @@ __global__ void __launch_bounds__(256) k_arn_spmv_sell(int32_t n, int32_t nslice
                                                        double *__restrict__ Q,
                                                        double *__restrict__ w, double *part, const double *nrm2,
                                                        double *H, double *wn, unsigned *ticket) {
+  pdl_wait_and_trigger();
   const double h = sqrt(*nrm2), sc = 1.0 / h;
   double *qj = Q + (size_t)j * n;
   const int lane = threadIdx.x & 31;
@@ -1116,6 +1147,7 @@ __global__ void __launch_bounds__(256) k_arn_orth(int32_t n, int j, int pass, co
                                                   double *__restrict__ U, const double *__restrict__ dh,
                                                   double *part, double *H, double *corr, double *nrm2,
                                                   unsigned *ticket) {
+  pdl_wait_and_trigger();
   double c[kArnoldiMax];
 #pragma unroll
   for (int l = 0; l < kArnoldiMax; ++l) c[l] = l <= j ? (pass == 0 ? H[l * 8 + j] : corr[l]) : 0.0;
@@ -1296,6 +1328,7 @@ struct OmegaJobs {
 };
 
 __global__ void k_omega_from_H(OmegaJobs jobs, int symmetric) {
+  pdl_wait_and_trigger();
   if (threadIdx.x >= 32) return;
   const double *__restrict__ H = jobs.H[blockIdx.x];
   const double *__restrict__ wn = jobs.wn[blockIdx.x];
@@ -1359,6 +1392,7 @@ __global__ void k_omega_from_H(OmegaJobs jobs, int symmetric) {
 // A (destroyed) -> Ainv.  fac: n doubles of scratch.
 __global__ void k_lu_inverse(int32_t n, double *__restrict__ A, double *__restrict__ Ainv, double *__restrict__ fac,
                              int *__restrict__ err) {
+  pdl_wait_and_trigger();
   __shared__ double bv_s[32];
   __shared__ int bi_s[32];
   __shared__ int piv;
@@ -1433,6 +1467,7 @@ __global__ void k_lu_inverse(int32_t n, double *__restrict__ A, double *__restri
 
 __global__ void k_dense_from_csr(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                                  const double *__restrict__ val, double *__restrict__ A) {
+  pdl_wait_and_trigger();
   int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   for (int32_t p = rp[i]; p < rp[i + 1]; ++p) A[(int64_t)i * n + ci[p]] = val[p];
@@ -1445,6 +1480,7 @@ __device__ void cholesky_inverse_body(int32_t n, double *__restrict__ A, double 
 
 __global__ void k_cholesky_inverse(int32_t n, double *__restrict__ A, double *__restrict__ Ainv,
                                    int *__restrict__ err) {
+  pdl_wait_and_trigger();
   cholesky_inverse_body(n, A, Ainv, err);
 }
 
@@ -1452,6 +1488,7 @@ __global__ void k_cholesky_inverse(int32_t n, double *__restrict__ A, double *__
 __global__ void k_cholesky_inverse_batched(int32_t nsys, const int32_t *__restrict__ off,
                                            const int64_t *__restrict__ boff, double *__restrict__ A,
                                            double *__restrict__ Ainv, int *__restrict__ err) {
+  pdl_wait_and_trigger();
   const int32_t s = blockIdx.x;
   if (s >= nsys) return;
   cholesky_inverse_body(off[s + 1] - off[s], A + boff[s], Ainv + boff[s], err);
@@ -1501,16 +1538,19 @@ __device__ void cholesky_inverse_body(int32_t n, double *__restrict__ A, double 
 
 __global__ void k_gather_i32(int32_t n, const int32_t *__restrict__ idx, const int32_t *__restrict__ src,
                              int32_t *__restrict__ dst) {
+  pdl_wait_and_trigger();
   int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) dst[i] = src[idx[i]];
 }
 
 // block-diagonal assembly: rows of system s shifted by (row0, nnz0)
 __global__ void k_shift_rowptr(int32_t n, const int32_t *__restrict__ rp, int64_t nnz0, int32_t *__restrict__ out) {
+  pdl_wait_and_trigger();
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += gridDim.x * blockDim.x)
     out[i] = (int32_t)(rp[i] + nnz0);
 }
 __global__ void k_shift_col(int64_t nnz, const int32_t *__restrict__ ci, int32_t row0, int32_t *__restrict__ out) {
+  pdl_wait_and_trigger();
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x)
     out[p] = ci[p] + row0;
 }
@@ -1519,6 +1559,7 @@ __global__ void k_shift_col(int64_t nnz, const int32_t *__restrict__ ci, int32_t
 __global__ void k_dense_blocks(int32_t nsys, const int32_t *__restrict__ off, const int64_t *__restrict__ boff,
                                const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                                const double *__restrict__ val, double *__restrict__ dense) {
+  pdl_wait_and_trigger();
   const int32_t s = blockIdx.x;
   if (s >= nsys) return;
   const int32_t r0 = off[s], m = off[s + 1] - r0;
@@ -1528,12 +1569,18 @@ __global__ void k_dense_blocks(int32_t nsys, const int32_t *__restrict__ off, co
 }
 
 __global__ void k_fill_f64(int64_t n, double *p, double v) {
+  pdl_wait_and_trigger();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     p[i] = v;
 }
 
 // ============================================================== host side
 namespace {
+
+// host_pinned (64 doubles): ints [0, 2) PMIS round counts, doubles [0, levels)
+// omega read-back, ints at double offset 40: setup flags (symmetry, aggregation
+// error), read at the next synchronisation
+constexpr int kPinnedSetupFlags = 40;
 
 template <class T>
 T read_scalar(const T *dev, cudaStream_t s) {
@@ -1563,7 +1610,8 @@ Coarsening coarsen_level(Hierarchy &h, int k, cudaStream_t s, int32_t *agg_out, 
   DevBuf<int32_t> rowcnt(n + 1), colcnt(n + 1), deg(n + 1), off(n + 1), cursor(n + 1);
   AMG_CUDA(cudaMemsetAsync(colcnt.p, 0, sizeof(int32_t) * (n + 1), s));
   AMG_CUDA(cudaMemsetAsync(cursor.p, 0, sizeof(int32_t) * (n + 1), s));
-  AMG_COUNT(), k_strength<<<grid_for(n, 256), 256, 0, s>>>(n, L.rp, L.ci, L.val, h.p.alpha, C.p, rowcnt.p, colcnt.p);
+  AMG_COUNT(), klaunch_sm(k_strength, grid_for(n, 256), 256, 0, s, n, L.rp, L.ci, L.val, h.p.alpha, C.p, rowcnt.p,
+      colcnt.p);
   AMG_LAUNCH_CHECK();
   DevBuf<int32_t> ucount(n + 1), Sptr(n + 1);
   DevBuf<int32_t> Scol;
@@ -1572,24 +1620,28 @@ Coarsening coarsen_level(Hierarchy &h, int k, cudaStream_t s, int32_t *agg_out, 
     DevBuf<uint8_t> S(nnz);
     DevBuf<int> nonsym(1);
     AMG_CUDA(cudaMemsetAsync(nonsym.p, 0, sizeof(int), s));
-    AMG_COUNT(), k_sym_mirror<<<grid_for(n, 256), 256, 0, s>>>(n, L.rp, L.ci, C.p, S.p, ucount.p, nonsym.p);
+    AMG_COUNT(), klaunch_sm(k_sym_mirror, grid_for(n, 256), 256, 0, s, n, L.rp, L.ci, C.p, S.p, ucount.p, nonsym.p);
     AMG_LAUNCH_CHECK();
+    // the flag rides on the scan's synchronisation
+    int32_t *flag_host = reinterpret_cast<int32_t *>(h.host_pinned + kPinnedSetupFlags);
+    AMG_CUDA(cudaMemcpyAsync(flag_host, nonsym.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     exclusive_scan<int32_t, int32_t>(ucount.p, Sptr.p, n, s, &ns);
-    if (!read_scalar(nonsym.p, s)) {
+    if (!*flag_host) {
       Scol.resize((size_t)ns + 1);
-      AMG_COUNT(), k_sym_mirror_fill<<<grid_for(n, 256), 256, 0, s>>>(n, L.rp, L.ci, S.p, Sptr.p, Scol.p);
+      AMG_COUNT(), klaunch_sm(k_sym_mirror_fill, grid_for(n, 256), 256, 0, s, n, L.rp, L.ci, S.p, Sptr.p, Scol.p);
       AMG_LAUNCH_CHECK();
     } else {  // general pattern: collect C rows and transposed entries, sort, deduplicate
-      AMG_COUNT(), k_add_i32<<<gb, 256, 0, s>>>(n, rowcnt.p, colcnt.p, deg.p);
+      AMG_COUNT(), klaunch_sm(k_add_i32, gb, 256, 0, s, n, rowcnt.p, colcnt.p, deg.p);
       int32_t total = 0;
       exclusive_scan<int32_t, int32_t>(deg.p, off.p, n, s, &total);
       DevBuf<int32_t> tmp((size_t)total + 1);
-      AMG_COUNT(), k_sym_fill<<<grid_for(n, 256), 256, 0, s>>>(n, L.rp, L.ci, C.p, rowcnt.p, off.p, cursor.p, tmp.p);
-      AMG_COUNT(), k_sort_unique<<<grid_for(n, 128), 128, 0, s>>>(n, off.p, tmp.p, ucount.p);
+      AMG_COUNT(), klaunch_sm(k_sym_fill, grid_for(n, 256), 256, 0, s, n, L.rp, L.ci, C.p, rowcnt.p, off.p, cursor.p,
+          tmp.p);
+      AMG_COUNT(), klaunch_sm(k_sort_unique, grid_for(n, 128), 128, 0, s, n, off.p, tmp.p, ucount.p);
       AMG_LAUNCH_CHECK();
       exclusive_scan<int32_t, int32_t>(ucount.p, Sptr.p, n, s, &ns);
       Scol.resize((size_t)ns + 1);
-      AMG_COUNT(), k_compact<<<grid_for(n, 256), 256, 0, s>>>(n, off.p, tmp.p, Sptr.p, Scol.p);
+      AMG_COUNT(), klaunch_sm(k_compact, grid_for(n, 256), 256, 0, s, n, off.p, tmp.p, Sptr.p, Scol.p);
       AMG_LAUNCH_CHECK();
     }
   }
@@ -1599,7 +1651,7 @@ Coarsening coarsen_level(Hierarchy &h, int k, cudaStream_t s, int32_t *agg_out, 
   DevBuf<uint64_t> key(n), Tw(n), Tw2(mk > 2 ? n : 1);
   DevBuf<int32_t> Ti(n), Ti2(mk > 2 ? n : 1), und(1);
   DevBuf<int8_t> st(n);
-  AMG_COUNT(), k_mis_keys<<<gb, 256, 0, s>>>(n, colcnt.p, h.p.seed, k, key.p, st.p);
+  AMG_COUNT(), klaunch_sm(k_mis_keys, gb, 256, 0, s, n, colcnt.p, h.p.seed, k, key.p, st.p);
   AMG_LAUNCH_CHECK();
   Coarsening out;
   {
@@ -1615,16 +1667,16 @@ Coarsening coarsen_level(Hierarchy &h, int k, cudaStream_t s, int32_t *agg_out, 
     for (int round = 0; round < 100000 && !done; ++round) {
       const int b = round & 1;
       AMG_CUDA(cudaMemsetAsync(und2.p + b, 0, sizeof(int32_t), s));
-      AMG_COUNT(), k_pmis_max1<<<grid_for(n, 256), 256, 0, s>>>(n, Sptr.p, Scol.p, st.p, key.p, Tw.p, Ti.p);
+      AMG_COUNT(), klaunch_sm(k_pmis_max1, grid_for(n, 256), 256, 0, s, n, Sptr.p, Scol.p, st.p, key.p, Tw.p, Ti.p);
       uint64_t *tw = Tw.p, *tw2 = Tw2.p;
       int32_t *ti = Ti.p, *ti2 = Ti2.p;
       for (int r = 2; r < mk; ++r) {
-        AMG_COUNT(), k_pmis_maxk<<<grid_for(n, 256), 256, 0, s>>>(n, Sptr.p, Scol.p, tw, ti, tw2, ti2);
+        AMG_COUNT(), klaunch_sm(k_pmis_maxk, grid_for(n, 256), 256, 0, s, n, Sptr.p, Scol.p, tw, ti, tw2, ti2);
         std::swap(tw, tw2);
         std::swap(ti, ti2);
       }
-      AMG_COUNT(), k_pmis_max2_decide<<<grid_for(n, 256), 256, 0, s>>>(n, Sptr.p, Scol.p, tw, ti, st.p,
-                                                                       und2.p + b, mk >= 2);
+      AMG_COUNT(), klaunch_sm(k_pmis_max2_decide, grid_for(n, 256), 256, 0, s, n, Sptr.p, Scol.p, tw, ti, st.p,
+                              und2.p + b, mk >= 2);
       AMG_LAUNCH_CHECK();
       AMG_CUDA(cudaMemcpyAsync(pin + b, und2.p + b, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
       AMG_CUDA(cudaEventRecord(ev[b], s));
@@ -1644,22 +1696,25 @@ Coarsening coarsen_level(Hierarchy &h, int k, cudaStream_t s, int32_t *agg_out, 
   // aggregation
   DevBuf<int32_t> r1(n), r2(n), isroot(n + 1), cid(n + 1), err(1);
   AMG_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
-  AMG_COUNT(), k_agg_pass1<<<grid_for(n, 256), 256, 0, s>>>(n, Sptr.p, Scol.p, st.p, key.p, r1.p, isroot.p);
+  AMG_COUNT(), klaunch_sm(k_agg_pass1, grid_for(n, 256), 256, 0, s, n, Sptr.p, Scol.p, st.p, key.p, r1.p, isroot.p);
   int32_t *ra = r1.p, *rb = r2.p;
   for (int d = 2; d <= mk; ++d) {  // passes 2..k
-    AMG_COUNT(), k_agg_pass2<<<grid_for(n, 256), 256, 0, s>>>(n, Sptr.p, Scol.p, st.p, key.p, ra, rb);
+    AMG_COUNT(), klaunch_sm(k_agg_pass2, grid_for(n, 256), 256, 0, s, n, Sptr.p, Scol.p, st.p, key.p, ra, rb);
     std::swap(ra, rb);
   }
   AMG_LAUNCH_CHECK();
   int32_t nc = 0;
   exclusive_scan<int32_t, int32_t>(isroot.p, cid.p, n, s, &nc);
-  AMG_COUNT(), k_agg_final<<<gb, 256, 0, s>>>(n, ra, cid.p, agg_out, err.p);
+  AMG_COUNT(), klaunch_sm(k_agg_final, gb, 256, 0, s, n, ra, cid.p, agg_out, err.p);
   AMG_LAUNCH_CHECK();
   if (next_sys_off) {  // coarse rows of system s start at the number of roots before its first row
-    AMG_COUNT(), k_gather_i32<<<blocks_for(h.nsys + 1), 256, 0, s>>>(h.nsys + 1, L.sys_off, cid.p, next_sys_off);
+    AMG_COUNT(), klaunch_sm(k_gather_i32, blocks_for(h.nsys + 1), 256, 0, s, h.nsys + 1, L.sys_off, cid.p,
+        next_sys_off);
     AMG_LAUNCH_CHECK();
   }
-  if (read_scalar(err.p, s) != 0) throw Error{AMG_ERR_SETUP, "aggregation left a node unassigned"};
+  // checked at the next synchronisation (the member kernels skip an unassigned node)
+  AMG_CUDA(cudaMemcpyAsync(reinterpret_cast<int32_t *>(h.host_pinned + kPinnedSetupFlags) + 1, err.p, sizeof(int),
+                           cudaMemcpyDeviceToHost, s));
   out.nc = nc;
   return out;
 }
@@ -1674,7 +1729,7 @@ void build_solve_matrix(Hierarchy &h, Level &L, cudaStream_t s, bool fresh) {
   const unsigned g = blocks_for((int64_t)L.nslices * 32);
   auto layout = [&](bool split, int64_t *&sptr, int32_t *&scol, int64_t &entries) {
     DevBuf<int64_t> w32(L.nslices + 1);
-    AMG_COUNT(), k_slice_width<<<g, 256, 0, s>>>(n, L.nslices, L.rp, L.ci, split, w32.p);
+    AMG_COUNT(), klaunch_sm(k_slice_width, g, 256, 0, s, n, L.nslices, L.rp, L.ci, split, w32.p);
     AMG_LAUNCH_CHECK();
     sptr = h.arena.get<int64_t>(L.nslices + 1);
     exclusive_scan<int64_t, int64_t>(w32.p, sptr, L.nslices, s, &entries);
@@ -1687,18 +1742,18 @@ void build_solve_matrix(Hierarchy &h, Level &L, cudaStream_t s, bool fresh) {
   switch (h.p.precision) {
     case AMG_PREC_F64:
       if (fresh) L.sval = h.arena.get<double>(entries);
-      AMG_COUNT(), k_build_sell<double><<<g, 256, 0, s>>>(n, L.nslices, L.rp, L.ci, L.val, L.sptr, L.scol,
-                                                          (double *)L.sval, nullptr);
+      AMG_COUNT(), klaunch_sm(k_build_sell<double>, g, 256, 0, s, n, L.nslices, L.rp, L.ci, L.val, L.sptr, L.scol,
+          (double *)L.sval, nullptr);
       break;
     case AMG_PREC_F32:
       if (fresh) L.sval = h.arena.get<float>(entries);
-      AMG_COUNT(), k_build_sell<float><<<g, 256, 0, s>>>(n, L.nslices, L.rp, L.ci, L.val, L.sptr, L.scol,
-                                                         (float *)L.sval, L.sdiag);
+      AMG_COUNT(), klaunch_sm(k_build_sell<float>, g, 256, 0, s, n, L.nslices, L.rp, L.ci, L.val, L.sptr, L.scol,
+          (float *)L.sval, L.sdiag);
       break;
     default:
       if (fresh) L.sval = h.arena.get<__nv_bfloat16>(entries);
-      AMG_COUNT(), k_build_sell<__nv_bfloat16><<<g, 256, 0, s>>>(n, L.nslices, L.rp, L.ci, L.val, L.sptr, L.scol,
-                                                                 (__nv_bfloat16 *)L.sval, L.sdiag);
+      AMG_COUNT(), klaunch_sm(k_build_sell<__nv_bfloat16>, g, 256, 0, s, n, L.nslices, L.rp, L.ci, L.val, L.sptr,
+          L.scol, (__nv_bfloat16 *)L.sval, L.sdiag);
   }
   AMG_LAUNCH_CHECK();
   if (&L != &h.lev[0]) return;
@@ -1707,8 +1762,8 @@ void build_solve_matrix(Hierarchy &h, Level &L, cudaStream_t s, bool fresh) {
       layout(false, L.sptr64, L.scol64, L.sell64_entries);
       L.sval64 = h.arena.get<double>(L.sell64_entries);
     }
-    AMG_COUNT(), k_build_sell<double><<<g, 256, 0, s>>>(n, L.nslices, L.rp, L.ci, L.val, L.sptr64, L.scol64,
-                                                        L.sval64, nullptr);
+    AMG_COUNT(), klaunch_sm(k_build_sell<double>, g, 256, 0, s, n, L.nslices, L.rp, L.ci, L.val, L.sptr64, L.scol64,
+        L.sval64, nullptr);
     AMG_LAUNCH_CHECK();
   } else {
     L.sptr64 = L.sptr;
@@ -1738,21 +1793,21 @@ int arnoldi_omega(Hierarchy &h, int k, const double *diag, double *H, double *wn
   DevBuf<unsigned> ticket(1);
   AMG_CUDA(cudaMemsetAsync(H, 0, sizeof(double) * 72, s));
   AMG_CUDA(cudaMemsetAsync(ticket.p, 0, sizeof(unsigned), s));
-  AMG_COUNT(), k_arn_start<<<g, 256, 0, s>>>(n, h.p.seed, k, diag, W.p, U.p, dh.p, part.p, nrm2.p, ticket.p);
+  AMG_COUNT(), klaunch_sm(k_arn_start, g, 256, 0, s, n, h.p.seed, k, diag, W.p, U.p, dh.p, part.p, nrm2.p, ticket.p);
   for (int j = 0; j < m; ++j) {
     if (sp64)
-      AMG_COUNT(), k_arn_spmv_sell<<<gs, 256, 0, s>>>(n, L.nslices, j, sp64, sc64, sv64, dh.p, W.p, U.p, Q.p, w.p,
-                                                      part.p, nrm2.p, H, wn, ticket.p);
+      AMG_COUNT(), klaunch_sm(k_arn_spmv_sell, gs, 256, 0, s, n, L.nslices, j, sp64, sc64, sv64, dh.p, W.p, U.p, Q.p,
+          w.p, part.p, nrm2.p, H, wn, ticket.p);
     else if (wide)
-      AMG_COUNT(), k_arn_spmv<8><<<gc, 256, 0, s>>>(n, j, L.rp, L.ci, L.val, dh.p, W.p, U.p, Q.p, w.p, part.p, nrm2.p,
-                                                    H, wn, ticket.p);
+      AMG_COUNT(), klaunch_sm(k_arn_spmv<8>, gc, 256, 0, s, n, j, L.rp, L.ci, L.val, dh.p, W.p, U.p, Q.p, w.p, part.p,
+          nrm2.p, H, wn, ticket.p);
     else
-      AMG_COUNT(), k_arn_spmv<4><<<gc, 256, 0, s>>>(n, j, L.rp, L.ci, L.val, dh.p, W.p, U.p, Q.p, w.p, part.p, nrm2.p,
-                                                    H, wn, ticket.p);
-    AMG_COUNT(), k_arn_orth<<<g, 256, 0, s>>>(n, j, 0, Q.p, w.p, W.p, U.p, dh.p, part.p, H, corr.p, nrm2.p,
-                                               ticket.p);
-    AMG_COUNT(), k_arn_orth<<<g, 256, 0, s>>>(n, j, 1, Q.p, w.p, W.p, U.p, dh.p, part.p, H, corr.p, nrm2.p,
-                                               ticket.p);
+      AMG_COUNT(), klaunch_sm(k_arn_spmv<4>, gc, 256, 0, s, n, j, L.rp, L.ci, L.val, dh.p, W.p, U.p, Q.p, w.p, part.p,
+          nrm2.p, H, wn, ticket.p);
+    AMG_COUNT(), klaunch_sm(k_arn_orth, g, 256, 0, s, n, j, 0, Q.p, w.p, W.p, U.p, dh.p, part.p, H, corr.p, nrm2.p,
+        ticket.p);
+    AMG_COUNT(), klaunch_sm(k_arn_orth, g, 256, 0, s, n, j, 1, Q.p, w.p, W.p, U.p, dh.p, part.p, H, corr.p, nrm2.p,
+        ticket.p);
   }
   AMG_LAUNCH_CHECK();
   return m;
@@ -1778,7 +1833,7 @@ void build_hierarchy(Hierarchy &h, const amg_csr &A, cudaStream_t s) {
   {
     DevBuf<int> err(1);
     AMG_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
-    AMG_COUNT(), k_check_csr<<<blocks_for(n), 256, 0, s>>>(n, A.nnz, L0.rp, L0.ci, L0.val, err.p);
+    AMG_COUNT(), klaunch_sm(k_check_csr, blocks_for(n), 256, 0, s, n, A.nnz, L0.rp, L0.ci, L0.val, err.p);
     AMG_LAUNCH_CHECK();
     const int e = read_scalar(err.p, s);
     if (e) {
@@ -1791,7 +1846,7 @@ void build_hierarchy(Hierarchy &h, const amg_csr &A, cudaStream_t s) {
     }
   }
   L0.B = h.arena.get<double>(n);
-  AMG_COUNT(), k_fill_f64<<<grid_for(n, 256), 256, 0, s>>>(n, L0.B, 1.0);  // B_0 = 1
+  AMG_COUNT(), klaunch_sm(k_fill_f64, grid_for(n, 256), 256, 0, s, n, L0.B, 1.0);  // B_0 = 1
   AMG_LAUNCH_CHECK();
   coarsen_all(h, s);
 }
@@ -1828,14 +1883,14 @@ void build_hierarchy_batch(Hierarchy &h, int32_t nsys, const amg_csr *As, cudaSt
     AMG_CUDA(cudaMemcpyAsync(trp.p, A.row_ptr, sizeof(int32_t) * ((size_t)A.n + 1), kind, s));
     AMG_CUDA(cudaMemcpyAsync(tci.p, A.col, sizeof(int32_t) * (size_t)A.nnz, kind, s));
     AMG_CUDA(cudaMemcpyAsync(L0.val + zoff[q], A.val, sizeof(double) * (size_t)A.nnz, kind, s));
-    AMG_COUNT(), k_shift_rowptr<<<grid_for(A.n + 1, 256), 256, 0, s>>>(A.n, trp.p, zoff[q], L0.rp + roff[q]);
-    AMG_COUNT(), k_shift_col<<<grid_for(A.nnz, 256), 256, 0, s>>>(A.nnz, tci.p, roff[q], L0.ci + zoff[q]);
+    AMG_COUNT(), klaunch_sm(k_shift_rowptr, grid_for(A.n + 1, 256), 256, 0, s, A.n, trp.p, zoff[q], L0.rp + roff[q]);
+    AMG_COUNT(), klaunch_sm(k_shift_col, grid_for(A.nnz, 256), 256, 0, s, A.nnz, tci.p, roff[q], L0.ci + zoff[q]);
     AMG_LAUNCH_CHECK();
   }
   {
     DevBuf<int> err(1);
     AMG_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
-    AMG_COUNT(), k_check_csr<<<blocks_for(L0.n), 256, 0, s>>>(L0.n, L0.nnz, L0.rp, L0.ci, L0.val, err.p);
+    AMG_COUNT(), klaunch_sm(k_check_csr, blocks_for(L0.n), 256, 0, s, L0.n, L0.nnz, L0.rp, L0.ci, L0.val, err.p);
     AMG_LAUNCH_CHECK();
     if (read_scalar(err.p, s)) throw Error{AMG_ERR_BAD_INPUT, "invalid CSR in the batch"};
   }
@@ -1843,7 +1898,7 @@ void build_hierarchy_batch(Hierarchy &h, int32_t nsys, const amg_csr *As, cudaSt
   L0.sys_off = h.arena.get<int32_t>(nsys + 1);
   AMG_CUDA(cudaMemcpyAsync(L0.sys_off, roff.data(), sizeof(int32_t) * (nsys + 1), cudaMemcpyHostToDevice, s));
   L0.B = h.arena.get<double>(L0.n);
-  AMG_COUNT(), k_fill_f64<<<grid_for(L0.n, 256), 256, 0, s>>>(L0.n, L0.B, 1.0);
+  AMG_COUNT(), klaunch_sm(k_fill_f64, grid_for(L0.n, 256), 256, 0, s, L0.n, L0.B, 1.0);
   AMG_LAUNCH_CHECK();
   AMG_CUDA(cudaStreamSynchronize(s));
   coarsen_all(h, s);
@@ -1884,27 +1939,29 @@ void coarsen_all(Hierarchy &h, cudaStream_t s) {
       DevBuf<int32_t> cnt(nc + 1), cur(nc + 1);
       AMG_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * (nc + 1), s));
       AMG_CUDA(cudaMemsetAsync(cur.p, 0, sizeof(int32_t) * (nc + 1), s));
-      AMG_COUNT(), k_count_members<<<blocks_for(L.n), 256, 0, s>>>(L.n, agg, cnt.p);
+      AMG_COUNT(), klaunch_sm(k_count_members, blocks_for(L.n), 256, 0, s, L.n, agg, cnt.p);
       exclusive_scan<int32_t, int32_t>(cnt.p, L.aptr, nc, s);
-      AMG_COUNT(), k_fill_members<<<blocks_for(L.n), 256, 0, s>>>(L.n, agg, L.aptr, cur.p, L.amem);
-      AMG_COUNT(), k_sort_members<<<grid_for(nc, 128), 128, 0, s>>>(nc, L.aptr, L.amem);
+      AMG_COUNT(), klaunch_sm(k_fill_members, blocks_for(L.n), 256, 0, s, L.n, agg, L.aptr, cur.p, L.amem);
+      AMG_COUNT(), klaunch_sm(k_sort_members, grid_for(nc, 128), 128, 0, s, nc, L.aptr, L.amem);
       AMG_LAUNCH_CHECK();
     }
     Level &Cl = h.lev[k + 1];
     Cl.n = nc;
     Cl.B = h.arena.get<double>(nc);
     L.pw64 = h.arena.get<double>(L.n);
-    AMG_COUNT(), k_interp<<<grid_for(nc, 128), 128, 0, s>>>(nc, L.aptr, L.amem, L.B, Cl.B, L.pw64);
+    AMG_COUNT(), klaunch_sm(k_interp, grid_for(nc, 128), 128, 0, s, nc, L.aptr, L.amem, L.B, Cl.B, L.pw64);
     AMG_LAUNCH_CHECK();
     // Galerkin keyed sum: count, offsets, fill
     Cl.rp = h.arena.get<int32_t>((size_t)nc + 1);
     {  // one walk per coarse row into upper-bound slots, then compaction
       DevBuf<int32_t> ccount(nc + 1), rlen(nc + 1), ub(nc + 1), maxlen(1);
       AMG_CUDA(cudaMemsetAsync(maxlen.p, 0, sizeof(int32_t), s));
-      AMG_COUNT(), k_run_length<<<grid_for(nc, 256), 256, 0, s>>>(nc, L.aptr, L.amem, L.rp, rlen.p, maxlen.p);
+      AMG_COUNT(), klaunch_sm(k_run_length, grid_for(nc, 256), 256, 0, s, nc, L.aptr, L.amem, L.rp, rlen.p, maxlen.p);
       AMG_LAUNCH_CHECK();
       exclusive_scan<int32_t, int32_t>(rlen.p, ub.p, nc, s);
       const int32_t mx = read_scalar(maxlen.p, s);
+      if (reinterpret_cast<const int32_t *>(h.host_pinned + kPinnedSetupFlags)[1] != 0)
+        throw Error{AMG_ERR_SETUP, "aggregation left a node unassigned"};
       DevBuf<int32_t> tci(L.nnz + 1);
       DevBuf<double> tval(L.nnz + 1);
       // shared-memory sort path sized by the longest run (one warp per coarse row):
@@ -1926,9 +1983,9 @@ void coarsen_all(Hierarchy &h, cudaStream_t s) {
         const int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, kGalSmemBudget / per));
         const size_t smem = per * wpb;
         AMG_CUDA(cudaFuncSetAttribute(k_galerkin_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        AMG_COUNT(), k_galerkin_smem<<<grid_for(nc, wpb, 152 * 64), wpb * 32, smem, s>>>(
-            nc, pcap, hbits, marked_only, L.aptr, L.amem, L.rp, L.ci, L.val, agg, L.pw64, ccount.p, ub.p, tci.p,
-            tval.p, L.plan ? L.gpos : nullptr, L.plan ? L.grow : nullptr, L.plan ? tseg.p : nullptr);
+        AMG_COUNT(), klaunch_sm(k_galerkin_smem, grid_for(nc, wpb, 152 * 64), wpb * 32, smem, s, nc, pcap, hbits,
+            marked_only, L.aptr, L.amem, L.rp, L.ci, L.val, agg, L.pw64, ccount.p, ub.p, tci.p, tval.p,
+            L.plan ? L.gpos : nullptr, L.plan ? L.grow : nullptr, L.plan ? tseg.p : nullptr);
         AMG_LAUNCH_CHECK();
       };
       const int32_t cap1 = std::min(cap, kGalCapFirst);
@@ -1936,8 +1993,8 @@ void coarsen_all(Hierarchy &h, cudaStream_t s) {
       if (mx > cap1) gal_pass(cap, true);
       if (mx > cap) {  // runs longer than the cap: walked from global memory
         const int gw = grid_for((int64_t)nc * 32, 256, 152 * 64);
-        AMG_COUNT(), k_galerkin<true><<<gw, 256, 0, s>>>(nc, L.aptr, L.amem, L.rp, L.ci, L.val, agg, L.pw64,
-                                                         ccount.p, ub.p, tci.p, tval.p, true);
+        AMG_COUNT(), klaunch_sm(k_galerkin<true>, gw, 256, 0, s, nc, L.aptr, L.amem, L.rp, L.ci, L.val, agg, L.pw64,
+            ccount.p, ub.p, tci.p, tval.p, true);
         AMG_LAUNCH_CHECK();
       }
       int32_t cnnz = 0;
@@ -1945,12 +2002,13 @@ void coarsen_all(Hierarchy &h, cudaStream_t s) {
       Cl.nnz = cnnz;
       Cl.ci = h.arena.get<int32_t>(cnnz);
       Cl.val = h.arena.get<double>(cnnz);
-      AMG_COUNT(), k_compact_rows<<<grid_for(nc, 256), 256, 0, s>>>(nc, ub.p, Cl.rp, tci.p, tval.p, Cl.ci, Cl.val);
+      AMG_COUNT(), klaunch_sm(k_compact_rows, grid_for(nc, 256), 256, 0, s, nc, ub.p, Cl.rp, tci.p, tval.p, Cl.ci,
+          Cl.val);
       AMG_LAUNCH_CHECK();
       if (L.plan) {
         L.gptr = h.arena.get<int32_t>((size_t)cnnz + 1);
-        AMG_COUNT(), k_compact_plan<<<grid_for(nc, 256), 256, 0, s>>>(nc, ub.p, Cl.rp, tseg.p, L.gptr,
-                                                                      (int32_t)L.nnz);
+        AMG_COUNT(), klaunch_sm(k_compact_plan, grid_for(nc, 256), 256, 0, s, nc, ub.p, Cl.rp, tseg.p, L.gptr,
+            (int32_t)L.nnz);
         AMG_LAUNCH_CHECK();
       }
     }
@@ -1974,7 +2032,7 @@ void finish_levels(Hierarchy &h, cudaStream_t s, bool fresh) {
     Level &L = h.lev[q];
     build_solve_matrix(h, L, s, fresh);
     diag[q].resize(L.n);
-    AMG_COUNT(), k_diag<<<blocks_for(L.n), 256, 0, s>>>(L.n, L.rp, L.ci, L.val, diag[q].p);
+    AMG_COUNT(), klaunch_sm(k_diag, blocks_for(L.n), 256, 0, s, L.n, L.rp, L.ci, L.val, diag[q].p);
     AMG_LAUNCH_CHECK();
     L.omega = p.omega;  // omega_mode 1; mode 0 reads the estimate back after the loop
     if (q < h.L - 1 && p.omega_mode == 0) {
@@ -1987,7 +2045,7 @@ void finish_levels(Hierarchy &h, cudaStream_t s, bool fresh) {
     }
   }
   if (nj) {  // every level's omega = (4/3) / rho in one launch
-    AMG_COUNT(), k_omega_from_H<<<nj, 32, 0, s>>>(jobs, p.symmetric);
+    AMG_COUNT(), klaunch_sm(k_omega_from_H, nj, 32, 0, s, jobs, p.symmetric);
     AMG_LAUNCH_CHECK();
   }
   for (int q = 0; q < h.L; ++q) make_row_data(h, h.lev[q], diag[q].p, s);  // per-row smoother data
@@ -2023,9 +2081,10 @@ void finish_levels(Hierarchy &h, cudaStream_t s, bool fresh) {
     DevBuf<int> err(1);
     AMG_CUDA(cudaMemsetAsync(dense.p, 0, sizeof(double) * (size_t)boff[h.nsys], s));
     AMG_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
-    AMG_COUNT(), k_dense_blocks<<<h.nsys, 128, 0, s>>>(h.nsys, Lc.sys_off, h.binv_off, Lc.rp, Lc.ci, Lc.val, dense.p);
-    AMG_COUNT(), k_cholesky_inverse_batched<<<h.nsys, 256, 0, s>>>(h.nsys, Lc.sys_off, h.binv_off, dense.p, h.binv,
-                                                                   err.p);
+    AMG_COUNT(), klaunch_sm(k_dense_blocks, h.nsys, 128, 0, s, h.nsys, Lc.sys_off, h.binv_off, Lc.rp, Lc.ci, Lc.val,
+        dense.p);
+    AMG_COUNT(), klaunch_sm(k_cholesky_inverse_batched, h.nsys, 256, 0, s, h.nsys, Lc.sys_off, h.binv_off, dense.p,
+        h.binv, err.p);
     AMG_LAUNCH_CHECK();
     if (read_scalar(err.p, s)) throw Error{AMG_ERR_SETUP, "a system's coarsest matrix is not positive definite"};
     return;
@@ -2040,12 +2099,12 @@ void finish_levels(Hierarchy &h, cudaStream_t s, bool fresh) {
     DevBuf<int> err(1);
     AMG_CUDA(cudaMemsetAsync(dense.p, 0, sizeof(double) * (size_t)Lc.n * Lc.n, s));
     AMG_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
-    AMG_COUNT(), k_dense_from_csr<<<blocks_for(Lc.n), 256, 0, s>>>(Lc.n, Lc.rp, Lc.ci, Lc.val, dense.p);
+    AMG_COUNT(), klaunch_sm(k_dense_from_csr, blocks_for(Lc.n), 256, 0, s, Lc.n, Lc.rp, Lc.ci, Lc.val, dense.p);
     if (p.symmetric) {
-      AMG_COUNT(), k_cholesky_inverse<<<1, 1024, 0, s>>>(Lc.n, dense.p, h.coarse_inv, err.p);
+      AMG_COUNT(), klaunch_sm(k_cholesky_inverse, 1, 1024, 0, s, Lc.n, dense.p, h.coarse_inv, err.p);
     } else {
       DevBuf<double> fac(Lc.n);
-      AMG_COUNT(), k_lu_inverse<<<1, 1024, 0, s>>>(Lc.n, dense.p, h.coarse_inv, fac.p, err.p);
+      AMG_COUNT(), klaunch_sm(k_lu_inverse, 1, 1024, 0, s, Lc.n, dense.p, h.coarse_inv, fac.p, err.p);
     }
     AMG_LAUNCH_CHECK();
     if (read_scalar(err.p, s))
@@ -2069,14 +2128,14 @@ void resetup_values(Hierarchy &h, const double *val0, cudaStream_t s) {
   {
     DevBuf<int> err(1);
     AMG_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
-    AMG_COUNT(), k_check_csr<<<blocks_for(L0.n), 256, 0, s>>>(L0.n, L0.nnz, L0.rp, L0.ci, L0.val, err.p);
+    AMG_COUNT(), klaunch_sm(k_check_csr, blocks_for(L0.n), 256, 0, s, L0.n, L0.nnz, L0.rp, L0.ci, L0.val, err.p);
     AMG_LAUNCH_CHECK();
     if (read_scalar(err.p, s)) throw Error{AMG_ERR_BAD_INPUT, "new values: zero diagonal or non-finite value"};
   }
   for (int k = 0; k + 1 < h.L; ++k) {
     Level &L = h.lev[k], &C = h.lev[k + 1];
-    AMG_COUNT(), k_galerkin_values<<<grid_for(C.nnz, 256, 152 * 32), 256, 0, s>>>(
-        (int32_t)C.nnz, L.gptr, L.gpos, L.grow, L.ci, L.val, L.pw64, C.val);
+    AMG_COUNT(), klaunch_sm(k_galerkin_values, grid_for(C.nnz, 256, 152 * 32), 256, 0, s, (int32_t)C.nnz, L.gptr,
+        L.gpos, L.grow, L.ci, L.val, L.pw64, C.val);
     AMG_LAUNCH_CHECK();
   }
   finish_levels(h, s, false);
