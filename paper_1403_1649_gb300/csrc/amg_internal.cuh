@@ -50,6 +50,12 @@ int64_t &launch_counter();
 // blocks (release threshold = unlimited), so repeated setups do not pay for
 // cudaMalloc/cudaFree and never synchronise the device to free scratch.
 cudaMemPool_t device_pool();
+// a recycled 64-double pinned host buffer and a recycled non-blocking stream of
+// the current device; returned by amg_free
+double *pinned_scratch_get();
+void pinned_scratch_put(double *p);
+cudaStream_t stream_get();
+void stream_put(cudaStream_t st);
 // stream of the API call in progress on this thread (allocation order)
 cudaStream_t &current_stream();
 

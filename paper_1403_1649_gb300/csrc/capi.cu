@@ -1,6 +1,7 @@
 // capi.cu -- the C ABI of include/amg.h: argument checks, stream handoff,
 // error translation (no exception crosses the boundary).
 #include <cstring>
+#include <mutex>
 
 #include "amg_internal.cuh"
 
@@ -29,6 +30,73 @@ cudaStream_t &current_stream() {
 bool &pdl_enabled() {
   static thread_local bool on = true;
   return on;
+}
+
+// Pinned 64-double staging buffers and streams of freed hierarchies are kept
+// for the next one: page-locking host memory and creating streams cost more
+// than a small setup.
+namespace {
+std::mutex g_recycle_mu;
+std::vector<double *> g_pinned_free;
+std::vector<cudaStream_t> g_stream_free[64];  // per device
+int current_device() {
+  int dev = 0;
+  AMG_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) throw Error{AMG_ERR_CUDA, "device index out of range"};
+  return dev;
+}
+}  // namespace
+
+cudaStream_t stream_get() {
+  const int dev = current_device();
+  {
+    std::lock_guard<std::mutex> lk(g_recycle_mu);
+    if (!g_stream_free[dev].empty()) {
+      cudaStream_t st = g_stream_free[dev].back();
+      g_stream_free[dev].pop_back();
+      return st;
+    }
+  }
+  cudaStream_t st = nullptr;
+  AMG_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  return st;
+}
+void stream_put(cudaStream_t st) {  // kept only when idle and not capturing
+  if (!st) return;
+  int dev = 0;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 ||
+      cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone ||
+      cudaStreamQuery(st) != cudaSuccess) {
+    if (cap == cudaStreamCaptureStatusActive) {
+      cudaGraph_t g = nullptr;
+      if (cudaStreamEndCapture(st, &g) == cudaSuccess && g) cudaGraphDestroy(g);
+    }
+    cudaGetLastError();
+    cudaStreamDestroy(st);
+    return;
+  }
+  std::lock_guard<std::mutex> lk(g_recycle_mu);
+  g_stream_free[dev].push_back(st);
+}
+
+double *pinned_scratch_get() {
+  {
+    std::lock_guard<std::mutex> lk(g_recycle_mu);
+    if (!g_pinned_free.empty()) {
+      double *p = g_pinned_free.back();
+      g_pinned_free.pop_back();
+      return p;
+    }
+  }
+  double *p = nullptr;
+  AMG_CUDA(cudaMallocHost(&p, 64 * sizeof(double)));
+  return p;
+}
+void pinned_scratch_put(double *p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_recycle_mu);
+  g_pinned_free.push_back(p);
 }
 
 cudaMemPool_t device_pool() {
@@ -161,7 +229,7 @@ int amg_setup(const amg_csr *A, const amg_params *params, void *stream, amg_hier
   *out = nullptr;
   amg_hierarchy *H = new amg_hierarchy();
   rc = guarded([&]() {
-    AMG_CUDA(cudaStreamCreateWithFlags(&H->stream, cudaStreamNonBlocking));
+    H->stream = amg::stream_get();
     AMG_CUDA(cudaEventCreateWithFlags(&H->ev_in, cudaEventDisableTiming));
     AMG_CUDA(cudaEventCreateWithFlags(&H->ev_out, cudaEventDisableTiming));
     AMG_CUDA(cudaEventCreate(&H->t0));
@@ -232,7 +300,7 @@ int amg_setup_batch(int32_t nsys, const amg_csr *As, const amg_params *params, v
   *out = nullptr;
   amg_hierarchy *H = new amg_hierarchy();
   rc = guarded([&]() {
-    AMG_CUDA(cudaStreamCreateWithFlags(&H->stream, cudaStreamNonBlocking));
+    H->stream = amg::stream_get();
     AMG_CUDA(cudaEventCreateWithFlags(&H->ev_in, cudaEventDisableTiming));
     AMG_CUDA(cudaEventCreateWithFlags(&H->ev_out, cudaEventDisableTiming));
     AMG_CUDA(cudaEventCreate(&H->t0));
@@ -562,12 +630,12 @@ void amg_free(amg_hierarchy *H) {
   amg::current_stream() = H->stream;
   H->h.arena.release();
   if (H->stream) cudaStreamSynchronize(H->stream);
-  if (H->h.host_pinned) cudaFreeHost(H->h.host_pinned);
+  amg::pinned_scratch_put(H->h.host_pinned);
   if (H->ev_in) cudaEventDestroy(H->ev_in);
   if (H->ev_out) cudaEventDestroy(H->ev_out);
   if (H->t0) cudaEventDestroy(H->t0);
   if (H->t1) cudaEventDestroy(H->t1);
-  if (H->stream) cudaStreamDestroy(H->stream);
+  amg::stream_put(H->stream);
   delete H;
 }
 

@@ -1817,7 +1817,7 @@ int arnoldi_omega(Hierarchy &h, int k, const double *diag, double *H, double *wn
 
 void build_hierarchy(Hierarchy &h, const amg_csr &A, cudaStream_t s) {
   const int32_t n = A.n;
-  if (!h.host_pinned) AMG_CUDA(cudaMallocHost(&h.host_pinned, 64 * sizeof(double)));
+  if (!h.host_pinned) h.host_pinned = pinned_scratch_get();
   // ---- level 0: copy and validate the input
   Level &L0 = h.lev[0];
   L0.n = n;
@@ -1855,7 +1855,7 @@ void build_hierarchy(Hierarchy &h, const amg_csr &A, cudaStream_t s) {
 // aggregation never couple the blocks, and roots are numbered in ascending
 // fine index, so every level keeps each system's rows contiguous.
 void build_hierarchy_batch(Hierarchy &h, int32_t nsys, const amg_csr *As, cudaStream_t s) {
-  if (!h.host_pinned) AMG_CUDA(cudaMallocHost(&h.host_pinned, 64 * sizeof(double)));
+  if (!h.host_pinned) h.host_pinned = pinned_scratch_get();
   h.batched = true;
   h.nsys = nsys;
   Level &L0 = h.lev[0];

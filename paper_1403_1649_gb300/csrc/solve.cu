@@ -1499,7 +1499,7 @@ void prepare_t(Hierarchy &h, cudaStream_t s) {
     h.gpart = h.arena.get<double>((size_t)(kMaxRestart + 1) * kRedBlocks);
     AMG_CUDA(cudaMemsetAsync(h.H, 0, sizeof(double) * (m + 1) * m, s));
   }
-  if (!h.host_pinned) AMG_CUDA(cudaMallocHost(&h.host_pinned, 64 * sizeof(double)));
+  if (!h.host_pinned) h.host_pinned = pinned_scratch_get();
   if (h.batched) prepare_batched(h, s);
   configure_tail(h, s);
   if (h.p.autotune) autotune_t<MV, VT>(h, s);
