@@ -1612,15 +1612,31 @@ int run_solve_t(Hierarchy &h, const double *b, double *x, double tol, int32_t *i
         eng.fcg_iteration(active, restart);
       }
     };
-    int *st_host = reinterpret_cast<int *>(h.host_pinned + 32);
-    for (;;) {
+    // The next iteration is queued before this one's state is read, so the GPU
+    // does not wait for the host between iterations; once an iteration stops
+    // (*active = 0) every kernel of the next one returns at once.
+    int *st_host = reinterpret_cast<int *>(h.host_pinned + 32);  // two slots of 8 ints
+    cudaEvent_t evs[2];
+    AMG_CUDA(cudaEventCreateWithFlags(&evs[0], cudaEventDisableTiming));
+    AMG_CUDA(cudaEventCreateWithFlags(&evs[1], cudaEventDisableTiming));
+    auto launch_iter = [&](int slot) {
       enqueue();
-      AMG_CUDA(cudaMemcpyAsync(st_host, h.it_dev, sizeof(int) * 8, cudaMemcpyDeviceToHost, s));
-      AMG_CUDA(cudaStreamSynchronize(s));
-      const int dst = st_host[4];
-      it = st_host[0];
-      if (dst == 0) continue;  // still iterating
-      if (dst == 1) {          // updated residual meets tol: check the true residual
+      AMG_CUDA(cudaMemcpyAsync(st_host + 8 * slot, h.it_dev, sizeof(int) * 8, cudaMemcpyDeviceToHost, s));
+      AMG_CUDA(cudaEventRecord(evs[slot], s));
+    };
+    int slot = 0;
+    launch_iter(slot);
+    for (;;) {
+      launch_iter(slot ^ 1);
+      AMG_CUDA(cudaEventSynchronize(evs[slot]));
+      const int dst = st_host[8 * slot + 4];
+      it = st_host[8 * slot];
+      if (dst == 0) {  // still iterating
+        slot ^= 1;
+        continue;
+      }
+      AMG_CUDA(cudaStreamSynchronize(s));  // the queued iteration ran and did nothing
+      if (dst == 1) {  // updated residual meets tol: check the true residual
         true_residual(h, S_TRUE_RR, s, launches);
         AMG_CUDA(cudaMemcpyAsync(h.host_pinned, L0.slots, sizeof(double) * kNumSlots, cudaMemcpyDeviceToHost, s));
         AMG_CUDA(cudaStreamSynchronize(s));
@@ -1636,11 +1652,16 @@ int run_solve_t(Hierarchy &h, const double *b, double *x, double tol, int32_t *i
         // iterative refinement: restart flexible CG from the true residual
         klaunch(k_set_state, 1, 32, s, h.it_dev, active, restart, h.status_dev, -1, 1, 1, 0);
         AMG_LAUNCH_CHECK();
+        slot = 0;
+        launch_iter(slot);
         continue;
       }
       status = dst;
       break;
     }
+    AMG_CUDA(cudaStreamSynchronize(s));
+    cudaEventDestroy(evs[0]);
+    cudaEventDestroy(evs[1]);
     hist.resize((size_t)it + 1);
     if (it > 0)
       AMG_CUDA(cudaMemcpyAsync(&hist[1], h.hist + 1, sizeof(double) * (size_t)it, cudaMemcpyDeviceToHost, s));
