@@ -232,10 +232,12 @@ __device__ __forceinline__ bool tuple_gt(uint64_t wa, int32_t ia, uint64_t wb, i
 }
 
 // first max round over the closed neighbourhood, from the current states
+// (also clears the round's undecided count *und_reset, which the decision fills)
 __global__ void k_pmis_max1(int32_t n, const int32_t *__restrict__ Sptr, const int32_t *__restrict__ Scol,
                             const int8_t *__restrict__ s, const uint64_t *__restrict__ key,
-                            uint64_t *__restrict__ Tw, int32_t *__restrict__ Ti) {
+                            uint64_t *__restrict__ Tw, int32_t *__restrict__ Ti, int32_t *__restrict__ und_reset) {
   pdl_wait_and_trigger();
+  if (und_reset && blockIdx.x == 0 && threadIdx.x == 0) *und_reset = 0;
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     uint64_t bw = pack_tuple(s[i], key[i]);
     int32_t bi = i;
@@ -277,10 +279,13 @@ __global__ void k_pmis_maxk(int32_t n, const int32_t *__restrict__ Sptr, const i
 
 // the last max round (none for MIS(1)), then the decision of Alg. 2 for
 // undecided nodes
+// The block that finishes last stores the undecided count in the mapped pinned
+// host word host_out, so the host reads it after the round's event without a copy.
 __global__ void k_pmis_max2_decide(int32_t n, const int32_t *__restrict__ Sptr,
                                    const int32_t *__restrict__ Scol, const uint64_t *__restrict__ Tw,
                                    const int32_t *__restrict__ Ti, int8_t *__restrict__ s,
-                                   int32_t *__restrict__ undecided, bool last_max) {
+                                   int32_t *__restrict__ undecided, bool last_max, unsigned *__restrict__ ticket,
+                                   volatile int32_t *host_out) {
   pdl_wait_and_trigger();
   int32_t local = 0;
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -306,6 +311,16 @@ __global__ void k_pmis_max2_decide(int32_t n, const int32_t *__restrict__ Sptr,
   }
   local = __reduce_add_sync(0xffffffffu, local);
   if ((threadIdx.x & 31) == 0 && local) atomicAdd(undecided, local);
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    *host_out = atomicAdd(undecided, 0);
+    *ticket = 0;
+    __threadfence_system();
+  }
 }
 
 // ============================================================== aggregation
@@ -1659,15 +1674,19 @@ Coarsening coarsen_level(Hierarchy &h, int k, cudaStream_t s, int32_t *agg_out, 
     // r-1's count while round r runs.  Once a round leaves no undecided node the
     // round after it changes nothing, so one speculative round is harmless.
     DevBuf<int32_t> und2(2);
+    DevBuf<unsigned> ticket(1);
+    AMG_CUDA(cudaMemsetAsync(ticket.p, 0, sizeof(unsigned), s));
     int32_t *pin = reinterpret_cast<int32_t *>(h.host_pinned);
+    int32_t *pin_dev = nullptr;  // the same words as the device sees them
+    AMG_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void **>(&pin_dev), pin, 0));
     cudaEvent_t ev[2];
     AMG_CUDA(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
     AMG_CUDA(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
     bool done = false;
     for (int round = 0; round < 100000 && !done; ++round) {
       const int b = round & 1;
-      AMG_CUDA(cudaMemsetAsync(und2.p + b, 0, sizeof(int32_t), s));
-      AMG_COUNT(), klaunch_sm(k_pmis_max1, grid_for(n, 256), 256, 0, s, n, Sptr.p, Scol.p, st.p, key.p, Tw.p, Ti.p);
+      AMG_COUNT(), klaunch_sm(k_pmis_max1, grid_for(n, 256), 256, 0, s, n, Sptr.p, Scol.p, st.p, key.p, Tw.p, Ti.p,
+                              und2.p + b);
       uint64_t *tw = Tw.p, *tw2 = Tw2.p;
       int32_t *ti = Ti.p, *ti2 = Ti2.p;
       for (int r = 2; r < mk; ++r) {
@@ -1676,9 +1695,8 @@ Coarsening coarsen_level(Hierarchy &h, int k, cudaStream_t s, int32_t *agg_out, 
         std::swap(ti, ti2);
       }
       AMG_COUNT(), klaunch_sm(k_pmis_max2_decide, grid_for(n, 256), 256, 0, s, n, Sptr.p, Scol.p, tw, ti, st.p,
-                              und2.p + b, mk >= 2);
+                              und2.p + b, mk >= 2, ticket.p, (volatile int32_t *)(pin_dev + b));
       AMG_LAUNCH_CHECK();
-      AMG_CUDA(cudaMemcpyAsync(pin + b, und2.p + b, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
       AMG_CUDA(cudaEventRecord(ev[b], s));
       if (round >= 1) {
         AMG_CUDA(cudaEventSynchronize(ev[b ^ 1]));

@@ -294,6 +294,26 @@ def test_not_converged_and_zero_rhs(gpu):
     assert info["status"] == gpu.AMG_OK and info["iters"] == 0 and not x.any()
 
 
+def test_true_residual_check_and_refinement(gpu):
+    """A tolerance near the FP64 floor: the recursively updated residual meets it
+    before the true residual does, so the solve checks the true residual and
+    restarts flexible CG from it (iterative refinement) until the true residual
+    meets the tolerance or the iteration cap ends the solve."""
+    A = P.poisson2d(37)
+    b = P.rhs_uniform(A.n, 6)
+    for prec in (0, 1):
+        g = gpu.Hierarchy(A, alpha=0.25, seed=5, precision=prec, max_iter=60)
+        x, info = g.solve(b, tol=1e-14, allow=(gpu.AMG_OK, gpu.AMG_ERR_NOT_CONVERGED))
+        true_rel = np.linalg.norm(b - A.matvec(x)) / np.linalg.norm(b)
+        assert len(info["hist"]) == info["iters"] + 1 <= 61
+        assert abs(info["final_relres"] - true_rel) <= 5e-15 + 0.5 * true_rel
+        if info["status"] == gpu.AMG_OK:
+            assert info["final_relres"] <= 1e-14
+        else:
+            assert info["iters"] == 60 and true_rel < 1e-12
+        print(f"precision {prec}: status {info['status']}, {info['iters']} iterations, true relres {true_rel:.2e}")
+
+
 def test_device_and_host_buffers_agree(gpu):
     import torch
     A, alpha, seed = case("poisson3d_20")
