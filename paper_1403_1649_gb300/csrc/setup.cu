@@ -1029,9 +1029,10 @@ __global__ void __launch_bounds__(256) k_arn_start(int32_t n, uint64_t seed, int
 }
 
 // step j, part 1: q_j = W / ||W||; w = M q_j = dh .* (A U) / ||W||;
-// h_lj = q_l . w (l <= j), wn_j = ||w||; h_{j,j-1} = ||W|| (j > 0).  T consecutive lanes share a row: lane t sums the
-// row's entries t, t + T, ... and the T partial sums meet in a fixed shuffle tree,
-// so that the entries of a row are read by neighbouring lanes.
+// h_lj = q_l . w (l <= j), wn_j = ||w||; h_{j,j-1} = ||W|| (j > 0).
+// T consecutive lanes share a row: lane t sums the row's entries t, t + T, ...
+// and the T partial sums meet in a fixed shuffle tree, so that the entries of a
+// row are read by neighbouring lanes.
 template <int T>
 __global__ void __launch_bounds__(256) k_arn_spmv(int32_t n, int j, const int32_t *__restrict__ rp,
                                                   const int32_t *__restrict__ ci, const double *__restrict__ val,
