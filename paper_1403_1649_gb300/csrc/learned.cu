@@ -183,10 +183,6 @@ __global__ void k_adam(int np, float *__restrict__ w, const double *__restrict__
   }
 }
 
-__global__ void k_to_half(int np, const float *__restrict__ w, __half *__restrict__ h) {
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < np; k += gridDim.x * blockDim.x) h[k] = __float2half_rn(w[k]);
-}
-
 // c_q = omega (delta_q0 + o_q)
 __global__ void k_coef_from_out(int32_t n, const float *__restrict__ out, double omega, double *__restrict__ coef) {
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < 3 * n; i += gridDim.x * blockDim.x)
