@@ -436,7 +436,7 @@ __global__ void k_interp(int32_t nc, const int32_t *__restrict__ aptr, const int
 // one term at a time, so every coarse value is the sequential sum.
 constexpr int kGalWarps = 8;   // warps per block of k_galerkin
 constexpr int32_t kGalCapMax = 4096;         // longest run staged by k_galerkin_smem
-constexpr int32_t kGalCapFirst = 112;        // run cap of its first pass (five blocks an SM)
+constexpr int32_t kGalCapFirst = 160;        // run cap of its first pass (three blocks an SM)
 constexpr size_t kGalSmemBudget = 200 << 10;  // its dynamic shared memory per block
 constexpr int kGalCap = 320;   // entries of one coarse row staged in shared memory
 
