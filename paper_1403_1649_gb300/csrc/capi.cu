@@ -101,9 +101,11 @@ void pinned_scratch_put(double *p) {
 
 cudaMemPool_t device_pool() {
   static cudaMemPool_t pools[64] = {};
+  static std::mutex mu;  // threads of one process create each device's pool once
   int dev = 0;
   AMG_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) throw Error{AMG_ERR_CUDA, "device index out of range"};
+  std::lock_guard<std::mutex> lk(mu);
   if (!pools[dev]) {
     cudaMemPoolProps props{};
     props.allocType = cudaMemAllocationTypePinned;
