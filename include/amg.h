@@ -116,7 +116,9 @@ typedef struct amg_solve_info {
   double final_relres;   /* ||b - A x||_2 / ||b||_2 recomputed in FP64 at exit */
   double solve_ms;       /* device time of the last solve (CUDA events)      */
   double setup_ms;       /* device time of the setup (CUDA events)           */
-  int64_t kernel_launches; /* kernels of this library launched by the last solve */
+  int64_t kernel_launches; /* kernels of this library launched by the last solve,
+                              including the one outer iteration queued after the
+                              stopping one (its kernels return at once)          */
   int64_t setup_launches;  /* kernels of this library launched by the setup       */
 } amg_solve_info;
 
@@ -125,7 +127,7 @@ typedef struct amg_hierarchy amg_hierarchy;
 /* Fill *p with the defaults: alpha 0.25, seed 0, coarse_max 64, max_levels 25,
  * kcycle_levels 2, kcycle_t 0.25, omega_mode 0, omega 2/3, precision F64,
  * outer FCG, restart 30, max_iter 500, use_graph 1, smoother 0, tail 0, pdl 1,
- * autotune 0, symmetric 1. */
+ * autotune 0, symmetric 1, mis_k 2. */
 void amg_default_params(amg_params *p);
 
 /* Alg. 1: build the hierarchy of A on the GPU.
