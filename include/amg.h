@@ -23,8 +23,9 @@
  *    setup and solve calls synchronise `stream` before returning because they
  *    take host-side decisions (level sizes, convergence).
  *  - Input arrays are borrowed: read during the call, never freed or kept.
- *  - A hierarchy owns all its device memory (cudaMalloc) and releases it in
- *    amg_free.  A hierarchy is used by one thread at a time.
+ *  - A hierarchy owns all its device memory (from a stream-ordered memory pool
+ *    per device that keeps freed blocks for reuse) and releases it in amg_free.
+ *    A hierarchy is used by one thread at a time.
  */
 #ifndef AMG_GB300_H
 #define AMG_GB300_H
@@ -84,7 +85,8 @@ typedef struct amg_params {
   int32_t tail;          /* run the coarse levels (at most 4096 rows, below the K-cycle
                             levels) in one launch per visit: 1 = a cluster of 8 blocks,
                             2 = a single block; 0 = one kernel per step                    */
-  int32_t pdl;           /* 1: launch solve kernels with programmatic dependent launch     */
+  int32_t pdl;           /* 1: launch setup and solve kernels with programmatic dependent
+                            launch (each kernel waits on its predecessor first)            */
   int32_t autotune;      /* 1: at setup, time each level's SpMV over candidate grid sizes
                             (and, for a batch, the row tile of the per-system inner
                             products) and keep the fastest; the choice is reported in
