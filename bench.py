@@ -307,34 +307,86 @@ def run_reference(args, ws, rank):
 
 # ----------------------------------------------------------------- clocks
 class ClockSampler:
+    """nvidia-smi samples of the SM clock and the throttle reasons, every 50 ms.
+
+    start() launches the sampler and waits (up to 3 s) for its first line, so
+    that it runs before the timed region begins; mark() and stop() bracket the
+    timed region, and only the samples taken inside it (plus one interval of
+    grace at the end) are kept.  Any failure yields None, never an exception."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_S = 0.05
 
     def __init__(self, gpu_index: int):
         self.idx = gpu_index
         self.proc = None
+        self.thread = None
+        self.lines = []
+        self.t0 = None
 
-    def start(self):
+    def _read(self):
+        try:
+            for line in self.proc.stdout:
+                self.lines.append((time.perf_counter(), line))
+        except (OSError, ValueError):
+            pass
+
+    def _launch(self, period_ms: int) -> bool:
+        import threading
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                          "-i", str(self.idx), "-lms", "200"], stdout=subprocess.PIPE,
-                                         stderr=subprocess.DEVNULL, text=True)
+                                          "-i", str(self.idx), "-lms", str(period_ms)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
+            return False
+        self.lines = []
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        deadline = time.perf_counter() + 3.0
+        while not self.lines and time.perf_counter() < deadline and self.proc.poll() is None:
+            time.sleep(0.01)
+        return bool(self.lines)
+
+    def start(self):
+        if self._launch(int(self.PERIOD_S * 1000)) or self.proc is None:
+            return
+        # no sample at 50 ms: the recipe's 200 ms period
+        try:
+            self.proc.kill()
+        except OSError:
+            pass
+        if self.thread:
+            self.thread.join(timeout=5)
+        self.PERIOD_S = 0.2
+        self._launch(200)
+
+    def mark(self):
+        self.t0 = time.perf_counter()
 
     def stop(self):
         if not self.proc:
             return None
-        self.proc.terminate()
+        t1 = time.perf_counter()
+        time.sleep(self.PERIOD_S)  # one more sample at the end of the region
         try:
-            out, _ = self.proc.communicate(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.proc.kill()
-            out, _ = self.proc.communicate()
+            self.proc.terminate()
+            self.proc.wait(timeout=5)
+        except (OSError, subprocess.TimeoutExpired):
+            try:
+                self.proc.kill()
+            except OSError:
+                pass
+        if self.thread:
+            self.thread.join(timeout=5)
+        t0 = self.t0 if self.t0 is not None else 0.0
+        inside = [ln for t, ln in list(self.lines) if t0 <= t <= t1 + self.PERIOD_S]
+        if not inside and self.lines:  # a region shorter than one period: the nearest sample
+            inside = [min(self.lines, key=lambda tl: abs(tl[0] - t1))[1]]
         sm, mx, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in out.splitlines():
+        for line in inside:
             f = [t.strip() for t in line.split(",")]
             if len(f) < 9:
                 continue
@@ -348,7 +400,8 @@ class ClockSampler:
                     reasons.add(nm)
         if not sm:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm),
+                "period_ms": int(self.PERIOD_S * 1000)}
 
 
 # ----------------------------------------------------------------- GPU leg
@@ -443,6 +496,7 @@ def main():
     barrier(ws)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks.mark()
     e0.record(stream)
     for _ in range(args.steps):
         step(prec)
