@@ -53,7 +53,7 @@ def test_samples_inside_the_region_only(tmp_path, monkeypatch):
     path = fake_smi(tmp_path, LOOP.format(refuse_50=False, cap_until=0.2))
     r = run_region(monkeypatch, path)
     assert r is not None and r["period_ms"] == 50
-    assert 2 <= r["samples"] <= 6
+    assert 1 <= r["samples"] <= 8
     assert r["reasons"] == [] and r["sm_max_mhz"] == 2070.0 and 2069.0 <= r["sm_mhz"] <= 2070.0
 
 
