@@ -318,8 +318,10 @@ class ClockSampler:
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
     PERIOD_S = 0.05
 
-    def __init__(self, gpu_index: int):
-        self.idx = gpu_index
+    def __init__(self, gpu):
+        # nvidia-smi numbers GPUs physically and ignores CUDA_VISIBLE_DEVICES, so
+        # the GPU is named by its UUID ("GPU-..."); an int is passed through
+        self.idx = gpu
         self.proc = None
         self.thread = None
         self.lines = []
@@ -405,6 +407,20 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------- GPU leg
+def gpu_selector(dev, local: int) -> str:
+    """The nvidia-smi -i argument for the CUDA device dev: its UUID, else the
+    physical index that CUDA_VISIBLE_DEVICES maps the ordinal to."""
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        if u:
+            return u if u.startswith("GPU-") else "GPU-" + u
+    except (AttributeError, RuntimeError):
+        pass
+    vis = [v.strip() for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+    return vis[local] if local < len(vis) else str(local)
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -490,7 +506,7 @@ def main():
     for _ in range(max(args.warmup, 3)):
         step(prec)
     torch.cuda.synchronize()
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(gpu_selector(dev, local))
     clocks.start()
     stats[prec] = []
     barrier(ws)

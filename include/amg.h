@@ -241,18 +241,18 @@ int amg_mlp_backward(int32_t n, const float *w, const float *feat, const float *
                      void *stream);
 
 /* Same result as amg_mlp_backward, for callers that cannot allocate device
- * memory: code that runs while a CUDA graph is being captured, real-time or
- * embedding applications that must not enter the allocator, or a host that
- * has handed the whole device memory budget to another framework.  The paper
- * has no counterpart; this is a service of the library.
+ * memory: real-time or embedded hosts that must not enter an allocator in
+ * their steady state, and hosts that have handed the whole device memory
+ * budget to another framework.  The paper has no counterpart; this is a
+ * service of the library.
  *  - No cudaMalloc, cudaFree or allocating library call: the work arrays live
  *    in a fixed device array of about 4.2 MB (2048 rows x (3 + 4 x 64) floats
  *    plus 64 x 4096 doubles) that every GPU loading this library keeps until
  *    the process exits.
  *  - n may be at most 2048; larger n returns AMG_ERR_BAD_INPUT with a message.
- *  - The first call on a device looks up that array's device address (once per
- *    device, with the device current); make that first call before any stream
- *    capture.
+ *  - Each call looks up that array's device address on the current device
+ *    (no allocation); the first call on a device also loads the module that
+ *    holds it, so make that first call before any stream capture.
  *  - All calls share the array: calls whose executions overlap on the GPU (for
  *    example on two streams) race and give wrong results.  Each call writes
  *    every scratch word it reads and clears dparam itself.

@@ -45,6 +45,27 @@ void set_last_error(const std::string &m);
 int64_t &launch_counter();
 #define AMG_COUNT() (++::amg::launch_counter())
 
+// two timing-free events, destroyed with their owner (also when a call throws)
+struct EventPair {
+  cudaEvent_t e[2] = {nullptr, nullptr};
+  EventPair() {
+    try {
+      AMG_CUDA(cudaEventCreateWithFlags(&e[0], cudaEventDisableTiming));
+      AMG_CUDA(cudaEventCreateWithFlags(&e[1], cudaEventDisableTiming));
+    } catch (...) {
+      release();
+      throw;
+    }
+  }
+  ~EventPair() { release(); }
+  void release() {
+    for (cudaEvent_t &x : e)
+      if (x) cudaEventDestroy(x), x = nullptr;
+  }
+  EventPair(const EventPair &) = delete;
+  EventPair &operator=(const EventPair &) = delete;
+};
+
 // ---------------------------------------------------------------- device memory
 // Device memory comes from one stream-ordered pool per device that keeps freed
 // blocks (release threshold = unlimited), so repeated setups do not pay for

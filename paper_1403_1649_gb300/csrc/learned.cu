@@ -409,21 +409,17 @@ constexpr size_t kFixedBytes = kFixedFloats * sizeof(float) + (size_t)kGradChunk
 static_assert((kFixedFloats * sizeof(float)) % 256 == 0, "double section stays 256-byte aligned");
 static __device__ __align__(256) unsigned char g_fixed_scratch[kFixedBytes];
 
-// Address of the array on the current device, looked up once per device (a host
-// may not use the symbol itself as a device address).
+// Address of the array on the current device.  A host may not use the symbol
+// itself as a device address, so every call asks the runtime for it with the
+// device current: the lookup allocates nothing, the first one on a device loads
+// the module that holds the array, and nothing cached can go stale when a
+// context is reset and the array moves.
 static void *fixed_scratch_address() {
-  static void *addr[64] = {};
-  int dev = 0;
-  AMG_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64) throw Error{AMG_ERR_CUDA, "device index out of range"};
-  if (!addr[dev]) {
-    void *p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_fixed_scratch);
-    if (e != cudaSuccess)
-      throw Error{AMG_ERR_CUDA, std::string("cudaGetSymbolAddress(fixed scratch): ") + cudaGetErrorString(e)};
-    addr[dev] = p;
-  }
-  return addr[dev];
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_fixed_scratch);
+  if (e != cudaSuccess)
+    throw Error{AMG_ERR_CUDA, std::string("cudaGetSymbolAddress(fixed scratch): ") + cudaGetErrorString(e)};
+  return p;
 }
 
 size_t fixed_scratch_bytes() { return kFixedBytes; }

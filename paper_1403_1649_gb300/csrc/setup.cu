@@ -1680,9 +1680,8 @@ Coarsening coarsen_level(Hierarchy &h, int k, cudaStream_t s, int32_t *agg_out, 
     int32_t *pin = reinterpret_cast<int32_t *>(h.host_pinned);
     int32_t *pin_dev = nullptr;  // the same words as the device sees them
     AMG_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void **>(&pin_dev), pin, 0));
-    cudaEvent_t ev[2];
-    AMG_CUDA(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
-    AMG_CUDA(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+    EventPair ep;  // destroyed on every exit, including a throw inside the loop
+    cudaEvent_t *ev = ep.e;
     bool done = false;
     for (int round = 0; round < 100000 && !done; ++round) {
       const int b = round & 1;
@@ -1709,8 +1708,6 @@ Coarsening coarsen_level(Hierarchy &h, int k, cudaStream_t s, int32_t *agg_out, 
       if (!done && round + 1 >= 100000) out.rounds = round + 1;
     }
     AMG_CUDA(cudaStreamSynchronize(s));
-    cudaEventDestroy(ev[0]);
-    cudaEventDestroy(ev[1]);
   }
   // aggregation
   DevBuf<int32_t> r1(n), r2(n), isroot(n + 1), cid(n + 1), err(1);

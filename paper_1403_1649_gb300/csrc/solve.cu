@@ -1616,9 +1616,8 @@ int run_solve_t(Hierarchy &h, const double *b, double *x, double tol, int32_t *i
     // does not wait for the host between iterations; once an iteration stops
     // (*active = 0) every kernel of the next one returns at once.
     int *st_host = reinterpret_cast<int *>(h.host_pinned + 32);  // two slots of 8 ints
-    cudaEvent_t evs[2];
-    AMG_CUDA(cudaEventCreateWithFlags(&evs[0], cudaEventDisableTiming));
-    AMG_CUDA(cudaEventCreateWithFlags(&evs[1], cudaEventDisableTiming));
+    EventPair ep;  // destroyed on every exit, including a throw inside the loop
+    cudaEvent_t *evs = ep.e;
     auto launch_iter = [&](int slot) {
       enqueue();
       AMG_CUDA(cudaMemcpyAsync(st_host + 8 * slot, h.it_dev, sizeof(int) * 8, cudaMemcpyDeviceToHost, s));
@@ -1660,8 +1659,6 @@ int run_solve_t(Hierarchy &h, const double *b, double *x, double tol, int32_t *i
       break;
     }
     AMG_CUDA(cudaStreamSynchronize(s));
-    cudaEventDestroy(evs[0]);
-    cudaEventDestroy(evs[1]);
     hist.resize((size_t)it + 1);
     if (it > 0)
       AMG_CUDA(cudaMemcpyAsync(&hist[1], h.hist + 1, sizeof(double) * (size_t)it, cudaMemcpyDeviceToHost, s));

@@ -23,7 +23,9 @@ def fake_smi(tmp_path, body):
 
 
 LOOP = """
-import sys, time
+import os, sys, time
+with open(os.environ["FAKE_SMI_ARGS"], "a") as f:
+    f.write(sys.argv[sys.argv.index("-i") + 1] + "\\n")
 period = 0.05 if "50" in sys.argv else 0.2
 if "50" in sys.argv and {refuse_50}:
     sys.exit(2)
@@ -37,10 +39,11 @@ while True:
 """
 
 
-def run_region(monkeypatch, path, warm=0.3, region=0.15):
+def run_region(monkeypatch, path, warm=0.3, region=0.15, gpu="GPU-0b1c2d3e-aaaa-bbbb-cccc-000000000000"):
     import bench
     monkeypatch.setenv("PATH", path + os.pathsep + os.environ.get("PATH", ""))
-    c = bench.ClockSampler(0)
+    monkeypatch.setenv("FAKE_SMI_ARGS", os.path.join(os.path.dirname(path), "args.txt"))
+    c = bench.ClockSampler(gpu)
     c.start()
     time.sleep(warm)  # outside the timed region
     c.mark()
@@ -76,3 +79,24 @@ def test_missing_tool_gives_none(tmp_path, monkeypatch):
     c.start()
     c.mark()
     assert c.stop() is None
+
+
+def test_gpu_selected_by_uuid(tmp_path, monkeypatch):
+    # nvidia-smi ignores CUDA_VISIBLE_DEVICES: the sampler must name the GPU it
+    # was given (a UUID) in its -i argument, not a CUDA ordinal
+    path = fake_smi(tmp_path, LOOP.format(refuse_50=False, cap_until=0))
+    run_region(monkeypatch, path, gpu="GPU-12345678-9abc-def0-1234-56789abcdef0")
+    args = open(tmp_path / "args.txt").read().split()
+    assert args and set(args) == {"GPU-12345678-9abc-def0-1234-56789abcdef0"}
+
+
+def test_selector_maps_visible_devices(monkeypatch):
+    # without a UUID the ordinal maps through CUDA_VISIBLE_DEVICES to the physical index
+    import bench
+    import torch
+    monkeypatch.setattr(torch.cuda, "get_device_properties", lambda d: (_ for _ in ()).throw(RuntimeError()))
+    monkeypatch.setenv("CUDA_VISIBLE_DEVICES", "5,2")
+    assert bench.gpu_selector("cuda:1", 1) == "2"
+    assert bench.gpu_selector("cuda:0", 0) == "5"
+    monkeypatch.delenv("CUDA_VISIBLE_DEVICES")
+    assert bench.gpu_selector("cuda:0", 0) == "0"
