@@ -67,16 +67,14 @@ def timed(fn, reps):
     return float(np.median(ts)), out
 
 
-def other_workload(args):
-    """One JSON line for a configuration other than the benchmark line."""
+def workload_results(name: str, reps: int = 1):
+    """Setup + solve of one of the other configurations on GPU 0, each variant
+    timed as the median of reps runs after one warm-up (CUDA events).  Returns
+    (headline value in DoF/s, ms per step, dtype, config, per-variant results)."""
     import torch
-    from paper_1403_1649_gb300 import amg, build
+    from paper_1403_1649_gb300 import amg
     from paper_1403_1649_gb300 import problems as P
-    build.build()
     dev = torch.device("cuda", 0)
-    reps = max(args.steps, 1)
-    line = {"metric": METRIC, "unit": "DoF/s", "n_gpus": 1, "steps": reps, "warmup": 1, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "data": "synthetic"}
 
     def run_single(A, b, **pk):
         rp, ci, va = (torch.from_numpy(a).to(dev) for a in (A.rowptr, A.col, A.val))
@@ -89,7 +87,7 @@ def other_workload(args):
             if pk.get("smoother") == 1:
                 amg.lib().amg_apply_learned_smoother(h, info["w16"].ctypes.data, None)
             xd.zero_()
-            amg.amg_solve(h, bd, xd, TOL, 2000)
+            amg.amg_solve(h, bd, xd, TOL, pk.get("max_iter", 2000), allow=info.get("allow", (amg.AMG_OK,)))
             i = amg.amg_last_solve_info(h)
             amg.amg_free(h)
             return i
@@ -105,100 +103,105 @@ def other_workload(args):
         w[:5248] = (rng.normal(size=5248) * 0.2).astype(np.float32)
         hist = np.zeros(150)
         arr = (C_void_p_array(len(train)))(*[t.h for t in train])
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
         rc = amg.lib().amg_train_smoother(arr, len(train), 150, 3e-3, 2, 11, w.ctypes.data, hist.ctypes.data, None)
         assert rc == 0, amg.amg_last_error()
         return w.astype(np.float16).view(np.uint16), time.perf_counter() - t0, hist
 
-    if args.workload == "varcoef3d_160":
+    def summary(t, i):
+        return {"ms": t, "setup_ms": i["setup_ms"], "solve_ms": i["solve_ms"], "iters": i["iters"],
+                "final_relres": i["final_relres"], "converged": i["status"] == amg.AMG_OK}
+
+    if name == "varcoef3d_160":
         A = P.varcoef3d(160, 2)
         b = P.rhs_uniform(A.n, 2)
         res = {}
-        allow = (amg.AMG_OK, amg.AMG_ERR_NOT_CONVERGED)
-        for name, pk in (("fgmres30_bf16", dict(outer=1, precision=2)), ("fgmres30_f64", dict(outer=1, precision=0)),
-                         ("fcg_bf16", dict(outer=0, precision=2)), ("fcg_f32", dict(outer=0, precision=1)),
-                         ("fcg_f64", dict(outer=0, precision=0))):
+        for var, pk in (("fcg_bf16", dict(outer=0, precision=2)), ("fcg_f32", dict(outer=0, precision=1)),
+                        ("fcg_f64", dict(outer=0, precision=0)), ("fgmres30_bf16", dict(outer=1, precision=2)),
+                        ("fgmres30_f64", dict(outer=1, precision=0))):
             cap = 600 if pk["outer"] == 1 else 2000
-            rp, ci, va = (torch.from_numpy(a).to(dev) for a in (A.rowptr, A.col, A.val))
-            bd = torch.from_numpy(b).to(dev)
-            xd = torch.zeros_like(bd)
-
-            def go():
-                h = amg.amg_setup(rp, ci, va, amg.amg_default_params(alpha=0.5, seed=2, restart=30, max_iter=cap, **pk))
-                xd.zero_()
-                amg.amg_solve(h, bd, xd, TOL, cap, allow=allow)
-                i = amg.amg_last_solve_info(h)
-                amg.amg_free(h)
-                return i
+            go, info = run_single(A, b, alpha=0.5, seed=2, restart=30, max_iter=cap, **pk)
+            info["allow"] = (amg.AMG_OK, amg.AMG_ERR_NOT_CONVERGED)
             t, i = timed(go, reps)
-            res[name] = {"ms": t, "setup_ms": i["setup_ms"], "solve_ms": i["solve_ms"], "iters": i["iters"],
-                         "final_relres": i["final_relres"], "converged": i["status"] == amg.AMG_OK}
-        line.update(value=A.n / (res["fcg_bf16"]["ms"] / 1e3), ms_per_step=res["fcg_bf16"]["ms"], dtype="bf16+f32+f64",
-                    config={"workload": "3D finite-volume -div(k grad u) 160^3 (n=4,096,000), k log-uniform "
-                                        "[1e-3,1e3] on 8^3 blocks, z x100 on x<80; K-cycle AMG, BF16 matrix values "
-                                        "(compensated FP32 diagonal) / FP32 vectors vs FP64, to 1e-8",
-                            "headline": "flexible CG with the BF16 preconditioner (FGMRES(30) stalls on this "
-                                        "problem: see fgmres30_* final_relres after 600 iterations)"},
-                    compare=res)
-    elif args.workload == "fem2d_1024":
+            res[var] = summary(t, i)
+        config = {"workload": "3D finite-volume -div(k grad u) 160^3 (n=4,096,000), k log-uniform "
+                              "[1e-3,1e3] on 8^3 blocks, z x100 on x<80; K-cycle AMG, BF16 matrix values "
+                              "(compensated FP32 diagonal) / FP32 vectors vs FP64, to 1e-8",
+                  "headline": "flexible CG with the BF16 preconditioner (FGMRES(30) stalls on this "
+                              "problem: see fgmres30_* final_relres after 600 iterations)"}
+        head = res["fcg_bf16"]
+        return A.n / (head["ms"] / 1e3), head["ms"], "bf16+f32+f64", config, res
+    if name == "fem2d_1024":
         A = P.fem2d(1024, 3)
         b = P.rhs_uniform(A.n, 3)
         w16, train_s, hist = train_weights(P.fem2d, 200)
         res = {}
-        for name, pk in (("jacobi_f64", dict(precision=0)), ("jacobi_f32", dict(precision=1)),
-                         ("learned_f32", dict(precision=1, smoother=1)), ("learned_f64", dict(precision=0, smoother=1))):
+        for var, pk in (("learned_f32", dict(precision=1, smoother=1)), ("jacobi_f64", dict(precision=0)),
+                        ("jacobi_f32", dict(precision=1)), ("learned_f64", dict(precision=0, smoother=1))):
             go, info = run_single(A, b, alpha=0.25, seed=3, omega_mode=1, omega=2.0 / 3.0, max_iter=2000, **pk)
             info["w16"] = w16
             t, i = timed(go, reps)
-            res[name] = {"ms": t, "setup_ms": i["setup_ms"], "solve_ms": i["solve_ms"], "iters": i["iters"],
-                         "final_relres": i["final_relres"]}
-        line.update(value=A.n / (res["learned_f32"]["ms"] / 1e3), ms_per_step=res["learned_f32"]["ms"],
-                    dtype="f32+f64",
-                    config={"workload": "2D P1 FEM, jittered 1024^2 nodes (n=1,048,576), learned per-row "
-                                        "polynomial smoother (MLP 16-64-64-3, FP16 weights) vs damped Jacobi "
-                                        "omega=2/3, flexible CG to 1e-8",
-                            "training": f"150 Adam steps on 4 two-level FEM problems (48^2..96^2), {train_s:.1f} s, "
-                                        f"two-grid factor {hist[0]:.4f} -> {hist[-1]:.4f}"},
-                    compare=res)
-    else:  # batch512
-        sides = P.batch_sizes(512, 4)
-        t0 = time.perf_counter()
-        mats = [P.varcoef2d(int(m), 4 + q) for q, m in enumerate(sides)]
-        rhs = np.concatenate([P.rhs_uniform(A.n, 4 + q) for q, A in enumerate(mats)])
-        gen_s = time.perf_counter() - t0
-        w16, train_s, hist = train_weights(lambda m, sd: P.varcoef2d(m, sd), 300)
-        dmats = [tuple(torch.from_numpy(a).to(dev) for a in (A.rowptr, A.col, A.val)) for A in mats]
-        bd = torch.from_numpy(rhs).to(dev)
-        xd = torch.zeros_like(bd)
-        ntot = int(rhs.size)
-        res = {}
-        shapes = {}
-        for name, pk in (("learned_f32_tuned", dict(precision=1, smoother=1, omega_mode=1, omega=2.0 / 3.0, autotune=1)),
-                         ("jacobi_f32_tuned", dict(precision=1, autotune=1)),
-                         ("jacobi_f64", dict(precision=0))):
-            def go():
-                h = amg.amg_setup_batch(dmats, amg.amg_default_params(alpha=0.25, seed=4, max_iter=2000, **pk))
-                if pk.get("smoother") == 1:
-                    assert amg.lib().amg_apply_learned_smoother(h, w16.ctypes.data, None) == 0, amg.amg_last_error()
-                xd.zero_()
-                rc, it, rel = amg.amg_solve_batch(h, bd, xd, TOL, len(mats))
-                i = amg.amg_last_solve_info(h)
-                lv = amg.amg_hierarchy_info(h)
-                amg.amg_free(h)
-                return i, it, rel, lv
-            t, (i, it, rel, lv) = timed(go, reps)
-            res[name] = {"ms": t, "setup_ms": i["setup_ms"], "solve_ms": i["solve_ms"], "max_iters": int(it.max()),
-                         "mean_iters": float(it.mean()), "worst_relres": float(rel.max())}
-            shapes[name] = [(l["n"], l["spmv_blocks"], l["seg_tile"]) for l in lv]
-        line.update(value=ntot / (res["learned_f32_tuned"]["ms"] / 1e3), ms_per_step=res["learned_f32_tuned"]["ms"],
-                    dtype="f32+f64",
-                    config={"workload": f"512 independent 2D variable-coefficient 5-point systems, sides uniform "
-                                        f"32..512 (n={ntot:,}), k log-uniform [1e-2,1e2]; one block-diagonal "
-                                        f"hierarchy, per-system flexible CG to 1e-8 (generation {gen_s:.0f} s)",
-                            "training": f"150 Adam steps on 4 two-level variable-coefficient problems (48^2..96^2), "
-                                        f"{train_s:.1f} s, two-grid factor {hist[0]:.4f} -> {hist[-1]:.4f}",
-                            "autotuned_shapes": shapes["learned_f32_tuned"]},
-                    compare=res)
+            res[var] = summary(t, i)
+        res["training_s"] = train_s
+        config = {"workload": "2D P1 FEM, jittered 1024^2 nodes (n=1,048,576), learned per-row "
+                              "polynomial smoother (MLP 16-64-64-3, FP16 weights) vs damped Jacobi "
+                              "omega=2/3, flexible CG to 1e-8",
+                  "training": f"150 Adam steps on 4 two-level FEM problems (48^2..96^2), {train_s:.2f} s, "
+                              f"two-grid factor {hist[0]:.4f} -> {hist[-1]:.4f}"}
+        head = res["learned_f32"]
+        return A.n / (head["ms"] / 1e3), head["ms"], "f32+f64", config, res
+    # batch512
+    sides = P.batch_sizes(512, 4)
+    t0 = time.perf_counter()
+    mats = [P.varcoef2d(int(m), 4 + q) for q, m in enumerate(sides)]
+    rhs = np.concatenate([P.rhs_uniform(A.n, 4 + q) for q, A in enumerate(mats)])
+    gen_s = time.perf_counter() - t0
+    w16, train_s, hist = train_weights(lambda m, sd: P.varcoef2d(m, sd), 300)
+    dmats = [tuple(torch.from_numpy(a).to(dev) for a in (A.rowptr, A.col, A.val)) for A in mats]
+    bd = torch.from_numpy(rhs).to(dev)
+    xd = torch.zeros_like(bd)
+    ntot = int(rhs.size)
+    res = {}
+    shapes = {}
+    for var, pk in (("learned_f32_tuned", dict(precision=1, smoother=1, omega_mode=1, omega=2.0 / 3.0, autotune=1)),
+                    ("jacobi_f32_tuned", dict(precision=1, autotune=1)),
+                    ("jacobi_f64", dict(precision=0))):
+        def go():
+            h = amg.amg_setup_batch(dmats, amg.amg_default_params(alpha=0.25, seed=4, max_iter=2000, **pk))
+            if pk.get("smoother") == 1:
+                assert amg.lib().amg_apply_learned_smoother(h, w16.ctypes.data, None) == 0, amg.amg_last_error()
+            xd.zero_()
+            rc, it, rel = amg.amg_solve_batch(h, bd, xd, TOL, len(mats))
+            i = amg.amg_last_solve_info(h)
+            lv = amg.amg_hierarchy_info(h)
+            amg.amg_free(h)
+            return i, it, rel, lv
+        t, (i, it, rel, lv) = timed(go, reps)
+        res[var] = {"ms": t, "setup_ms": i["setup_ms"], "solve_ms": i["solve_ms"], "max_iters": int(it.max()),
+                    "mean_iters": float(it.mean()), "worst_relres": float(rel.max()),
+                    "converged": bool((rel <= TOL).all())}
+        shapes[var] = [(l["n"], l["spmv_blocks"], l["seg_tile"]) for l in lv]
+    res["training_s"] = train_s
+    config = {"workload": f"512 independent 2D variable-coefficient 5-point systems, sides uniform "
+                          f"32..512 (n={ntot:,}), k log-uniform [1e-2,1e2]; one block-diagonal "
+                          f"hierarchy, per-system flexible CG to 1e-8 (generation {gen_s:.0f} s)",
+              "training": f"150 Adam steps on 4 two-level variable-coefficient problems (48^2..96^2), "
+                          f"{train_s:.2f} s, two-grid factor {hist[0]:.4f} -> {hist[-1]:.4f}",
+              "autotuned_shapes": shapes["learned_f32_tuned"]}
+    head = res["learned_f32_tuned"]
+    return ntot / (head["ms"] / 1e3), head["ms"], "f32+f64", config, res
+
+
+def other_workload(args):
+    """One JSON line for a configuration other than the benchmark line."""
+    from paper_1403_1649_gb300 import build
+    build.build()
+    reps = max(args.steps, 1)
+    value, ms, dtype, config, res = workload_results(args.workload, reps)
+    line = {"metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": 1, "steps": reps, "warmup": 1,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+            "data": "synthetic", "config": config, "compare": res}
     print(json.dumps(line), flush=True)
 
 

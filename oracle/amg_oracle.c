@@ -27,6 +27,30 @@
 #define OR_MAX_LEVELS 40
 #define OR_MAX_DENSE 8192
 
+/* The CPU-baseline timing build (compiled again with -fopenmp) runs the row
+ * loops of the solve stage on all host cores.  Its inner products add fixed
+ * chunks of OR_DOT_CHUNK terms in order and then the chunk sums in order, so
+ * its results do not depend on the thread count (they differ from this
+ * single-threaded build by rounding only), and its restriction sums each
+ * aggregate's members in ascending order as the scatter below does.  The
+ * setup stays single-threaded.  The plain build (no -fopenmp) is the parity
+ * reference; none of this is compiled into it. */
+#ifdef _OPENMP
+#include <omp.h>
+#define OR_PAR _Pragma("omp parallel for schedule(static)")
+#define OR_DOT_CHUNK 8192
+#else
+#define OR_PAR
+#endif
+
+int32_t or_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
 /* ------------------------------------------------------------------------- */
 /* counter-based random numbers: splitmix64 (Steele, Lea, Flood 2014)        */
 /* ------------------------------------------------------------------------- */
@@ -117,12 +141,13 @@ int64_t or_sym_graph(int32_t n, const int32_t *rp, const int32_t *ci, const uint
         tmp[off[i] + fill[i]++] = j;
         tmp[off[j] + fill[j]++] = i;
       }
+  OR_PAR
+  for (int32_t i = 0; i < n; ++i) qsort(tmp + off[i], (size_t)(off[i + 1] - off[i]), sizeof(int32_t), cmp_i32);
   int64_t total = 0;
   Sptr[0] = 0;
-  for (int32_t i = 0; i < n; ++i) {
+  for (int32_t i = 0; i < n; ++i) { /* each row sorted: drop repeats */
     int32_t *row = tmp + off[i];
     int32_t len = (int32_t)(off[i + 1] - off[i]);
-    qsort(row, (size_t)len, sizeof(int32_t), cmp_i32);
     for (int32_t k = 0; k < len; ++k) {
       if (k > 0 && row[k] == row[k - 1]) continue;
       if (total < cap) Scol[total] = row[k];
@@ -162,9 +187,13 @@ int32_t or_pmis(int32_t n, const int32_t *Sptr, const int32_t *Scol, const int32
   int32_t rounds = 0;
   for (;;) {
     int32_t undecided = 0;
+#ifdef _OPENMP
+#pragma omp parallel for reduction(+ : undecided)
+#endif
     for (int32_t i = 0; i < n; ++i) undecided += (s[i] == 0);
     if (undecided == 0) break;
     rounds++;
+    OR_PAR
     for (int32_t i = 0; i < n; ++i) { /* T_i <- (s_i, v_i, i) */
       T[i].s = s[i];
       T[i].cnt = count[i];
@@ -172,6 +201,7 @@ int32_t or_pmis(int32_t n, const int32_t *Sptr, const int32_t *Scol, const int32
       T[i].i = i;
     }
     for (int d = 1; d <= k; ++d) { /* k rounds of max over the closed neighbourhood */
+      OR_PAR
       for (int32_t i = 0; i < n; ++i) {
         tuple_t t = T[i];
         for (int32_t q = Sptr[i]; q < Sptr[i + 1]; ++q)
@@ -182,6 +212,7 @@ int32_t or_pmis(int32_t n, const int32_t *Sptr, const int32_t *Scol, const int32
       T = That;
       That = sw;
     }
+    OR_PAR
     for (int32_t i = 0; i < n; ++i) { /* decide undecided nodes */
       if (s[i] != 0) continue;
       if (T[i].i == i)
@@ -311,7 +342,26 @@ int64_t or_galerkin(int32_t n, const int32_t *rp, const int32_t *ci, const doubl
       e[p].pos = p;
       e[p].v = P ? (P[i] * val[p]) * P[j] : val[p];
     }
+#ifdef _OPENMP
+  { /* the same order as the one sort below: a stable counting sort of the
+       entries by I (positions stay ascending), then each row's run sorted by
+       (J, pos) on its own */
+    int64_t *bo = (int64_t *)calloc((size_t)nc + 2, sizeof(int64_t));
+    for (int64_t q = 0; q < nnz; ++q) bo[e[q].I + 1]++;
+    for (int32_t I = 0; I < nc; ++I) bo[I + 1] += bo[I];
+    gentry_t *e2 = (gentry_t *)malloc(sizeof(gentry_t) * (size_t)(nnz + 1));
+    int64_t *fill = (int64_t *)calloc((size_t)nc + 1, sizeof(int64_t));
+    for (int64_t q = 0; q < nnz; ++q) e2[bo[e[q].I] + fill[e[q].I]++] = e[q];
+    OR_PAR
+    for (int32_t I = 0; I < nc; ++I) qsort(e2 + bo[I], (size_t)(bo[I + 1] - bo[I]), sizeof(gentry_t), cmp_gentry);
+    free(e);
+    free(fill);
+    free(bo);
+    e = e2;
+  }
+#else
   qsort(e, (size_t)nnz, sizeof(gentry_t), cmp_gentry);
+#endif
   int64_t out = 0;
   for (int32_t I = 0; I <= nc; ++I) crp[I] = 0;
   int64_t q = 0;
@@ -597,6 +647,7 @@ typedef struct {
   double *P;     /* P_k(i, Agg(i))            */
   double *B;     /* near-null vector B_k      */
   double *poly;  /* n x 3 smoother coefficients or NULL */
+  int32_t *aptr, *amem; /* members of every aggregate, ascending (timing build only) */
   /* work vectors of this level */
   double *r, *bc, *xc, *c, *v, *rt, *d, *w, *u0, *u1;
 } or_level;
@@ -645,7 +696,7 @@ static void level_alloc_work(or_level *l) {
 
 static void level_free(or_level *l) {
   free(l->rp); free(l->ci); free(l->val); free(l->dinv); free(l->wd); free(l->agg);
-  free(l->P); free(l->B); free(l->poly);
+  free(l->P); free(l->B); free(l->poly); free(l->aptr); free(l->amem);
   free(l->r); free(l->bc); free(l->xc); free(l->c); free(l->v); free(l->rt); free(l->d);
   free(l->w); free(l->u0); free(l->u1);
 }
@@ -671,6 +722,39 @@ static int32_t check_csr(int32_t n, const int32_t *rp, const int32_t *ci, const 
     }
     if (!diag) return -2;
   }
+  return 0;
+}
+
+/* aggregate member lists (ascending) for the restriction of the timing build */
+static void build_members(or_hier *h) {
+#ifdef _OPENMP
+  for (int32_t q = 0; q < h->L - 1; ++q) {
+    or_level *L = &h->lev[q];
+    L->aptr = (int32_t *)calloc((size_t)L->nc + 1, sizeof(int32_t));
+    L->amem = (int32_t *)malloc(sizeof(int32_t) * ((size_t)L->n + 1));
+    for (int32_t i = 0; i < L->n; ++i) L->aptr[L->agg[i] + 1]++;
+    for (int32_t I = 0; I < L->nc; ++I) L->aptr[I + 1] += L->aptr[I];
+    int32_t *fill = (int32_t *)calloc((size_t)L->nc + 1, sizeof(int32_t));
+    for (int32_t i = 0; i < L->n; ++i) L->amem[L->aptr[L->agg[i]] + fill[L->agg[i]]++] = i;
+    free(fill);
+  }
+#else
+  (void)h;
+#endif
+}
+
+/* dense factor of the coarsest level: Cholesky (symmetric) or LU with partial
+ * pivoting; 0, or -6 (too large) / -7 (not positive definite / singular) */
+static int32_t factor_coarsest(or_hier *h) {
+  or_level *Lc = &h->lev[h->L - 1];
+  if (Lc->n > OR_MAX_DENSE) return -6;
+  h->chol = dalloc((size_t)Lc->n * (size_t)Lc->n);
+  for (int32_t i = 0; i < Lc->n; ++i)
+    for (int32_t pp = Lc->rp[i]; pp < Lc->rp[i + 1]; ++pp)
+      h->chol[(size_t)i * Lc->n + Lc->ci[pp]] = Lc->val[pp];
+  if (h->p.symmetric ? or_cholesky(Lc->n, h->chol)
+                     : or_lu(Lc->n, h->chol, h->piv = (int32_t *)malloc(sizeof(int32_t) * (size_t)(Lc->n + 1))))
+    return -7;
   return 0;
 }
 
@@ -760,23 +844,90 @@ or_hier *or_setup(int32_t n, const int32_t *rp, const int32_t *ci, const double 
       }
     }
   }
-  or_level *Lc = &h->lev[h->L - 1];
-  if (Lc->n > OR_MAX_DENSE) {
-    *err = -6;
-    or_free(h);
-    return NULL;
-  }
-  h->chol = dalloc((size_t)Lc->n * (size_t)Lc->n);
-  for (int32_t i = 0; i < Lc->n; ++i)
-    for (int32_t pp = Lc->rp[i]; pp < Lc->rp[i + 1]; ++pp)
-      h->chol[(size_t)i * Lc->n + Lc->ci[pp]] = Lc->val[pp];
-  if (p->symmetric ? or_cholesky(Lc->n, h->chol)
-                   : or_lu(Lc->n, h->chol, h->piv = (int32_t *)malloc(sizeof(int32_t) * (size_t)(Lc->n + 1)))) {
-    *err = -7;
+  build_members(h);
+  *err = factor_coarsest(h);
+  if (*err) {
     or_free(h);
     return NULL;
   }
   return h;
+}
+
+/* The rows [r0, r1) of level 0 and everything below them, as a hierarchy of
+ * their own.  When independent systems are set up together as one
+ * block-diagonal matrix, no strong connection joins two blocks, so no
+ * aggregate and no Galerkin entry crosses them and each system keeps a
+ * contiguous range of rows on every level; this view is the hierarchy that
+ * system is solved on.  Values are copied, nothing is recomputed except the
+ * dense factor of the coarsest block (as in or_setup). */
+or_hier *or_subsystem(const or_hier *h, int32_t r0, int32_t r1, int32_t *err) {
+  *err = -2;
+  if (r0 < 0 || r1 > h->lev[0].n || r0 >= r1) return NULL;
+  or_hier *s = (or_hier *)calloc(1, sizeof(or_hier));
+  s->p = h->p;
+  s->L = 0;
+  int32_t a = r0, b = r1;
+  for (int32_t k = 0; k < h->L; ++k) {
+    const or_level *L = &h->lev[k];
+    or_level *S = &s->lev[k];
+    s->L = k + 1;
+    const int32_t n = b - a;
+    const int64_t p0 = L->rp[a], p1 = L->rp[b];
+    S->n = n;
+    S->nnz = p1 - p0;
+    S->mis_rounds = L->mis_rounds;
+    S->omega = L->omega;
+    S->rp = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    S->ci = (int32_t *)malloc(sizeof(int32_t) * ((size_t)S->nnz + 1));
+    S->val = dalloc((size_t)S->nnz);
+    S->B = dalloc((size_t)n);
+    level_alloc_work(S);
+    for (int32_t i = 0; i <= n; ++i) S->rp[i] = (int32_t)(L->rp[a + i] - p0);
+    for (int64_t q = p0; q < p1; ++q) {
+      if (L->ci[q] < a || L->ci[q] >= b) goto fail; /* the block couples to other rows */
+      S->ci[q - p0] = L->ci[q] - a;
+      S->val[q - p0] = L->val[q];
+    }
+    for (int32_t i = 0; i < n; ++i) {
+      S->B[i] = L->B[a + i];
+      S->dinv[i] = L->dinv[a + i];
+      S->wd[i] = L->wd[a + i];
+    }
+    if (L->poly) {
+      S->poly = dalloc((size_t)n * 3);
+      memcpy(S->poly, L->poly + (size_t)a * 3, sizeof(double) * (size_t)n * 3);
+    }
+    if (k == h->L - 1) break;
+    /* the block's aggregates: a contiguous range of coarse rows that no row
+     * outside the block joins */
+    int32_t lo = INT32_MAX, hi = -1;
+    for (int32_t i = a; i < b; ++i) {
+      if (L->agg[i] < lo) lo = L->agg[i];
+      if (L->agg[i] > hi) hi = L->agg[i];
+    }
+    for (int32_t i = 0; i < L->n; ++i)
+      if ((i < a || i >= b) && L->agg[i] >= lo && L->agg[i] <= hi) goto fail;
+    S->nc = hi - lo + 1;
+    S->agg = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    S->P = dalloc((size_t)n);
+    for (int32_t i = 0; i < n; ++i) {
+      S->agg[i] = L->agg[a + i] - lo;
+      S->P[i] = L->P[a + i];
+    }
+    a = lo;
+    b = hi + 1;
+  }
+  build_members(s);
+  *err = factor_coarsest(s);
+  if (*err) {
+    or_free(s);
+    return NULL;
+  }
+  return s;
+fail:
+  or_free(s);
+  *err = -2;
+  return NULL;
 }
 
 int32_t or_nlevels(const or_hier *h) { return h->L; }
@@ -810,6 +961,7 @@ int32_t or_set_poly(or_hier *h, int32_t k, const double *coef) {
 }
 
 static void spmv(const or_level *L, const double *x, double *y) {
+  OR_PAR
   for (int32_t i = 0; i < L->n; ++i) {
     double acc = 0.0;
     for (int32_t p = L->rp[i]; p < L->rp[i + 1]; ++p) acc += L->val[p] * x[L->ci[p]];
@@ -818,6 +970,23 @@ static void spmv(const or_level *L, const double *x, double *y) {
 }
 
 static double dot(int32_t n, const double *a, const double *b) {
+#ifdef _OPENMP
+  const int32_t nch = (n + OR_DOT_CHUNK - 1) / OR_DOT_CHUNK;
+  if (nch > 1) {
+    double *part = (double *)malloc(sizeof(double) * (size_t)nch);
+    OR_PAR
+    for (int32_t c = 0; c < nch; ++c) {
+      double t = 0.0;
+      const int32_t e = c * OR_DOT_CHUNK + OR_DOT_CHUNK < n ? c * OR_DOT_CHUNK + OR_DOT_CHUNK : n;
+      for (int32_t i = c * OR_DOT_CHUNK; i < e; ++i) t += a[i] * b[i];
+      part[c] = t;
+    }
+    double s = 0.0;
+    for (int32_t c = 0; c < nch; ++c) s += part[c];
+    free(part);
+    return s;
+  }
+#endif
   double s = 0.0;
   for (int32_t i = 0; i < n; ++i) s += a[i] * b[i];
   return s;
@@ -830,13 +999,17 @@ static void smooth_pre(or_hier *h, int32_t k, const double *b, double *x) {
   or_level *L = &h->lev[k];
   int32_t n = L->n;
   if (!L->poly) {
+    OR_PAR
     for (int32_t i = 0; i < n; ++i) x[i] = L->wd[i] * b[i];
     return;
   }
+  OR_PAR
   for (int32_t i = 0; i < n; ++i) L->u0[i] = L->dinv[i] * b[i];
   spmv(L, L->u0, L->u1);
+  OR_PAR
   for (int32_t i = 0; i < n; ++i) L->u1[i] = L->dinv[i] * L->u1[i];
   spmv(L, L->u1, L->r);
+  OR_PAR
   for (int32_t i = 0; i < n; ++i) {
     double u2 = L->dinv[i] * L->r[i];
     x[i] = L->poly[3 * i] * L->u0[i] + L->poly[3 * i + 1] * L->u1[i] + L->poly[3 * i + 2] * u2;
@@ -851,16 +1024,21 @@ static void smooth_post(or_hier *h, int32_t k, const double *b, double *x) {
   or_level *L = &h->lev[k];
   int32_t n = L->n;
   spmv(L, x, L->r);
+  OR_PAR
   for (int32_t i = 0; i < n; ++i) L->r[i] = b[i] - L->r[i];
   if (!L->poly) {
+    OR_PAR
     for (int32_t i = 0; i < n; ++i) x[i] = x[i] + L->wd[i] * L->r[i];
     return;
   }
+  OR_PAR
   for (int32_t i = 0; i < n; ++i) L->u0[i] = L->dinv[i] * (L->poly[3 * i + 2] * L->r[i]);
   spmv(L, L->u0, L->u1);
+  OR_PAR
   for (int32_t i = 0; i < n; ++i)
     L->u1[i] = L->dinv[i] * L->u1[i] + L->dinv[i] * (L->poly[3 * i + 1] * L->r[i]);
   spmv(L, L->u1, L->u0);
+  OR_PAR
   for (int32_t i = 0; i < n; ++i)
     x[i] = x[i] + (L->dinv[i] * L->u0[i] + L->dinv[i] * (L->poly[3 * i] * L->r[i]));
 }
@@ -888,9 +1066,11 @@ static void krylov2(or_hier *h, int32_t m, const double *r, double *x) {
   double rho1 = gm ? dot(n, L->v, L->v) : dot(n, L->c, L->v);
   double a1 = gm ? dot(n, L->v, r) : dot(n, L->c, r);
   double s1 = a1 / rho1;
+  OR_PAR
   for (int32_t i = 0; i < n; ++i) L->rt[i] = r[i] - s1 * L->v[i];
   double nrt = sqrt(dot(n, L->rt, L->rt)), nr = sqrt(dot(n, r, r));
   if (nrt <= h->p.kcycle_t * nr) {
+    OR_PAR
     for (int32_t i = 0; i < n; ++i) x[i] = s1 * L->c[i];
     return;
   }
@@ -901,6 +1081,7 @@ static void krylov2(or_hier *h, int32_t m, const double *r, double *x) {
   double a2 = gm ? dot(n, L->w, L->rt) : dot(n, L->d, L->rt);
   double rho2 = bet - gam * gam / rho1;
   double cc = s1 - gam * a2 / (rho1 * rho2), cd = a2 / rho2;
+  OR_PAR
   for (int32_t i = 0; i < n; ++i) x[i] = cc * L->c[i] + cd * L->d[i];
 }
 
@@ -917,16 +1098,27 @@ static void cycle(or_hier *h, int32_t k, const double *b, double *x) {
   int32_t n = L->n;
   smooth_pre(h, k, b, x);                                  /* pre-smoothing */
   spmv(L, x, L->r);                                        /* r_k = b_k - A_k x_k */
+  OR_PAR
   for (int32_t i = 0; i < n; ++i) L->r[i] = b[i] - L->r[i];
+#ifdef _OPENMP
+  OR_PAR
+  for (int32_t I = 0; I < C->n; ++I) {                     /* the same sums, per aggregate */
+    double t = 0.0;
+    for (int32_t q = L->aptr[I]; q < L->aptr[I + 1]; ++q) t = t + L->P[L->amem[q]] * L->r[L->amem[q]];
+    C->bc[I] = t;
+  }
+#else
   for (int32_t I = 0; I < C->n; ++I) C->bc[I] = 0.0;       /* r_{k+1} = R_k r_k, summed in */
   for (int32_t i = 0; i < n; ++i)                          /* ascending fine index         */
     C->bc[L->agg[i]] = C->bc[L->agg[i]] + L->P[i] * L->r[i];
+#endif
   if (k + 1 == h->L - 1)
     coarsest_solve(h, C->bc, C->xc);                       /* exact coarse solve */
   else if (k < h->p.kcycle_levels)
     krylov2(h, k + 1, C->bc, C->xc);                       /* K-cycle coarse correction */
   else
     cycle(h, k + 1, C->bc, C->xc);                         /* V-cycle recursion */
+  OR_PAR
   for (int32_t i = 0; i < n; ++i) x[i] = x[i] + L->P[i] * C->xc[L->agg[i]]; /* prolongation */
   smooth_post(h, k, b, x);                                 /* post-smoothing */
 }
@@ -949,12 +1141,14 @@ static int32_t fcg(or_hier *h, const double *b, double *x, double tol, int32_t m
   double nb = sqrt(dot(n, b, b));
   if (nb == 0.0) nb = 1.0;
   spmv(L, x, r);
+  OR_PAR
   for (int32_t i = 0; i < n; ++i) r[i] = b[i] - r[i];
   double rel = sqrt(dot(n, r, r)) / nb;
   if (hist) hist[0] = rel;
   if (rel <= tol) status = 0;
   while (status == 1 && it < max_iter) {
     cycle(h, 0, r, z); /* restart: p = z */
+    OR_PAR
     for (int32_t i = 0; i < n; ++i) p[i] = z[i];
     for (;;) {
       spmv(L, p, q);
@@ -964,6 +1158,7 @@ static int32_t fcg(or_hier *h, const double *b, double *x, double tol, int32_t m
         break;
       }
       double alpha = pr / pq;
+      OR_PAR
       for (int32_t i = 0; i < n; ++i) {
         x[i] = x[i] + alpha * p[i];
         r[i] = r[i] - alpha * q[i];
@@ -973,6 +1168,7 @@ static int32_t fcg(or_hier *h, const double *b, double *x, double tol, int32_t m
       if (hist) hist[it] = rel;
       if (rel <= tol) {
         spmv(L, x, r); /* true residual */
+        OR_PAR
         for (int32_t i = 0; i < n; ++i) r[i] = b[i] - r[i];
         rel = sqrt(dot(n, r, r)) / nb;
         if (rel <= tol) status = 0;
@@ -981,11 +1177,13 @@ static int32_t fcg(or_hier *h, const double *b, double *x, double tol, int32_t m
       if (it >= max_iter) break;
       cycle(h, 0, r, z);
       double beta = -dot(n, z, q) / pq;
+      OR_PAR
       for (int32_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
     }
     if (status == -1) break;
   }
   spmv(L, x, r);
+  OR_PAR
   for (int32_t i = 0; i < n; ++i) r[i] = b[i] - r[i];
   *final_relres = sqrt(dot(n, r, r)) / nb;
   *iters = it;

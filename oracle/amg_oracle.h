@@ -95,12 +95,21 @@ void or_sym_eig(int32_t m, const double *a, double *w);
 int32_t or_cholesky(int32_t n, double *a);
 void or_chol_solve(int32_t n, const double *L, double *b);
 
+/* host threads the solve stage uses: 1 in the parity build, the OpenMP thread
+ * count in the CPU-baseline timing build (compiled with -fopenmp) */
+int32_t or_threads(void);
+
 /* ---- the whole method ---- */
 typedef struct or_hier or_hier;
 
 void or_default_params(or_params *p);
 or_hier *or_setup(int32_t n, const int32_t *rp, const int32_t *ci, const double *val,
                   const or_params *p, int32_t *err);
+/* The rows [r0, r1) of level 0 and their part of every coarser level, as a
+ * hierarchy of its own (the per-system view of independent systems set up
+ * together as one block-diagonal matrix).  NULL with err = -2 if the rows
+ * couple to other rows or an aggregate crosses the range on some level. */
+or_hier *or_subsystem(const or_hier *h, int32_t r0, int32_t r1, int32_t *err);
 int32_t or_nlevels(const or_hier *h);
 void or_level_info(const or_hier *h, int32_t k, int32_t *n, int64_t *nnz, double *omega,
                    int32_t *mis_rounds);

@@ -44,27 +44,32 @@ class ORParams(C.Structure):
     ]
 
 
+LIB_OMP = os.path.join(HERE, "_build", "libamg_oracle_omp.so")
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle shared library (idempotent)."""
+    """Compile the oracle shared library, and its OpenMP timing build for the
+    benchmark's CPU baseline (idempotent)."""
     os.makedirs(os.path.dirname(LIB), exist_ok=True)
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= max(
-            os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "amg_oracle.h"))):
-        return LIB
-    tmp = LIB + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-                           "-shared", "-o", tmp, SRC, "-lm"])
-    os.replace(tmp, LIB)
+    stamp = max(os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "amg_oracle.h")))
+    for out, extra in ((LIB, []), (LIB_OMP, ["-fopenmp"])):
+        if not force and os.path.exists(out) and os.path.getmtime(out) >= stamp:
+            continue
+        tmp = out + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+                               *extra, "-shared", "-o", tmp, SRC, "-lm"])
+        os.replace(tmp, out)
     return LIB
 
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    global _lib
-    if _lib is None:
+def lib(omp: bool = False):
+    """The parity build, or (omp=True) the OpenMP timing build of the CPU baseline."""
+    if omp not in _libs:
         build()
-        L = C.CDLL(LIB)
+        L = C.CDLL(LIB_OMP if omp else LIB)
         L.or_strength.argtypes = [C.c_int32, _i32p, _i32p, _f64p, C.c_double, _u8p]
         L.or_col_count.argtypes = [C.c_int32, _i32p, _i32p, _u8p, _i32p]
         L.or_sym_graph.argtypes = [C.c_int32, _i32p, _i32p, _u8p, _i32p, C.c_void_p, C.c_int64]
@@ -108,6 +113,8 @@ def lib():
                                C.POINTER(C.c_double)]
         L.or_solve.restype = C.c_int32
         L.or_free.argtypes = [C.c_void_p]
+        L.or_subsystem.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_int32)]
+        L.or_subsystem.restype = C.c_void_p
         L.or_krylov2_probe.argtypes = [C.c_void_p, C.c_int32, _f64p, _f64p, _f64p, _f64p]
         L.or_krylov2_probe.restype = C.c_int32
         _f32p = np.ctypeslib.ndpointer(dtype=np.float32, flags="C_CONTIGUOUS")
@@ -117,8 +124,9 @@ def lib():
         L.or_mlp_backward.argtypes = [C.c_int32, _f64p, _f32p, _f64p, _f64p, C.c_void_p]
         L.or_twogrid_loss.argtypes = [C.c_void_p, _f64p, C.c_int32, C.c_uint64, C.c_void_p]
         L.or_twogrid_loss.restype = C.c_double
-        _lib = L
-    return _lib
+        L.or_threads.restype = C.c_int32
+        _libs[omp] = L
+    return _libs[omp]
 
 
 def _csr_args(A):
@@ -299,6 +307,11 @@ class Level:
     B: np.ndarray | None = None
 
 
+def threads(omp: bool = True) -> int:
+    """Host threads the solve stage of the given build uses."""
+    return int(lib(omp).or_threads())
+
+
 def default_params(**kw) -> ORParams:
     p = ORParams()
     lib().or_default_params(C.byref(p))
@@ -310,27 +323,44 @@ def default_params(**kw) -> ORParams:
 class Hierarchy:
     """Aggregation AMG hierarchy (Alg. 1) and its solve phase, on the CPU in FP64."""
 
-    def __init__(self, A, **params):
+    def __init__(self, A, omp: bool = False, **params):
+        """omp=True: the OpenMP timing build (multi-threaded solve stage; the
+        benchmark's CPU baseline), otherwise the single-threaded parity build."""
+        self._L = lib(omp)
         self.params = default_params(**params)
         n, rp, ci, v = _csr_args(A)
         err = C.c_int32(0)
-        self.h = lib().or_setup(n, rp, ci, v, C.byref(self.params), C.byref(err))
+        self.h = self._L.or_setup(n, rp, ci, v, C.byref(self.params), C.byref(err))
         if not self.h:
             raise RuntimeError(f"oracle setup failed: {err.value}")
         self.n = n
 
+    def subsystem(self, r0: int, r1: int) -> "Hierarchy":
+        """The part of this hierarchy that belongs to rows [r0, r1) of level 0
+        (one system of a block-diagonal batch), as a hierarchy of its own."""
+        err = C.c_int32(0)
+        ptr = self._L.or_subsystem(self.h, r0, r1, C.byref(err))
+        if not ptr:
+            raise ValueError(f"rows [{r0}, {r1}) do not form an independent block ({err.value})")
+        sub = Hierarchy.__new__(Hierarchy)
+        sub._L = self._L
+        sub.params = self.params
+        sub.h = ptr
+        sub.n = r1 - r0
+        return sub
+
     def __del__(self):
         if getattr(self, "h", None):
-            lib().or_free(self.h)
+            self._L.or_free(self.h)
             self.h = None
 
     @property
     def nlevels(self) -> int:
-        return lib().or_nlevels(self.h)
+        return self._L.or_nlevels(self.h)
 
     def level(self, k: int) -> Level:
         n, nnz, om, mr = C.c_int32(), C.c_int64(), C.c_double(), C.c_int32()
-        lib().or_level_info(self.h, k, C.byref(n), C.byref(nnz), C.byref(om), C.byref(mr))
+        self._L.or_level_info(self.h, k, C.byref(n), C.byref(nnz), C.byref(om), C.byref(mr))
         n, nnz = n.value, nnz.value
         rp = np.zeros(n + 1, np.int32)
         ci = np.zeros(max(nnz, 1), np.int32)
@@ -339,24 +369,24 @@ class Hierarchy:
         agg = None if last else np.zeros(n, np.int32)
         P = None if last else np.zeros(n)
         B = np.zeros(n)
-        lib().or_level_copy(self.h, k, rp.ctypes.data, ci.ctypes.data, val.ctypes.data,
+        self._L.or_level_copy(self.h, k, rp.ctypes.data, ci.ctypes.data, val.ctypes.data,
                             None if last else agg.ctypes.data, None if last else P.ctypes.data, B.ctypes.data)
         return Level(n, nnz, om.value, mr.value, rp, ci[:nnz], val[:nnz], agg, P, B)
 
     def set_poly(self, k: int, coef: np.ndarray) -> None:
         coef = np.ascontiguousarray(coef, np.float64).reshape(-1)
-        if lib().or_set_poly(self.h, k, coef) != 0:
+        if self._L.or_set_poly(self.h, k, coef) != 0:
             raise ValueError("bad level for polynomial smoother")
 
     def precond(self, b: np.ndarray) -> np.ndarray:
         x = np.zeros(self.n)
-        lib().or_precond(self.h, np.ascontiguousarray(b, np.float64), x)
+        self._L.or_precond(self.h, np.ascontiguousarray(b, np.float64), x)
         return x
 
     def krylov2_probe(self, m: int, r: np.ndarray):
         n = self.level(m).n
         x, c, d = np.zeros(n), np.zeros(n), np.zeros(n)
-        if lib().or_krylov2_probe(self.h, m, np.ascontiguousarray(r, np.float64), x, c, d) != 0:
+        if self._L.or_krylov2_probe(self.h, m, np.ascontiguousarray(r, np.float64), x, c, d) != 0:
             raise ValueError("level has no K-cycle coarse part")
         return x, c, d
 
@@ -364,7 +394,7 @@ class Hierarchy:
         """Two-grid error reduction of the polynomial pre-smoother (levels 0, 1)."""
         coef = np.ascontiguousarray(coef, np.float64).reshape(-1)
         d = np.zeros_like(coef) if grad else None
-        L = lib().or_twogrid_loss(self.h, coef, nvec, seed, None if d is None else d.ctypes.data)
+        L = self._L.or_twogrid_loss(self.h, coef, nvec, seed, None if d is None else d.ctypes.data)
         return L, (None if d is None else d.reshape(-1, 3))
 
     def solve(self, b: np.ndarray, x0: np.ndarray | None = None, tol: float = 1e-8, max_iter: int = 200):
@@ -372,6 +402,6 @@ class Hierarchy:
         hist = np.zeros(max_iter + 2)
         it = C.c_int32()
         fr = C.c_double()
-        st = lib().or_solve(self.h, np.ascontiguousarray(b, np.float64), x, tol, max_iter, C.byref(it), hist,
+        st = self._L.or_solve(self.h, np.ascontiguousarray(b, np.float64), x, tol, max_iter, C.byref(it), hist,
                             C.byref(fr))
         return x, {"status": st, "iters": it.value, "hist": hist[:it.value + 1].copy(), "relres": fr.value}

@@ -1,9 +1,11 @@
 """Batches of independent systems in one block-diagonal hierarchy (GPU).
 
-A batch of one system reproduces the single-system hierarchy bit for bit; in
-a batch of systems of different sizes every system reaches the FP64 tolerance
-on its own, its solution agrees with the FP64 oracle solving that system alone
-to within the conditioning bound, and a converged system stops changing."""
+A batch of one system reproduces the single-system hierarchy bit for bit and,
+in FP64, its iterates; an FP64 batch of systems of different sizes has the
+oracle's hierarchy of the same block-diagonal matrix, and every system follows
+the oracle's solve of that system alone (on its part of the hierarchy) iterate
+for iterate; every system reaches the FP64 tolerance on its own, and a
+converged system stops changing."""
 import numpy as np
 import pytest
 
@@ -44,6 +46,72 @@ def test_batch_hierarchy_index_arrays_valid(env):
         assert amg.lib().amg_validate_hierarchy(h) == 0, amg.amg_last_error()
     finally:
         amg.amg_free(h)
+
+
+def test_batch_fp64_iterates_match_oracle_per_system(env):
+    """An FP64 batch of seven systems of uneven size, one with a zero right-hand
+    side, run for six outer iterations.  The batch hierarchy equals the oracle's
+    hierarchy of the same block-diagonal matrix bit for bit (same depth), and
+    every system's iterate and final FP64 residual equal those of the oracle
+    solving that system alone on its own part of that hierarchy, to 1e-10 and
+    1e-9: the per-system inner products, step lengths and Alg. 5 branches of the
+    batch are those of independent solves."""
+    amg, oracle = env
+    sides = [20, 33, 47, 12, 60, 8, 29]
+    mats = [P.varcoef2d(m, 40 + q) for q, m in enumerate(sides)]
+    rhs = [P.rhs_uniform(A.n, 70 + q) for q, A in enumerate(mats)]
+    rhs[2][:] = 0.0
+    b = np.concatenate(rhs)
+    h = amg.amg_setup_batch(mats, amg.amg_default_params(alpha=0.25, seed=1, precision=0, max_iter=6))
+    try:
+        nl = len(amg.amg_hierarchy_info(h))
+        o = oracle.Hierarchy(P.block_diag(mats), alpha=0.25, seed=1, max_levels=nl)
+        assert o.nlevels == nl
+        for k in range(nl):
+            gl, ol = amg.amg_export_level(h, k), o.level(k)
+            assert np.array_equal(gl["col"], ol.col) and np.array_equal(gl["val"], ol.val), k
+            if k < nl - 1:
+                assert np.array_equal(gl["agg"], ol.agg) and np.array_equal(gl["P"], ol.P), k
+                assert gl["omega"] == pytest.approx(ol.omega, rel=1e-12), k
+        x = np.zeros_like(b)
+        rc, it, rel = amg.amg_solve_batch(h, b, x, 0.0, len(mats), allow=(amg.AMG_OK, amg.AMG_ERR_NOT_CONVERGED))
+        off = np.cumsum([0] + [A.n for A in mats])
+        for q, A in enumerate(mats):
+            xs = x[off[q]:off[q + 1]]
+            if not rhs[q].any():
+                assert it[q] == 0 and not xs.any()
+                continue
+            sub = o.subsystem(int(off[q]), int(off[q + 1]))
+            xo, io = sub.solve(rhs[q], tol=0.0, max_iter=6)
+            assert it[q] == io["iters"] == 6, q
+            assert np.linalg.norm(xs - xo) <= 1e-10 * np.linalg.norm(xo), q
+            assert rel[q] == pytest.approx(io["relres"], rel=1e-9), q
+    finally:
+        amg.amg_free(h)
+
+
+def test_batch_of_one_fp64_iterates_equal_single_system(env):
+    """In FP64 a batch of one follows the single-system solve iterate for
+    iterate: six outer iterations agree to 1e-12 (the batch sums its inner
+    products per system tile, the single system inside the SpMV kernels)."""
+    amg, _ = env
+    A = P.varcoef2d(45, 5)
+    b = P.rhs_uniform(A.n, 5)
+    p = amg.amg_default_params(alpha=0.25, seed=3, precision=0, max_iter=6)
+    hb = amg.amg_setup_batch([A], p)
+    hs = amg.amg_setup(A.rowptr, A.col, A.val, p)
+    try:
+        allow = (amg.AMG_OK, amg.AMG_ERR_NOT_CONVERGED)
+        xb = np.zeros(A.n)
+        rc, it, rel = amg.amg_solve_batch(hb, b, xb, 0.0, 1, allow=allow)
+        xs = np.zeros(A.n)
+        rc2, its, hist = amg.amg_solve(hs, b, xs, 0.0, 6, allow=allow)
+        assert int(it[0]) == its == 6
+        assert np.linalg.norm(xb - xs) <= 1e-12 * np.linalg.norm(xs)
+        assert rel[0] == pytest.approx(amg.amg_last_solve_info(hs)["final_relres"], rel=1e-10)
+    finally:
+        amg.amg_free(hb)
+        amg.amg_free(hs)
 
 
 def test_batch_of_one_equals_single_system(env):

@@ -74,9 +74,17 @@ def test_nonsymmetric_mixed_precision_reaches_fp64_tolerance(env, prec):
     x, info = g.solve(b, tol=1e-8)
     assert info["status"] == amg.AMG_OK
     assert np.linalg.norm(b - A.matvec(x)) <= 1e-8 * np.linalg.norm(b) * (1 + 1e-6)
-    xo, _ = oracle.Hierarchy(A, alpha=0.25, seed=3, symmetric=0, outer=1).solve(b, tol=1e-12, max_iter=500)
-    print(f"precision {prec}: {info['iters']} FGMRES iterations, rel. error vs FP64 oracle "
-          f"{np.linalg.norm(x - xo) / np.linalg.norm(xo):.2e}")
+    xo, io = oracle.Hierarchy(A, alpha=0.25, seed=3, symmetric=0, outer=1).solve(b, tol=1e-12, max_iter=500)
+    err = np.linalg.norm(x - xo) / np.linalg.norm(xo)
+    # ||x - xo|| <= ||A^-1||_2 (||b - A x|| + ||b - A xo||), with
+    # ||A^-1||_2 <= sqrt(||A^-1||_1 ||A^-1||_inf) from the dense inverse
+    Ai = np.linalg.inv(A.to_dense())
+    ninv = np.sqrt(np.abs(Ai).sum(0).max() * np.abs(Ai).sum(1).max())
+    res = np.linalg.norm(b - A.matvec(x)) + np.linalg.norm(b - A.matvec(xo))
+    assert np.linalg.norm(x - xo) <= ninv * res * (1 + 1e-6)
+    assert err <= 1e-6
+    print(f"precision {prec}: {info['iters']} FGMRES iterations, rel. error vs FP64 oracle {err:.2e} "
+          f"(bound {ninv * res / np.linalg.norm(xo):.2e})")
 
 
 def test_nonsymmetric_needs_fgmres_and_a_single_system(env):

@@ -129,6 +129,68 @@ def test_spmv_every_level(gpu, orc, name):
         assert np.abs(yd.cpu().numpy() - ref).max() <= 1e-13 * np.abs(ref).max()
 
 
+def reduced_spmv_bound(A, x, u):
+    """Per-row bound on |y - A x| for the reduced-precision SELL product: values
+    rounded to a unit roundoff u with the rounding errors moved onto a
+    compensated diagonal (so the product differs from A x by
+    sum_j (a_ij - fl(a_ij)) (x_j - x_i)), FP32 accumulation of the row and an
+    FP32 diagonal."""
+    u32 = 2.0 ** -24
+    n = A.n
+    rows = np.repeat(np.arange(n), np.diff(A.rowptr))
+    off = A.col != rows
+    absterm = np.abs(A.val) * np.abs(x[A.col])
+    acc = np.bincount(rows, weights=absterm, minlength=n)
+    comp = np.bincount(rows[off], weights=(np.abs(A.val) * (np.abs(x[A.col]) + np.abs(x[rows])))[off], minlength=n)
+    width = np.diff(A.rowptr).astype(np.float64)
+    return (width + 4) * u32 * acc + u * comp + 1e-300
+
+
+@pytest.mark.parametrize("prec,grid", [(1, 128), (2, 128)])
+def test_reduced_precision_level0_spmv_full_size(gpu, prec, grid):
+    """The benchmarked level-0 product, at full size (128^3, 2,097,152 rows): the
+    FP32 (and BF16) SELL kernel with its split diagonal against the FP64 CSR
+    product of the same FP32 input vector, element by element, within the
+    rounding bound of each row."""
+    import torch
+    A = P.poisson3d(grid)
+    g = gpu.Hierarchy(A, alpha=0.5, seed=1, precision=prec)
+    x = (P.rhs_uniform(A.n, 22)).astype(np.float32)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.zeros_like(xd)
+    gpu.amg_spmv(g.h, 0, xd, yd)
+    torch.cuda.synchronize()
+    x64 = x.astype(np.float64)
+    ref = A.matvec(x64)
+    u = 2.0 ** -24 if prec == 1 else 2.0 ** -8
+    err = np.abs(yd.cpu().numpy().astype(np.float64) - ref)
+    bound = reduced_spmv_bound(A, x64, u)
+    assert (err <= bound).all(), (err / bound).max()
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_reduced_precision_spmv_every_level_varcoef(gpu, orc, prec):
+    """Reduced-precision products of every level of a variable-coefficient
+    hierarchy (values not exact in FP32 / BF16, so the compensated diagonal is
+    exercised), element by element within the rounding bound."""
+    import torch
+    A, alpha, seed = case("varcoef3d_24")
+    g = gpu.Hierarchy(A, alpha=alpha, seed=seed, precision=prec)
+    u = 2.0 ** -24 if prec == 1 else 2.0 ** -8
+    for k in range(g.nlevels):
+        L = g.level(k)
+        Ak = P.CSR(L["n"], L["rowptr"], L["col"], L["val"])
+        x = P.rhs_uniform(Ak.n, 30 + k).astype(np.float32)
+        xd = torch.from_numpy(x).cuda()
+        yd = torch.zeros_like(xd)
+        gpu.amg_spmv(g.h, k, xd, yd)
+        torch.cuda.synchronize()
+        x64 = x.astype(np.float64)
+        err = np.abs(yd.cpu().numpy().astype(np.float64) - Ak.matvec(x64))
+        bound = reduced_spmv_bound(Ak, x64, u)
+        assert (err <= bound).all(), (k, (err / bound).max())
+
+
 @pytest.mark.parametrize("prec", [1, 2])
 def test_mixed_precision_reaches_fp64_tolerance(gpu, orc, prec):
     A, g, o = pair(gpu, orc, "varcoef3d_16", precision=prec)
