@@ -29,7 +29,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "solve ms & DoF/s to 1e-8 rel. residual, mixed/learned vs FP64 AMG; SpMV % HBM"
 M_GRID = 128
-SAMPLE_GRID = 96  # CPU oracle sample: same discretisation on a 96^3 grid
 ALPHA, SEED, TOL = 0.5, 1, 1e-8
 PREC = {"f64": 0, "f32": 1, "bf16": 2}
 PREC_DTYPE = {"f64": "f64", "f32": "f32+f64", "bf16": "bf16+f32+f64"}
@@ -43,6 +42,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="f32", choices=list(PREC))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the other configurations (C3, C4, C5) that the default line reports under configs")
     ap.add_argument("--profile-spmv", action="store_true",
                     help="set up the workload and run two level-0 SpMV launches per precision (ncu target)")
     ap.add_argument("--workload", default="poisson3d_128",
@@ -265,21 +266,28 @@ def max_over_ranks(v: float, ws: int) -> float:
 
 
 # ----------------------------------------------------------------- CPU oracle leg
-def oracle_sample(grid: int = SAMPLE_GRID):
-    """The FP64 CPU oracle, as it stands, on one setup + solve (single thread)."""
+def oracle_sample(grid: int = M_GRID, omp: bool = True):
+    """The FP64 CPU oracle, as it stands, on one setup + solve of the workload:
+    its OpenMP timing build on all host cores (omp=True; the parts of the setup
+    that dominate and the whole solve stage threaded) or its single-threaded
+    parity build."""
     from oracle import oracle
     from paper_1403_1649_gb300 import problems as P
     oracle.build()
     A = P.poisson3d(grid)
     b = P.rhs_uniform(A.n, SEED)
     t0 = time.perf_counter()
-    H = oracle.Hierarchy(A, alpha=ALPHA, seed=SEED)
+    H = oracle.Hierarchy(A, omp=omp, alpha=ALPHA, seed=SEED)
+    t1 = time.perf_counter()
     x, info = H.solve(b, tol=TOL, max_iter=500)
     dt = time.perf_counter() - t0
-    return {"value": A.n / dt, "unit": "DoF/s", "cores": 1, "kind": "oracle",
-            "sample": f"3D 7-point Poisson {grid}^3 (n={A.n}), oracle setup + FP64 FCG solve to {TOL:g} "
-                      f"({info['iters']} iterations, {dt:.2f} s), same discretisation/alpha/seed as the workload",
-            "seconds": dt}
+    cores = oracle.threads(omp)
+    return {"value": A.n / dt, "unit": "DoF/s", "cores": cores, "kind": "oracle",
+            "sample": f"3D 7-point Poisson {grid}^3 (n={A.n}), the workload's own input: oracle setup + FP64 "
+                      f"FCG solve to {TOL:g} ({info['iters']} iterations; setup {t1 - t0:.2f} s, solve "
+                      f"{dt - (t1 - t0):.2f} s) on {cores} host thread(s)"
+                      + (" (OpenMP timing build)" if omp else " (single-threaded parity build)"),
+            "seconds": dt, "setup_s": t1 - t0, "solve_s": dt - (t1 - t0), "iters": info["iters"]}
 
 
 def run_reference(args, ws, rank):
@@ -287,22 +295,24 @@ def run_reference(args, ws, rank):
         return
     for _ in range(args.warmup):
         oracle_sample()
-    vals, secs = [], []
+    secs = []
+    last = None
     for _ in range(args.steps):
-        r = oracle_sample()
-        vals.append(r["value"])
-        secs.append(r["seconds"])
+        last = oracle_sample()
+        secs.append(last["seconds"])
     total = sum(secs)
-    n = SAMPLE_GRID ** 3
+    n = M_GRID ** 3
     value = n * args.steps / total
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"3D 7-point Poisson {SAMPLE_GRID}^3 sample of the 128^3 workload, CPU oracle"},
-        "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} x oracle setup + FP64 FCG solve on 3D 7-point Poisson "
-                                   f"{SAMPLE_GRID}^3, single thread"},
+        "config": {"workload": "3D 7-point Poisson 128^3 (n=2,097,152, nnz=14,581,760), RHS U[-1,1] seed 1; "
+                               "aggregation AMG (alpha 0.5, PMIS(2) seed 1, coarse <= 64) K-cycle preconditioner "
+                               "in FP64 flexible CG to 1e-8: the FP64 CPU oracle (OpenMP timing build)"},
+        "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": last["cores"], "kind": "oracle",
+                         "sample": f"{args.steps} x oracle setup + FP64 FCG solve on the 128^3 workload itself, "
+                                   f"{last['cores']} host threads"},
         "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -648,9 +658,36 @@ def main():
         amg.amg_free(h)
         resetup_ms = {"resetup_ms": float(np.median(rs[1:])), "full_setup_ms": full_ms}
 
+    # the other configurations: C3 (160^3 jump coefficients, BF16 vs FP64), C4 (FEM,
+    # learned smoother vs FP64 Jacobi), C5 (512 batched systems); each variant one
+    # warm-up and one timed setup + solve, outside the timed region
+    configs = None
+    if rank == 0 and not args.no_compare:
+        configs = {}
+        for name in ("fem2d_1024", "varcoef3d_160", "batch512"):
+            t0 = time.perf_counter()
+            v, ms, dt, cfg, res = workload_results(name, 1)
+            configs[name] = {"value": v, "unit": "DoF/s", "ms_per_step": ms, "dtype": dt,
+                             "workload": cfg["workload"], "compare": res,
+                             "wall_s": time.perf_counter() - t0}
+            for k in ("training", "headline"):
+                if k in cfg:
+                    configs[name][k] = cfg[k]
+        # the spec comparison: the mixed-precision learned-smoother solve
+        # against the plain FP64 solve of the same problem, to the same 1e-8
+        c4, c5 = configs["fem2d_1024"]["compare"], configs["batch512"]["compare"]
+        configs["learned_mixed_vs_f64"] = {
+            "fem2d_1024": {"learned_f32_ms": c4["learned_f32"]["ms"], "jacobi_f64_ms": c4["jacobi_f64"]["ms"],
+                           "speedup": c4["jacobi_f64"]["ms"] / c4["learned_f32"]["ms"]},
+            "batch512": {"learned_f32_ms": c5["learned_f32_tuned"]["ms"], "jacobi_f64_ms": c5["jacobi_f64"]["ms"],
+                         "speedup": c5["jacobi_f64"]["ms"] / c5["learned_f32_tuned"]["ms"]}}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = oracle_sample()
+        cpu = oracle_sample(M_GRID, omp=True)
+        one = oracle_sample(M_GRID, omp=False)
+        cpu["single_thread"] = {"value": one["value"], "cores": 1, "setup_s": one["setup_s"],
+                                "solve_s": one["solve_s"], "iters": one["iters"]}
         cpu.pop("seconds", None)
 
     if rank == 0:
@@ -675,6 +712,7 @@ def main():
             "gpu_launches": launches,
             "roofline": roof,
             "cpu_baseline": cpu,
+            "configs": configs,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)
