@@ -1552,6 +1552,82 @@ __device__ void cholesky_inverse_body(int32_t n, double *__restrict__ A, double 
   }
 }
 
+// Inverse of a small SPD matrix held in shared memory by Gauss-Jordan sweeps
+// (no pivoting: the pivots of an SPD matrix are the diagonals of its Schur
+// complements, all positive; a pivot that is not marks the matrix as not
+// positive definite).  Sweep p, with f_i = a_ip / a_pp:
+//   a_ij -= f_i a_pj (i, j != p);  a_pj /= a_pp;  a_ip = -f_i;  a_pp = 1 / a_pp,
+// and after n sweeps a = A^-1.  Every sweep updates the n^2 entries with all
+// threads of the block (one fused multiply-add an entry), so the n sweeps cost
+// 3n barriers instead of the n dependent steps per column of forward and back
+// substitution.  FP64 runs at a few operations per clock per SM on this part,
+// so the multiply-add count, not the barriers, sets the time.
+constexpr int32_t kGjMax = 120;  // n^2 + n doubles of shared memory (113 KB)
+__device__ void gj_inverse_body(int32_t n, const double *__restrict__ A, double *__restrict__ Ainv,
+                                int *__restrict__ err, double *a) {
+  __shared__ int bad;
+  __shared__ double inv_sh;  // 1 / a_pp of the coming sweep, formed once by thread 0
+  double *f = a + (size_t)n * n;
+  const int32_t nn = n * n;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int32_t t = threadIdx.x; t < nn; t += blockDim.x) a[t] = A[t];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    bad = !(a[0] > 0.0);
+    inv_sh = 1.0 / a[0];
+  }
+  __syncthreads();
+  for (int32_t p = 0; p < n && !bad; ++p) {  // bad is uniform: read after a barrier
+    const double inv = inv_sh;
+    for (int32_t i = threadIdx.x; i < n; i += blockDim.x) f[i] = a[i * n + p] * inv;
+    __syncthreads();
+    for (int32_t i = wid; i < n; i += nw) {  // warp per row, lanes over the columns
+      if (i == p) continue;
+      const double fi = f[i];
+      for (int32_t j = lane; j < n; j += 32)
+        if (j != p) a[i * n + j] = fma(-fi, a[p * n + j], a[i * n + j]);
+    }
+    __syncthreads();
+    for (int32_t t = threadIdx.x; t < n; t += blockDim.x)
+      if (t != p) {
+        a[p * n + t] *= inv;
+        a[t * n + p] = -f[t];
+      }
+    if (threadIdx.x == 0) {
+      a[p * n + p] = inv;
+      if (p + 1 < n) {  // the next pivot is final once this sweep's update is done
+        const double piv = a[(p + 1) * n + p + 1];
+        bad = !(piv > 0.0);
+        inv_sh = 1.0 / piv;
+      }
+    }
+    __syncthreads();
+  }
+  if (bad) {
+    if (threadIdx.x == 0) *err = 1;
+    return;
+  }
+  for (int32_t t = threadIdx.x; t < nn; t += blockDim.x) Ainv[t] = a[t];
+}
+
+__global__ void k_gj_inverse(int32_t n, const double *__restrict__ A, double *__restrict__ Ainv,
+                             int *__restrict__ err) {
+  extern __shared__ double gj_a[];
+  pdl_wait_and_trigger();
+  gj_inverse_body(n, A, Ainv, err, gj_a);
+}
+
+// one thread block per system block of a batch
+__global__ void k_gj_inverse_batched(int32_t nsys, const int32_t *__restrict__ off,
+                                     const int64_t *__restrict__ boff, const double *__restrict__ A,
+                                     double *__restrict__ Ainv, int *__restrict__ err) {
+  extern __shared__ double gj_a[];
+  pdl_wait_and_trigger();
+  const int32_t s = blockIdx.x;
+  if (s >= nsys) return;
+  gj_inverse_body(off[s + 1] - off[s], A + boff[s], Ainv + boff[s], err, gj_a);
+}
+
 __global__ void k_gather_i32(int32_t n, const int32_t *__restrict__ idx, const int32_t *__restrict__ src,
                              int32_t *__restrict__ dst) {
   pdl_wait_and_trigger();
@@ -2099,8 +2175,15 @@ void finish_levels(Hierarchy &h, cudaStream_t s, bool fresh) {
     AMG_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
     AMG_COUNT(), klaunch_sm(k_dense_blocks, h.nsys, 128, 0, s, h.nsys, Lc.sys_off, h.binv_off, Lc.rp, Lc.ci, Lc.val,
         dense.p);
-    AMG_COUNT(), klaunch_sm(k_cholesky_inverse_batched, h.nsys, 256, 0, s, h.nsys, Lc.sys_off, h.binv_off, dense.p,
-        h.binv, err.p);
+    if (bmax <= kGjMax) {  // every block in shared memory
+      const size_t sm = sizeof(double) * ((size_t)bmax * bmax + bmax);
+      AMG_CUDA(cudaFuncSetAttribute(k_gj_inverse_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      AMG_COUNT(), klaunch_sm(k_gj_inverse_batched, h.nsys, 256, sm, s, h.nsys, (const int32_t *)Lc.sys_off,
+                              (const int64_t *)h.binv_off, (const double *)dense.p, h.binv, err.p);
+    } else {
+      AMG_COUNT(), klaunch_sm(k_cholesky_inverse_batched, h.nsys, 256, 0, s, h.nsys, Lc.sys_off, h.binv_off, dense.p,
+                              h.binv, err.p);
+    }
     AMG_LAUNCH_CHECK();
     if (read_scalar(err.p, s)) throw Error{AMG_ERR_SETUP, "a system's coarsest matrix is not positive definite"};
     return;
@@ -2116,7 +2199,11 @@ void finish_levels(Hierarchy &h, cudaStream_t s, bool fresh) {
     AMG_CUDA(cudaMemsetAsync(dense.p, 0, sizeof(double) * (size_t)Lc.n * Lc.n, s));
     AMG_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
     AMG_COUNT(), klaunch_sm(k_dense_from_csr, blocks_for(Lc.n), 256, 0, s, Lc.n, Lc.rp, Lc.ci, Lc.val, dense.p);
-    if (p.symmetric) {
+    if (p.symmetric && Lc.n <= kGjMax) {  // in shared memory
+      const size_t sm = sizeof(double) * ((size_t)Lc.n * Lc.n + Lc.n);
+      AMG_CUDA(cudaFuncSetAttribute(k_gj_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      AMG_COUNT(), klaunch_sm(k_gj_inverse, 1, 1024, sm, s, Lc.n, (const double *)dense.p, h.coarse_inv, err.p);
+    } else if (p.symmetric) {
       AMG_COUNT(), klaunch_sm(k_cholesky_inverse, 1, 1024, 0, s, Lc.n, dense.p, h.coarse_inv, err.p);
     } else {
       DevBuf<double> fac(Lc.n);
