@@ -206,6 +206,57 @@ def other_workload(args):
     print(json.dumps(line), flush=True)
 
 
+def solve_bytes(levels, trace, iters: int, prec: str) -> dict:
+    """Algorithmic bytes of one solve: the cycle as run (per-level visits, Alg. 5
+    coarse parts and second inner steps from amg_cycle_trace) times the bytes
+    each kernel of it must move (stored matrix entries, index arrays and the
+    vectors it reads and writes; SELL padding not counted), plus the FP64 outer
+    flexible-CG work of every iteration."""
+    vb = {"f64": 8, "f32": 4, "bf16": 2}[prec]
+    xb = 8 if prec == "f64" else 4
+    L = len(levels)
+    n = [lv["n"] for lv in levels]
+    nnz = [lv["nnz"] for lv in levels]
+
+    def sell(k):
+        if prec == "f64":
+            return 12 * nnz[k] + 8 * (n[k] // 32 + 1)
+        return (nnz[k] - n[k]) * (4 + vb) + 4 * n[k] + 8 * (n[k] // 32 + 1)
+
+    def spmv(k, extra):
+        return sell(k) + (2 + extra) * xb * n[k]
+
+    def cycle(k):
+        nc = n[k + 1]
+        b = spmv(k, 1) + spmv(k, 3)  # residual, post-smoothing
+        b += 4 * n[k] + 2 * xb * n[k] + 4 * (nc + 1) + xb * nc  # restriction
+        if k + 1 < L - 1:
+            b += 2 * xb * nc  # the next level's smoothing start
+        else:
+            b += 8 * nc * nc + xb * nc  # coarsest inverse applied in the same launch
+        b += 4 * n[k] + 3 * xb * n[k] + xb * nc  # prolongation
+        return b
+
+    def kfirst(m):
+        return spmv(m, 1) + 5 * xb * n[m] + 3 * xb * n[m]  # v = A c with dots, r~ (and x0), combination
+
+    def ksecond(m):
+        return spmv(m, 2)
+
+    n0, z0 = n[0], nnz[0]
+    outer = 12 * z0 + 8 * (n0 // 32 + 1) + 24 * n0  # q = A p in FP64 with p^T q, p^T r
+    outer += 24 * n0 + 48 * n0  # p = z + beta p; x, r updates
+    outer += (8 * n0 + 3 * xb * n0) + (xb * n0 + 16 * n0) if prec != "f64" else 8 * n0
+    total = iters * outer
+    per_level = []
+    for k in range(L - 1):
+        b = int(trace["visits"][k]) * cycle(k)
+        b += int(trace["kcalls"][k]) * kfirst(k) + int(trace["second"][k]) * ksecond(k)
+        per_level.append(b)
+        total += b
+    return {"bytes": int(total), "outer_bytes_per_iter": int(outer), "cycle_bytes_per_level": per_level}
+
+
 def C_void_p_array(n):
     import ctypes
     return ctypes.c_void_p * n
@@ -510,7 +561,9 @@ def main():
         xd.zero_()
         rc, it, _ = amg.amg_solve(h, bd, xd, TOL, 500, stream.cuda_stream)
         info = amg.amg_last_solve_info(h)
-        info["levels"] = [lv["n"] for lv in amg.amg_hierarchy_info(h)]
+        lv = amg.amg_hierarchy_info(h)
+        info["levels"] = [l["n"] for l in lv]
+        info["solve_bytes"] = solve_bytes(lv, amg.amg_cycle_trace(h), it, prec)
         amg.amg_free(h)
         stats.setdefault(tag or prec, []).append(info)
         return info
@@ -690,6 +743,15 @@ def main():
                                 "solve_s": one["solve_s"], "iters": one["iters"]}
         cpu.pop("seconds", None)
 
+    solve_eff = None
+    if rank == 0:
+        sb = infos[-1]["solve_bytes"]
+        peaks_ = measured_peaks()
+        pk = peaks_["hbm_gbs"] if peaks_ else 6800.0
+        gbs = sb["bytes"] / (float(np.mean([i["solve_ms"] for i in infos])) / 1e3) / 1e9
+        solve_eff = {"bytes_per_solve": sb["bytes"], "gbs": gbs, "frac": gbs / pk, "peak": pk,
+                     "bytes_by_level": sb["cycle_bytes_per_level"], "outer_bytes_per_iter": sb["outer_bytes_per_iter"],
+                     "how": "cycle as run (amg_cycle_trace) x algorithmic bytes per kernel / mean solve time"}
     if rank == 0:
         mean = lambda key: float(np.mean([i[key] for i in infos]))
         line = {
@@ -706,6 +768,7 @@ def main():
             "values_only_resetup": resetup_ms,
             "final_relres": float(infos[-1]["final_relres"]),
             "solve_dof_per_s": n / (mean("solve_ms") / 1e3),
+            "solve_effective": solve_eff,
             "compare": extra,
             "e2e": {"value": ws * n / (e2e_step / 1e3), "unit": "DoF/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},

@@ -306,6 +306,18 @@ int amg_validate_hierarchy(const amg_hierarchy *h);
 /* Statistics of the last setup/solve on this hierarchy. */
 int amg_last_solve_info(const amg_hierarchy *h, amg_solve_info *info);
 
+/* Cycle trace of the last amg_solve or amg_precond on this hierarchy (Alg. 4
+ * and Alg. 5 as run): per level k (host arrays of capacity cap, any may be
+ * NULL) visits[k] = times the cycle ran on level k (level 0: the preconditioner
+ * applications; the coarsest: its exact solves), kcalls[k] = times the
+ * Krylov-accelerated coarse part of Alg. 5 ran on level k, second[k] = how many
+ * of those took the second inner step (||r~|| > t ||r||).  The counts come from
+ * device counters read once after the solve.  Returns AMG_ERR_UNSUPPORTED for
+ * batches and for the cluster tail (tail = 1, 2), which run their levels
+ * without the counters, and before the first solve. */
+int amg_cycle_trace(const amg_hierarchy *h, int64_t *visits, int64_t *kcalls, int64_t *second, int32_t cap,
+                    int32_t *nlevels);
+
 /* Release every device and host resource of the hierarchy (NULL is a no-op). */
 void amg_free(amg_hierarchy *h);
 

@@ -658,6 +658,9 @@ struct or_hier {
   or_level lev[OR_MAX_LEVELS];
   double *chol; /* dense Cholesky (symmetric) or LU (nonsymmetric) factor of A_{L-1} */
   int32_t *piv; /* LU row interchanges */
+  /* cycle trace of the last solve / preconditioner application: cycle visits
+   * per level, Alg. 5 coarse parts run there, second inner steps taken */
+  int64_t visits[OR_MAX_LEVELS], kcalls[OR_MAX_LEVELS], second[OR_MAX_LEVELS];
 };
 
 void or_default_params(or_params *p) {
@@ -1061,6 +1064,7 @@ static void krylov2(or_hier *h, int32_t m, const double *r, double *x) {
   or_level *L = &h->lev[m];
   int32_t n = L->n;
   int gm = h->p.outer == 1;
+  h->kcalls[m]++;
   cycle(h, m, r, L->c);
   spmv(L, L->c, L->v);
   double rho1 = gm ? dot(n, L->v, L->v) : dot(n, L->c, L->v);
@@ -1074,6 +1078,7 @@ static void krylov2(or_hier *h, int32_t m, const double *r, double *x) {
     for (int32_t i = 0; i < n; ++i) x[i] = s1 * L->c[i];
     return;
   }
+  h->second[m]++;
   cycle(h, m, L->rt, L->d);
   spmv(L, L->d, L->w);
   double gam = gm ? dot(n, L->w, L->v) : dot(n, L->d, L->v);
@@ -1089,6 +1094,7 @@ static void krylov2(or_hier *h, int32_t m, const double *r, double *x) {
  * after prolongation ("r~_k" is not defined at level k): r_k = b_k - A_k x_k,
  * and the post-smoothing step uses b_k as its right-hand side. */
 static void cycle(or_hier *h, int32_t k, const double *b, double *x) {
+  h->visits[k]++;
   if (k == h->L - 1) {
     coarsest_solve(h, b, x);
     return;
@@ -1112,8 +1118,10 @@ static void cycle(or_hier *h, int32_t k, const double *b, double *x) {
   for (int32_t i = 0; i < n; ++i)                          /* ascending fine index         */
     C->bc[L->agg[i]] = C->bc[L->agg[i]] + L->P[i] * L->r[i];
 #endif
-  if (k + 1 == h->L - 1)
+  if (k + 1 == h->L - 1) {
+    h->visits[k + 1]++;
     coarsest_solve(h, C->bc, C->xc);                       /* exact coarse solve */
+  }
   else if (k < h->p.kcycle_levels)
     krylov2(h, k + 1, C->bc, C->xc);                       /* K-cycle coarse correction */
   else
@@ -1123,7 +1131,22 @@ static void cycle(or_hier *h, int32_t k, const double *b, double *x) {
   smooth_post(h, k, b, x);                                 /* post-smoothing */
 }
 
-void or_precond(or_hier *h, const double *b, double *x) { cycle(h, 0, b, x); }
+static void trace_reset(or_hier *h) {
+  for (int32_t k = 0; k < OR_MAX_LEVELS; ++k) h->visits[k] = h->kcalls[k] = h->second[k] = 0;
+}
+
+void or_cycle_trace(const or_hier *h, int64_t *visits, int64_t *kcalls, int64_t *second) {
+  for (int32_t k = 0; k < h->L; ++k) {
+    visits[k] = h->visits[k];
+    kcalls[k] = h->kcalls[k];
+    second[k] = h->second[k];
+  }
+}
+
+void or_precond(or_hier *h, const double *b, double *x) {
+  trace_reset(h);
+  cycle(h, 0, b, x);
+}
 
 /* Flexible CG (Sec. 2.2; the K-cycle is a variable preconditioner).  Reading:
  * one-term A-orthogonalisation, beta = -(z^T q_old)/(p_old^T q_old), which
@@ -1276,6 +1299,7 @@ static int32_t fgmres(or_hier *h, const double *b, double *x, double tol, int32_
 
 int32_t or_solve(or_hier *h, const double *b, double *x, double tol, int32_t max_iter,
                  int32_t *iters, double *hist, double *final_relres) {
+  trace_reset(h);
   if (h->p.outer == 1) return fgmres(h, b, x, tol, max_iter, iters, hist, final_relres);
   return fcg(h, b, x, tol, max_iter, iters, hist, final_relres);
 }

@@ -120,6 +120,10 @@ void or_level_copy(const or_hier *h, int32_t k, int32_t *rp, int32_t *ci, double
 int32_t or_set_poly(or_hier *h, int32_t k, const double *coef);
 /* one application of the preconditioner (Alg. 5 on level 0 from x = 0) */
 void or_precond(or_hier *h, const double *b, double *x);
+/* cycle trace of the last or_solve / or_precond: per level the cycle visits
+ * (the coarsest: its exact solves), the Alg. 5 coarse parts run there, and the
+ * second inner steps they took (each array h's level count long) */
+void or_cycle_trace(const or_hier *h, int64_t *visits, int64_t *kcalls, int64_t *second);
 /* outer Krylov solve; x holds x0 on entry.  hist gets the relative residual
  * norm after every iteration (hist[0] = initial).  Returns 0 if converged,
  * 1 if not, <0 on breakdown.                                                */

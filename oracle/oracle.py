@@ -114,6 +114,7 @@ def lib(omp: bool = False):
         L.or_solve.restype = C.c_int32
         L.or_free.argtypes = [C.c_void_p]
         L.or_subsystem.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_int32)]
+        L.or_cycle_trace.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.or_subsystem.restype = C.c_void_p
         L.or_krylov2_probe.argtypes = [C.c_void_p, C.c_int32, _f64p, _f64p, _f64p, _f64p]
         L.or_krylov2_probe.restype = C.c_int32
@@ -377,6 +378,13 @@ class Hierarchy:
         coef = np.ascontiguousarray(coef, np.float64).reshape(-1)
         if self._L.or_set_poly(self.h, k, coef) != 0:
             raise ValueError("bad level for polynomial smoother")
+
+    def cycle_trace(self) -> dict:
+        """Per level: cycle visits, Alg. 5 coarse parts run, second inner steps (last solve/precond)."""
+        nl = self.nlevels
+        v, k, s2 = (np.zeros(nl, np.int64) for _ in range(3))
+        self._L.or_cycle_trace(self.h, v.ctypes.data, k.ctypes.data, s2.ctypes.data)
+        return {"visits": v, "kcalls": k, "second": s2}
 
     def precond(self, b: np.ndarray) -> np.ndarray:
         x = np.zeros(self.n)

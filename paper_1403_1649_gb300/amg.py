@@ -84,6 +84,7 @@ def lib() -> C.CDLL:
         L.amg_hierarchy_info.argtypes = [vp, vp, i32, C.POINTER(i32)]
         L.amg_export_level.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp]
         L.amg_last_solve_info.argtypes = [vp, C.POINTER(amg_solve_info)]
+        L.amg_cycle_trace.argtypes = [vp, vp, vp, vp, i32, vp]
         L.amg_free.argtypes = [vp]
         L.amg_free.restype = None
         L.amg_last_error.argtypes = []
@@ -263,6 +264,15 @@ def amg_last_solve_info(h) -> dict:
     s = amg_solve_info()
     _check(lib().amg_last_solve_info(h, C.byref(s)))
     return {k: getattr(s, k) for k, _ in amg_solve_info._fields_}
+
+
+def amg_cycle_trace(h) -> dict:
+    """Per level: cycle visits, Alg. 5 coarse parts run, second inner steps taken (last solve)."""
+    nl = C.c_int32()
+    _check(lib().amg_hierarchy_info(h, None, 0, C.byref(nl)))
+    v, k, s2 = (np.zeros(nl.value, np.int64) for _ in range(3))
+    _check(lib().amg_cycle_trace(h, v.ctypes.data, k.ctypes.data, s2.ctypes.data, nl.value, None))
+    return {"visits": v, "kcalls": k, "second": s2}
 
 
 def amg_free(h) -> None:

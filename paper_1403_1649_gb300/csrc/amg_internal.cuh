@@ -134,6 +134,7 @@ constexpr int kNumSlots = 32;       // Krylov scalars per level
 // scalar slots of a level (double) used by the K-cycle coarse step at that level
 enum Slot {
   S_RHO1 = 0, S_A1, S_S1, S_NRT2, S_NR2, S_GAM, S_BET, S_A2, S_CC, S_CD,
+  S_TAKEN,  // second inner steps of Alg. 5 taken at this level in the current solve
   // outer Krylov (level 0 only)
   S_PQ = 12, S_PR, S_ALPHA, S_BETA, S_RR, S_NB2, S_REL, S_ZQ, S_TRUE_RR, S_TOL, S_MAXIT,
 };
@@ -249,6 +250,11 @@ struct Hierarchy {
   int64_t graph_launches = 0;     // kernels in one replay of the captured iteration
   double *host_pinned = nullptr;  // small pinned staging buffer
   bool poly_set[kMaxLevels] = {};
+  // cycle trace of the last solve or preconditioner application: per level the
+  // cycle visits, the Krylov-accelerated coarse parts of Alg. 5 run there, and
+  // how many of those took the second inner step
+  int64_t visits[kMaxLevels] = {}, kcalls[kMaxLevels] = {}, second[kMaxLevels] = {};
+  bool trace_ok = false;
 };
 
 // ---------------------------------------------------------------- helpers

@@ -618,6 +618,23 @@ int amg_validate_hierarchy(const amg_hierarchy *H) {
   });
 }
 
+int amg_cycle_trace(const amg_hierarchy *H, int64_t *visits, int64_t *kcalls, int64_t *second, int32_t cap,
+                    int32_t *nlevels) {
+  if (!H) return AMG_ERR_BAD_INPUT;
+  const amg::Hierarchy &h = H->h;
+  if (nlevels) *nlevels = h.L;
+  if (h.batched || !h.trace_ok) {
+    amg::set_last_error("amg_cycle_trace: no trace (batch, cluster tail, or no solve yet)");
+    return AMG_ERR_UNSUPPORTED;
+  }
+  for (int k = 0; k < h.L && k < cap; ++k) {
+    if (visits) visits[k] = h.visits[k];
+    if (kcalls) kcalls[k] = h.kcalls[k];
+    if (second) second[k] = h.second[k];
+  }
+  return AMG_OK;
+}
+
 int amg_last_solve_info(const amg_hierarchy *H, amg_solve_info *info) {
   if (!H || !info) return AMG_ERR_BAD_INPUT;
   *info = H->h.info;

@@ -387,6 +387,7 @@ __global__ void k_decide(const double *__restrict__ part, int nb, double *__rest
     slots[S_NR2] = nr2;
     const bool accept_first = sqrt(nrt2) <= t * sqrt(nr2);
     *flag = (active && !accept_first) ? 1 : 0;
+    if (active && !accept_first) slots[S_TAKEN] += 1.0;  // cycle trace (one thread)
   }
 }
 
@@ -1554,6 +1555,36 @@ void true_residual(Hierarchy &h, int dst, cudaStream_t s, int64_t &launches) {
   AMG_LAUNCH_CHECK();
 }
 
+// cycle trace: clear the per-level counts of second inner steps before a solve
+void trace_reset(Hierarchy &h, cudaStream_t s) {
+  for (int k = 0; k < h.L; ++k) klaunch(k_set_slot, 1, 32, s, h.lev[k].slots, S_TAKEN, 0.0);
+  AMG_LAUNCH_CHECK();
+  h.trace_ok = false;
+}
+
+// after a solve with `apps` preconditioner applications: the counts of second
+// steps, and from them the visits of every level (Alg. 5 at level m runs the
+// cycle of m once, twice when its second step is taken; Alg. 4 recurses once)
+void trace_collect(Hierarchy &h, int64_t apps, cudaStream_t s) {
+  std::vector<double> pin(h.L, 0.0);
+  for (int k = 0; k < h.L; ++k)
+    AMG_CUDA(cudaMemcpyAsync(&pin[k], h.lev[k].slots + S_TAKEN, sizeof(double), cudaMemcpyDeviceToHost, s));
+  AMG_CUDA(cudaStreamSynchronize(s));
+  for (int k = 0; k < kMaxLevels; ++k) h.visits[k] = h.kcalls[k] = h.second[k] = 0;
+  h.visits[0] = apps;
+  for (int k = 0; k + 1 < h.L; ++k) {
+    const int m = k + 1;
+    if (m < h.L - 1 && k < h.p.kcycle_levels && h.tail_t != m) {
+      h.kcalls[m] = h.visits[k];
+      h.second[m] = (int64_t)pin[m];
+      h.visits[m] = h.visits[k] + h.second[m];
+    } else {
+      h.visits[m] = h.visits[k];
+    }
+  }
+  h.trace_ok = h.tail_t < 0;  // the cluster tail runs its levels without the counters
+}
+
 template <class MV, class VT>
 int run_solve_t(Hierarchy &h, const double *b, double *x, double tol, int32_t *iters, double *res_hist,
                 cudaStream_t s) {
@@ -1564,6 +1595,7 @@ int run_solve_t(Hierarchy &h, const double *b, double *x, double tol, int32_t *i
   int *active = h.it_dev + 1, *restart = h.it_dev + 2;
   copy_in(h.b, b, n, s);
   copy_in(h.x, x, n, s);
+  trace_reset(h, s);
   // ||b||^2 and the initial residual
   klaunch(k_dot64, ew_grid(n), kThreads, s, n, h.b, h.b, L0.partials + 6 * kRedBlocks, nullptr);
   klaunch(k_store_sum, 1, kThreads, s, L0.partials + 6 * kRedBlocks, ew_grid(n), L0.slots + S_NB2);
@@ -1670,6 +1702,7 @@ int run_solve_t(Hierarchy &h, const double *b, double *x, double tol, int32_t *i
   copy_out(x, h.x, n, s);
   AMG_CUDA(cudaStreamSynchronize(s));
   h.info.final_relres = zero_b ? std::sqrt(h.host_pinned[S_TRUE_RR]) : std::sqrt(h.host_pinned[S_TRUE_RR] / nb2);
+  trace_collect(h, it, s);
   h.info.iters = it;
   h.info.status = status;
   h.info.kernel_launches = launches;
@@ -1693,6 +1726,7 @@ int run_fgmres_t(Hierarchy &h, const double *b, double *x, double tol, int32_t *
   int *active = h.it_dev + 1;
   copy_in(h.b, b, n, s);
   copy_in(h.x, x, n, s);
+  trace_reset(h, s);
   const int ng = ew_grid(n);
   klaunch(k_dot64, ng, kThreads, s, n, h.b, h.b, L0.partials + 6 * kRedBlocks, nullptr);
   klaunch(k_store_sum, 1, kThreads, s, L0.partials + 6 * kRedBlocks, ng, L0.slots + S_NB2);
@@ -1782,6 +1816,7 @@ int run_fgmres_t(Hierarchy &h, const double *b, double *x, double tol, int32_t *
   copy_out(x, h.x, n, s);
   AMG_CUDA(cudaStreamSynchronize(s));
   h.info.final_relres = std::sqrt(h.host_pinned[S_RR] / nb2);
+  trace_collect(h, it, s);
   h.info.iters = it;
   h.info.status = status;
   h.info.kernel_launches = launches;
@@ -2033,10 +2068,12 @@ template <class MV, class VT>
 void run_precond_t(Hierarchy &h, const double *b, double *x, cudaStream_t s) {
   Engine<MV, VT> eng(h, s);
   const int32_t n = h.lev[0].n;
+  if (!h.batched) trace_reset(h, s);
   copy_in(h.r, b, n, s);
   eng.precond(h.r, h.z, nullptr, false);
   copy_out(x, h.z, n, s);
   AMG_CUDA(cudaStreamSynchronize(s));
+  if (!h.batched) trace_collect(h, 1, s);
   h.info.kernel_launches = eng.launches;
 }
 

@@ -113,6 +113,27 @@ def test_solve_converges_like_oracle(gpu, orc, name):
         assert np.linalg.norm(xg - xo) <= 1e-10 * np.linalg.norm(xo)
 
 
+@pytest.mark.parametrize("name", ["poisson3d_20", "varcoef3d_24", "fem2d_48", "aniso2d_40"])
+@pytest.mark.parametrize("outer", [0, 1])
+def test_cycle_trace_matches_oracle(gpu, orc, name, outer):
+    """The cycle as run: per level the visits, the Alg. 5 coarse parts and the
+    second inner steps they took (||r~|| > t ||r||), counted on the device during
+    an FP64 solve to 1e-8, equal the oracle's counts for the same solve."""
+    A, g, o = pair(gpu, orc, name, outer=outer, restart=30)
+    b = P.rhs_uniform(A.n, 27)
+    xg, ig = g.solve(b, tol=1e-8)
+    xo, io = o.solve(b, tol=1e-8, max_iter=500)
+    assert ig["iters"] == io["iters"]
+    tg, to = gpu.amg_cycle_trace(g.h), o.cycle_trace()
+    for key in ("visits", "kcalls", "second"):
+        assert np.array_equal(tg[key], to[key]), (key, tg[key], to[key])
+    assert tg["visits"][0] == ig["iters"] and tg["second"].sum() > 0
+    g.precond(b)
+    o.precond(b)
+    tg, to = gpu.amg_cycle_trace(g.h), o.cycle_trace()
+    assert all(np.array_equal(tg[k], to[k]) for k in tg) and tg["visits"][0] == 1
+
+
 @pytest.mark.parametrize("name", ["poisson2d_37", "varcoef3d_24", "fem2d_48"])
 def test_spmv_every_level(gpu, orc, name):
     import torch

@@ -826,3 +826,34 @@ def test_openmp_timing_build_matches_parity_build(oracle_mod):
     if i_s["iters"] == i_o["iters"]:
         assert np.linalg.norm(xs - xo) <= 1e-10 * np.linalg.norm(xs)
     assert oracle_mod.threads(omp=False) == 1 and oracle_mod.threads(omp=True) >= 1
+
+
+def test_cycle_trace_follows_alg4_alg5(oracle_mod):
+    """The oracle's cycle trace obeys the control flow of Alg. 4 / Alg. 5: the
+    preconditioner applications equal the flexible-CG iterations; Alg. 5 at level
+    m runs once per visit of level m-1 (for m-1 among the Krylov-accelerated
+    levels) and visits level m once more for every second inner step taken;
+    Alg. 4 visits the next level once; the coarsest is solved once per visit of
+    the level above.  With t = 0 the second step always runs; with a threshold
+    beyond any norm ratio the first step is always accepted."""
+    A = P.poisson3d(20)
+    b = P.rhs_uniform(A.n, 1)
+    for kw in ({}, {"kcycle_levels": 1}, {"kcycle_levels": 0}, {"kcycle_t": 0.0}, {"kcycle_t": 1e300}):
+        o = oracle_mod.Hierarchy(A, alpha=0.5, seed=1, **kw)
+        x, info = o.solve(b, tol=1e-8)
+        t = o.cycle_trace()
+        L = o.nlevels
+        kl = kw.get("kcycle_levels", 2)
+        assert L >= 4 and t["visits"][0] == info["iters"]
+        for m in range(1, L):
+            k = m - 1
+            if m < L - 1 and k < kl:
+                assert t["kcalls"][m] == t["visits"][k]
+                assert 0 <= t["second"][m] <= t["kcalls"][m]
+                assert t["visits"][m] == t["visits"][k] + t["second"][m]
+            else:
+                assert t["kcalls"][m] == 0 and t["visits"][m] == t["visits"][k]
+        if kw.get("kcycle_t") == 0.0:
+            assert all(t["second"][m] == t["kcalls"][m] for m in range(1, L - 1))
+        if kw.get("kcycle_t") == 1e300:
+            assert t["second"].sum() == 0
