@@ -3,11 +3,11 @@
 // training minimises.  The paper lists polynomial smoothers as future work
 // (Sec. 5); the network and its training are this library's own.
 //
-// MLP: 16 -> 64 -> 64 -> 3, tanh, FP16 weights converted to FP32 in shared
-// memory, FP32 arithmetic.  Coefficients: c_q = omega_k (delta_q0 + o_q).
-// The total work is ~5.3 kFLOP per row (about 0.1 ms for a million rows), so
-// the layers run on the CUDA cores; the weight gradients are deterministic
-// fixed-order sums over rows.
+// MLP: 16 -> 64 -> 64 -> 3, tanh, FP16 weights.  Inference runs the three
+// layers on the tensor cores (mma.sync, FP16 operands with FP32 accumulation,
+// activations as two FP16 parts); training keeps FP32 master weights on the
+// CUDA cores.  Coefficients: c_q = omega_k (delta_q0 + o_q).  The weight
+// gradients are deterministic fixed-order sums over rows.
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -111,6 +111,124 @@ __global__ void __launch_bounds__(256) k_mlp_forward(int32_t n, const WT *__rest
     out[(size_t)i * NO] = o0;
     out[(size_t)i * NO + 1] = o1;
     out[(size_t)i * NO + 2] = o2;
+  }
+}
+
+// ------------------------------------------------------------------ MLP forward on tensor cores
+// Inference with the FP16 weights as given: each warp takes 16 rows and runs the
+// three layers as mma.sync m16n8k16 products (FP16 operands, FP32
+// accumulation), the weights as B operands from shared memory.  An activation
+// (FP32) enters as the sum of two FP16 parts, hi = fp16(h) and lo = fp16(h - hi),
+// each multiplied by the exact FP16 weight and accumulated in FP32: about 22
+// significant bits per product, so the outputs agree with the FP32 CUDA-core
+// evaluation to FP32 rounding, where FP16 activations alone would lose three
+// decimal digits.  The accumulator fragment of one layer (rows g, g+8; columns
+// 2t, 2t+1 of each 8-column tile) is the A-operand fragment of the next, so the
+// hidden activations never leave registers.
+__device__ __forceinline__ uint32_t pack_h2(__half x, __half y) {
+  __half2 v = __halves2half2(x, y);
+  return *reinterpret_cast<uint32_t *>(&v);
+}
+__device__ __forceinline__ void split_h2(float x, float y, uint32_t &hi, uint32_t &lo) {
+  const __half xh = __float2half_rn(x), yh = __float2half_rn(y);
+  hi = pack_h2(xh, yh);
+  lo = pack_h2(__float2half_rn(x - __half2float(xh)), __float2half_rn(y - __half2float(yh)));
+}
+// c += A (16x16, row) * B (16x8, col)
+__device__ __forceinline__ void mma_16816(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+constexpr int kTcWarps = 4;
+__global__ void __launch_bounds__(32 * kTcWarps) k_mlp_forward_tc(int32_t n, const __half *__restrict__ wg,
+                                                                  const float *__restrict__ feat,
+                                                                  float *__restrict__ out) {
+  __shared__ __align__(16) __half w[NP + 1];
+  __shared__ float bias[2 * NH + NO];
+  for (int k = threadIdx.x; k < NP; k += blockDim.x) w[k] = wg[k];
+  for (int k = threadIdx.x; k < NH; k += blockDim.x) {
+    bias[k] = __half2float(wg[B1O + k]);
+    bias[NH + k] = __half2float(wg[B2O + k]);
+  }
+  if (threadIdx.x < NO) bias[2 * NH + threadIdx.x] = __half2float(wg[B3O + threadIdx.x]);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  auto wpair = [&](int idx) { return *reinterpret_cast<const uint32_t *>(&w[idx]); };
+  for (int32_t tile = blockIdx.x * kTcWarps + (threadIdx.x >> 5); (int64_t)tile * 16 < n;
+       tile += gridDim.x * kTcWarps) {
+    const int32_t ra = tile * 16 + g, rb = ra + 8;
+    // layer 1: A = features (16 x 16)
+    uint32_t ah[4], al[4];
+    {
+      auto fv = [&](int32_t r, int k) { return r < n ? feat[(size_t)r * NF + k] : 0.0f; };
+      split_h2(fv(ra, 2 * t), fv(ra, 2 * t + 1), ah[0], al[0]);
+      split_h2(fv(rb, 2 * t), fv(rb, 2 * t + 1), ah[1], al[1]);
+      split_h2(fv(ra, 2 * t + 8), fv(ra, 2 * t + 9), ah[2], al[2]);
+      split_h2(fv(rb, 2 * t + 8), fv(rb, 2 * t + 9), ah[3], al[3]);
+    }
+    float c[8][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      const int col = 8 * nt + 2 * t;
+      c[nt][0] = c[nt][2] = bias[col];
+      c[nt][1] = c[nt][3] = bias[col + 1];
+      const int wrow = W1O + (8 * nt + g) * NF + 2 * t;
+      const uint32_t b0 = wpair(wrow), b1 = wpair(wrow + 8);
+      mma_16816(c[nt], ah, b0, b1);
+      mma_16816(c[nt], al, b0, b1);
+    }
+    // tanh, then the accumulators as the A operand of the next layer (4 k-tiles)
+    uint32_t hh[4][4], hl[4][4];
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+      split_h2(tanhf(c[2 * kk][0]), tanhf(c[2 * kk][1]), hh[kk][0], hl[kk][0]);
+      split_h2(tanhf(c[2 * kk][2]), tanhf(c[2 * kk][3]), hh[kk][1], hl[kk][1]);
+      split_h2(tanhf(c[2 * kk + 1][0]), tanhf(c[2 * kk + 1][1]), hh[kk][2], hl[kk][2]);
+      split_h2(tanhf(c[2 * kk + 1][2]), tanhf(c[2 * kk + 1][3]), hh[kk][3], hl[kk][3]);
+    }
+    // layer 2: 64 x 64
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      const int col = 8 * nt + 2 * t;
+      c[nt][0] = c[nt][2] = bias[NH + col];
+      c[nt][1] = c[nt][3] = bias[NH + col + 1];
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const int wrow = W2O + (8 * nt + g) * NH + 16 * kk + 2 * t;
+        const uint32_t b0 = wpair(wrow), b1 = wpair(wrow + 8);
+        mma_16816(c[nt], hh[kk], b0, b1);
+        mma_16816(c[nt], hl[kk], b0, b1);
+      }
+    }
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+      split_h2(tanhf(c[2 * kk][0]), tanhf(c[2 * kk][1]), hh[kk][0], hl[kk][0]);
+      split_h2(tanhf(c[2 * kk][2]), tanhf(c[2 * kk][3]), hh[kk][1], hl[kk][1]);
+      split_h2(tanhf(c[2 * kk + 1][0]), tanhf(c[2 * kk + 1][1]), hh[kk][2], hl[kk][2]);
+      split_h2(tanhf(c[2 * kk + 1][2]), tanhf(c[2 * kk + 1][3]), hh[kk][3], hl[kk][3]);
+    }
+    // layer 3: 3 outputs in the first 8-column tile (columns 3..7 zero)
+    float o[4];
+    o[0] = o[2] = 2 * t < NO ? bias[2 * NH + 2 * t] : 0.0f;
+    o[1] = o[3] = 2 * t + 1 < NO ? bias[2 * NH + 2 * t + 1] : 0.0f;
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+      const int wrow = W3O + g * NH + 16 * kk + 2 * t;
+      const uint32_t b0 = g < NO ? wpair(wrow) : 0u, b1 = g < NO ? wpair(wrow + 8) : 0u;
+      mma_16816(o, hh[kk], b0, b1);
+      mma_16816(o, hl[kk], b0, b1);
+    }
+    if (ra < n) {
+      if (2 * t < NO) out[(size_t)ra * NO + 2 * t] = o[0];
+      if (2 * t + 1 < NO) out[(size_t)ra * NO + 2 * t + 1] = o[1];
+    }
+    if (rb < n) {
+      if (2 * t < NO) out[(size_t)rb * NO + 2 * t] = o[2];
+      if (2 * t + 1 < NO) out[(size_t)rb * NO + 2 * t + 1] = o[3];
+    }
   }
 }
 
@@ -367,8 +485,10 @@ void features(const Hierarchy &h, int level, float *feat_dev, cudaStream_t s) {
 }
 
 void mlp_forward_half(int32_t n, const uint16_t *w16_dev, const float *feat, float *out, cudaStream_t s) {
-  AMG_COUNT(), k_mlp_forward<__half><<<g256(n), 256, 0, s>>>(n, reinterpret_cast<const __half *>(w16_dev), feat, out,
-                                                             nullptr, nullptr);
+  if (n <= 0) return;
+  const int blocks = grid_for(((int64_t)n + 15) / 16, kTcWarps, 152 * 16);
+  AMG_COUNT(), k_mlp_forward_tc<<<blocks, 32 * kTcWarps, 0, s>>>(n, reinterpret_cast<const __half *>(w16_dev), feat,
+                                                                 out);
   AMG_LAUNCH_CHECK();
 }
 

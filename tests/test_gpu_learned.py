@@ -91,6 +91,29 @@ def test_mlp_forward_and_backward(env):
     assert (np.abs(g - gref) <= 2e-5 * S + 1e-12).all(), (np.abs(g - gref) / (S + 1e-30)).max()
 
 
+@pytest.mark.parametrize("rows,scale", [(1, 0.3), (17, 0.3), (1000, 0.3), (4099, 0.6)])
+def test_mlp_forward_tensor_cores_ragged(env, rows, scale):
+    """Inference runs on the tensor cores 16 rows per warp (FP16 weights, each FP32
+    activation as two FP16 parts, FP32 accumulation): row counts that are not a
+    multiple of 16, and weights large enough to saturate tanh, against the
+    oracle's FP32 evaluation element by element."""
+    torch, amg, oracle = env
+    rng = np.random.default_rng(rows)
+    w16 = (rng.normal(size=oracle.NPARAM) * scale).astype(np.float16)
+    feat = oracle.features(P.fem2d(70, 6))[:rows].copy()
+    dev = torch.device("cuda")
+    fd = torch.from_numpy(feat).to(dev)
+    out = torch.full((rows * 3,), np.nan, dtype=torch.float32, device=dev)
+    w16d = torch.from_numpy(w16.view(np.uint16).astype(np.int16)).to(dev)
+    assert amg.lib().amg_mlp_forward(rows, C.c_void_p(w16d.data_ptr()), C.c_void_p(fd.data_ptr()),
+                                     C.c_void_p(out.data_ptr()), None) == 0
+    torch.cuda.synchronize()
+    ref = oracle.mlp_forward(w16.view(np.uint16), feat)
+    got = out.cpu().numpy().reshape(rows, 3)
+    assert np.isfinite(got).all()
+    assert np.allclose(got, ref, rtol=1e-5, atol=1e-5), np.abs(got - ref).max()
+
+
 def test_twogrid_loss_and_gradient(env):
     torch, amg, oracle = env
     A = P.fem2d(24, 5)
