@@ -1028,12 +1028,87 @@ __global__ void __launch_bounds__(256) k_arn_start(int32_t n, uint64_t seed, int
   }
 }
 
+// The inner products of step j after w = M q_j.  Arnoldi (nonsymmetric A):
+// h_lj = q_l . w for l <= j, and ||w||^2.  Lanczos (symmetric A, where the
+// Arnoldi matrix is tridiagonal and the recurrence needs only q_j and q_{j-1}):
+// alpha_j = q_j . w and ||w||^2.
+template <bool LZ>
+__device__ __forceinline__ void arn_accumulate(double (&v)[kArnSlots], int j, int32_t n, int32_t i,
+                                               const double *__restrict__ Q, double qi, double wi) {
+  if (LZ) {
+    v[0] += qi * wi;
+    v[1] += wi * wi;
+    return;
+  }
+#pragma unroll
+  for (int l = 0; l < kArnSlots; ++l) {  // static indices: the sums stay in registers
+    if (l < j) v[l] += Q[(size_t)l * n + i] * wi;
+    else if (l == j) v[l] += qi * wi;
+    else if (l == j + 1) v[l] += wi * wi;
+  }
+}
+
+// Block partials and, in the last block, the column j of H: Arnoldi h_lj
+// (l <= j) and h_{j,j-1} = ||W|| = h; Lanczos alpha_j on the diagonal and
+// beta_{j-1} = h on both sides of it.  wn_j = ||M q_j|| for the breakdown test.
+template <bool LZ>
+__device__ __forceinline__ void arn_finish(const double (&v)[kArnSlots], int j, double h, double *part, double *H,
+                                           double *wn, unsigned *ticket) {
+  const int ns = LZ ? 2 : j + 2;
+  arn_block_partials(v, ns, part);
+  if (arn_last_block(ticket)) {
+    __shared__ double tot[kArnSlots];
+    arn_totals(part, ns, tot);
+    if (LZ) {
+      if (threadIdx.x == 0) {
+        H[j * 8 + j] = tot[0];
+        wn[j] = sqrt(tot[1]);
+        if (j > 0) H[j * 8 + (j - 1)] = H[(j - 1) * 8 + j] = h;
+      }
+    } else {
+      if ((int)threadIdx.x <= j) H[threadIdx.x * 8 + j] = tot[threadIdx.x];
+      if ((int)threadIdx.x == j + 1) wn[j] = sqrt(tot[j + 1]);
+      if (threadIdx.x == 0 && j > 0) H[j * 8 + (j - 1)] = h;
+    }
+    if (threadIdx.x == 0) *ticket = 0;
+  }
+}
+
+// Lanczos step j, part 2: w -= alpha_j q_j + beta_{j-1} q_{j-1}; W = w,
+// U = dh .* w, nrm2 = ||w||^2 (beta_j^2)
+__global__ void __launch_bounds__(256) k_lz_update(int32_t n, int j, const double *__restrict__ Q,
+                                                   const double *__restrict__ w, double *__restrict__ W,
+                                                   double *__restrict__ U, const double *__restrict__ dh,
+                                                   double *part, const double *__restrict__ H, double *nrm2,
+                                                   unsigned *ticket) {
+  pdl_wait_and_trigger();
+  const double a = H[j * 8 + j], b = j > 0 ? H[j * 8 + (j - 1)] : 0.0;
+  const double *qj = Q + (size_t)j * n, *qp = j > 0 ? Q + (size_t)(j - 1) * n : nullptr;
+  double v[kArnSlots] = {0.0};
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double wi = w[i] - a * qj[i];
+    if (qp) wi -= b * qp[i];
+    W[i] = wi;
+    U[i] = dh[i] * wi;
+    v[0] += wi * wi;
+  }
+  arn_block_partials(v, 1, part);
+  if (arn_last_block(ticket)) {
+    __shared__ double tot[kArnSlots];
+    arn_totals(part, 1, tot);
+    if (threadIdx.x == 0) {
+      *nrm2 = tot[0];
+      *ticket = 0;
+    }
+  }
+}
+
 // step j, part 1: q_j = W / ||W||; w = M q_j = dh .* (A U) / ||W||;
 // h_lj = q_l . w (l <= j), wn_j = ||w||; h_{j,j-1} = ||W|| (j > 0).
 // T consecutive lanes share a row: lane t sums the row's entries t, t + T, ...
 // and the T partial sums meet in a fixed shuffle tree, so that the entries of a
 // row are read by neighbouring lanes.
-template <int T>
+template <int T, bool LZ>
 __global__ void __launch_bounds__(256) k_arn_spmv(int32_t n, int j, const int32_t *__restrict__ rp,
                                                   const int32_t *__restrict__ ci, const double *__restrict__ val,
                                                   const double *__restrict__ dh, const double *__restrict__ W,
@@ -1073,30 +1148,16 @@ __global__ void __launch_bounds__(256) k_arn_spmv(int32_t n, int j, const int32_
       const double wi = dh[i] * (sc * acc), qi = sc * W[i];
       qj[i] = qi;
       w[i] = wi;
-#pragma unroll
-      for (int l = 0; l < kArnSlots; ++l) {  // static indices: the sums stay in registers
-        if (l < j) v[l] += Q[(size_t)l * n + i] * wi;
-        else if (l == j) v[l] += qi * wi;
-        else if (l == j + 1) v[l] += wi * wi;
-      }
+      arn_accumulate<LZ>(v, j, n, i, Q, qi, wi);
     }
   }
-  arn_block_partials(v, j + 2, part);
-  if (arn_last_block(ticket)) {
-    __shared__ double tot[kArnSlots];
-    arn_totals(part, j + 2, tot);
-    if ((int)threadIdx.x <= j) H[threadIdx.x * 8 + j] = tot[threadIdx.x];
-    if ((int)threadIdx.x == j + 1) wn[j] = sqrt(tot[j + 1]);
-    if (threadIdx.x == 0) {
-      if (j > 0) H[j * 8 + (j - 1)] = h;
-      *ticket = 0;
-    }
-  }
+  arn_finish<LZ>(v, j, h, part, H, wn, ticket);
 }
 
 // step j, part 1 on a level with an FP64 SELL-32 copy of A (one warp per slice,
 // coalesced loads; the same sums in the same order as the CSR kernel above plus
 // zero terms of the padding)
+template <bool LZ>
 __global__ void __launch_bounds__(256) k_arn_spmv_sell(int32_t n, int32_t nslices, int j,
                                                        const int64_t *__restrict__ sptr, const int32_t *__restrict__ scol,
                                                        const double *__restrict__ sval, const double *__restrict__ dh,
@@ -1133,25 +1194,10 @@ __global__ void __launch_bounds__(256) k_arn_spmv_sell(int32_t n, int32_t nslice
       const double wi = dh[i] * (sc * acc), qi = sc * W[i];
       qj[i] = qi;
       w[i] = wi;
-#pragma unroll
-      for (int l = 0; l < kArnSlots; ++l) {
-        if (l < j) v[l] += Q[(size_t)l * n + i] * wi;
-        else if (l == j) v[l] += qi * wi;
-        else if (l == j + 1) v[l] += wi * wi;
-      }
+      arn_accumulate<LZ>(v, j, n, i, Q, qi, wi);
     }
   }
-  arn_block_partials(v, j + 2, part);
-  if (arn_last_block(ticket)) {
-    __shared__ double tot[kArnSlots];
-    arn_totals(part, j + 2, tot);
-    if ((int)threadIdx.x <= j) H[threadIdx.x * 8 + j] = tot[threadIdx.x];
-    if ((int)threadIdx.x == j + 1) wn[j] = sqrt(tot[j + 1]);
-    if (threadIdx.x == 0) {
-      if (j > 0) H[j * 8 + (j - 1)] = h;
-      *ticket = 0;
-    }
-  }
+  arn_finish<LZ>(v, j, h, part, H, wn, ticket);
 }
 
 // step j, parts 2 and 3 (classical Gram-Schmidt twice): w -= sum_l c_l q_l with
@@ -1886,16 +1932,39 @@ int arnoldi_omega(Hierarchy &h, int k, const double *diag, double *H, double *wn
   AMG_CUDA(cudaMemsetAsync(H, 0, sizeof(double) * 72, s));
   AMG_CUDA(cudaMemsetAsync(ticket.p, 0, sizeof(unsigned), s));
   AMG_COUNT(), klaunch_sm(k_arn_start, g, 256, 0, s, n, h.p.seed, k, diag, W.p, U.p, dh.p, part.p, nrm2.p, ticket.p);
+  // symmetric A: the Lanczos form of the process (M = |D|^-1/2 A |D|^-1/2 is
+  // symmetric, so the Arnoldi matrix is tridiagonal): one product and one
+  // three-term update a step; otherwise Arnoldi with classical Gram-Schmidt twice
+  const bool lz = h.p.symmetric != 0;
   for (int j = 0; j < m; ++j) {
-    if (sp64)
-      AMG_COUNT(), klaunch_sm(k_arn_spmv_sell, gs, 256, 0, s, n, L.nslices, j, sp64, sc64, sv64, dh.p, W.p, U.p, Q.p,
-          w.p, part.p, nrm2.p, H, wn, ticket.p);
-    else if (wide)
-      AMG_COUNT(), klaunch_sm(k_arn_spmv<8>, gc, 256, 0, s, n, j, L.rp, L.ci, L.val, dh.p, W.p, U.p, Q.p, w.p, part.p,
-          nrm2.p, H, wn, ticket.p);
-    else
-      AMG_COUNT(), klaunch_sm(k_arn_spmv<4>, gc, 256, 0, s, n, j, L.rp, L.ci, L.val, dh.p, W.p, U.p, Q.p, w.p, part.p,
-          nrm2.p, H, wn, ticket.p);
+    if (sp64) {
+      if (lz)
+        AMG_COUNT(), klaunch_sm(k_arn_spmv_sell<true>, gs, 256, 0, s, n, L.nslices, j, sp64, sc64, sv64, dh.p, W.p,
+                                U.p, Q.p, w.p, part.p, nrm2.p, H, wn, ticket.p);
+      else
+        AMG_COUNT(), klaunch_sm(k_arn_spmv_sell<false>, gs, 256, 0, s, n, L.nslices, j, sp64, sc64, sv64, dh.p, W.p,
+                                U.p, Q.p, w.p, part.p, nrm2.p, H, wn, ticket.p);
+    } else if (wide) {
+      if (lz)
+        AMG_COUNT(), klaunch_sm(k_arn_spmv<8, true>, gc, 256, 0, s, n, j, L.rp, L.ci, L.val, dh.p, W.p, U.p, Q.p, w.p,
+                                part.p, nrm2.p, H, wn, ticket.p);
+      else
+        AMG_COUNT(), klaunch_sm(k_arn_spmv<8, false>, gc, 256, 0, s, n, j, L.rp, L.ci, L.val, dh.p, W.p, U.p, Q.p, w.p,
+                                part.p, nrm2.p, H, wn, ticket.p);
+    } else {
+      if (lz)
+        AMG_COUNT(), klaunch_sm(k_arn_spmv<4, true>, gc, 256, 0, s, n, j, L.rp, L.ci, L.val, dh.p, W.p, U.p, Q.p, w.p,
+                                part.p, nrm2.p, H, wn, ticket.p);
+      else
+        AMG_COUNT(), klaunch_sm(k_arn_spmv<4, false>, gc, 256, 0, s, n, j, L.rp, L.ci, L.val, dh.p, W.p, U.p, Q.p, w.p,
+                                part.p, nrm2.p, H, wn, ticket.p);
+    }
+    if (lz) {
+      if (j + 1 < m)  // the last step's update is not used
+        AMG_COUNT(), klaunch_sm(k_lz_update, g, 256, 0, s, n, j, (const double *)Q.p, (const double *)w.p, W.p, U.p,
+                                (const double *)dh.p, part.p, (const double *)H, nrm2.p, ticket.p);
+      continue;
+    }
     AMG_COUNT(), klaunch_sm(k_arn_orth, g, 256, 0, s, n, j, 0, Q.p, w.p, W.p, U.p, dh.p, part.p, H, corr.p, nrm2.p,
         ticket.p);
     AMG_COUNT(), klaunch_sm(k_arn_orth, g, 256, 0, s, n, j, 1, Q.p, w.p, W.p, U.p, dh.p, part.p, H, corr.p, nrm2.p,
