@@ -137,8 +137,13 @@ constexpr int sell_min_blocks() { return sizeof(VT) == 4 ? 6 : 4; }
 // a few hundred slices leaves most of the GPU idle and each warp's chain of
 // dependent loads sets the time, so there every load of a coarse row (15-30
 // entries) goes out in one or two steps.
+// With fused inner products the FP32-vector kernel needs more than the 40
+// registers of six resident blocks (it spilled there): four blocks, 64 registers.
+template <class MV, class VT, bool DOTS>
+constexpr int sell_launch_blocks() { return DOTS ? 4 : sell_min_blocks<VT>(); }
+
 template <class MV, class VT, int EPI, bool DOTS, bool GATE, int UW = 0>
-__global__ void __launch_bounds__(kThreads, UW ? 1 : sell_min_blocks<VT>()) k_sell(SellArgs<VT> a) {
+__global__ void __launch_bounds__(kThreads, UW ? 1 : sell_launch_blocks<MV, VT, DOTS>()) k_sell(SellArgs<VT> a) {
   pdl_wait_and_trigger();
   if (a.pred && *a.pred == 0) return;
   const int lane = threadIdx.x & 31;
