@@ -107,7 +107,7 @@ typedef struct amg_level_info {
   int32_t n_coarse;   /* n_{k+1} (0 on the coarsest level)                  */
   int32_t mis_rounds; /* PMIS iterations (k max rounds each) of this level  */
   double omega;       /* damped-Jacobi weight of this level                 */
-  int32_t spmv_blocks; /* thread blocks of this level's SpMV launches          */
+  int32_t spmv_blocks; /* thread blocks of the level's SpMV launches that fuse inner products */
   int32_t seg_tile;    /* rows per tile of the per-system inner products of a
                           batch (0: not a batch)                              */
 } amg_level_info;

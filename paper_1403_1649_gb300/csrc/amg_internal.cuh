@@ -161,12 +161,20 @@ struct Level {
   // a_ii plus the rounding errors of the row's off-diagonals, so that row sums
   // stay exact and the rounded matrix stays spectrally equivalent to A.
   int32_t nslices = 0;
-  int32_t sell_blocks = 0;    // grid of this level's SpMV launches (set at prepare, autotuned)
+  int32_t sell_blocks = 0;    // grid of this level's SpMV launches with fused inner products
+                              // (set at prepare, autotuned; at most kRedBlocks)
+  int32_t sell_plain_blocks = 0;  // grid of the launches without inner products (default: a
+                                  // warp per slice)
   int32_t seg_tile = 0;       // batch: rows per tile of the per-system inner products
   int64_t sell_entries = 0;
   int64_t *sptr = nullptr;
   int32_t *scol = nullptr;
   void *sval = nullptr;
+  // FP32 values: the entries as pairs instead of scol / sval (both null).  Entry
+  // e of lane l in slice sl is {column, value bits} in half (e & 1) of
+  // spair[sptr[sl] / 2 + 32 (e / 2) + l], so that a lane reads two entries with
+  // one 16-byte load; slice widths are even.
+  int4 *spair = nullptr;
   float *sdiag = nullptr;
   // level 0 only: every entry in FP64 for the outer Krylov method and the true
   // residual (the same arrays as sptr / scol / sval in FP64 mode)
@@ -201,6 +209,7 @@ struct TailLevel {
   const int64_t *sptr;
   const int32_t *scol;
   const void *sval;
+  const int4 *spair;   // FP32 values: entries as pairs (scol / sval null)
   const float *sdiag;  // split diagonal of a reduced-precision level (else null)
   const void *wd, *pw;
   const int32_t *agg, *aptr, *amem;

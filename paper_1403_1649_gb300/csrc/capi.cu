@@ -558,10 +558,17 @@ int amg_validate_hierarchy(const amg_hierarchy *H) {
       for (int32_t i = 0; i < L.n; ++i) expect(rp[i] <= rp[i + 1], k, "row pointers not monotone");
       for (int32_t c : ci) expect(c >= 0 && c < L.n, k, "column out of range");
       auto sp = fetch(L.sptr, (size_t)L.nslices + 1);
-      auto sc = fetch(L.scol, (size_t)L.sell_entries);
       expect(sp[0] == 0 && sp[L.nslices] == L.sell_entries, k, "SELL pointer ends");
-      for (int32_t q = 0; q < L.nslices; ++q) expect(sp[q] <= sp[q + 1] && (sp[q + 1] - sp[q]) % 32 == 0, k, "SELL slice");
-      for (int32_t c : sc) expect(c >= 0 && c < L.n, k, "SELL column out of range");
+      const int64_t unit = L.spair ? 64 : 32;  // pairs: slice widths are even
+      for (int32_t q = 0; q < L.nslices; ++q)
+        expect(sp[q] <= sp[q + 1] && (sp[q + 1] - sp[q]) % unit == 0, k, "SELL slice");
+      if (L.spair) {  // {column, value bits} pairs: the columns are the even words
+        auto pw = fetch(reinterpret_cast<const int32_t *>(L.spair), 2 * (size_t)L.sell_entries);
+        for (size_t q = 0; q < pw.size(); q += 2) expect(pw[q] >= 0 && pw[q] < L.n, k, "SELL column out of range");
+      } else {
+        auto sc = fetch(L.scol, (size_t)L.sell_entries);
+        for (int32_t c : sc) expect(c >= 0 && c < L.n, k, "SELL column out of range");
+      }
       if (k == 0 && L.sptr64 != L.sptr) {
         auto sp64 = fetch(L.sptr64, (size_t)L.nslices + 1);
         auto sc64 = fetch(L.scol64, (size_t)L.sell64_entries);

@@ -867,10 +867,11 @@ __global__ void k_diag(int32_t n, const int32_t *__restrict__ rp, const int32_t 
   diag[i] = d;
 }
 
-// SELL-32: width of every slice = longest row in it
-// width of each slice = its longest row (off-diagonal entries only when split)
+// SELL-32: width of each slice = its longest row (off-diagonal entries only when
+// split), rounded up to even for the pair layout of FP32 values
 __global__ void k_slice_width(int32_t n, int32_t nslices, const int32_t *__restrict__ rp,
-                              const int32_t *__restrict__ ci, bool split, int64_t *__restrict__ width32) {
+                              const int32_t *__restrict__ ci, bool split, bool pairs,
+                              int64_t *__restrict__ width32) {
   pdl_wait_and_trigger();
   const int lane = threadIdx.x & 31;
   const int32_t sl = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -880,6 +881,7 @@ __global__ void k_slice_width(int32_t n, int32_t nslices, const int32_t *__restr
   if (row < n)
     for (int32_t p = rp[row]; p < rp[row + 1]; ++p) len += (split && ci[p] == row) ? 0 : 1;
   len = __reduce_max_sync(0xffffffffu, len);
+  if (pairs) len = (len + 1) & ~1;
   if (lane == 0) width32[sl] = (int64_t)len * kSlice;
 }
 
@@ -901,11 +903,13 @@ template <> __device__ __forceinline__ double back_to_double<__nv_bfloat16>(__nv
 // CSR -> SELL-32 (column-major within a slice; padding: own row, value 0).
 // split: skip the diagonal entry and store sdiag[i] = a_ii + sum_j (a_ij - fl(a_ij))
 // over the row's off-diagonals, in FP64 then rounded once to FP32.
+// spair (FP32 values only): the entries go to the pair layout instead of scol /
+// sval, entry e of the lane as half (e & 1) of int4 sptr[sl] / 2 + 32 (e / 2) + lane.
 template <class MV>
 __global__ void k_build_sell(int32_t n, int32_t nslices, const int32_t *__restrict__ rp,
                              const int32_t *__restrict__ ci, const double *__restrict__ val,
                              const int64_t *__restrict__ sptr, int32_t *__restrict__ scol, MV *__restrict__ sval,
-                             float *__restrict__ sdiag) {
+                             int4 *__restrict__ spair, float *__restrict__ sdiag) {
   pdl_wait_and_trigger();
   const int lane = threadIdx.x & 31;
   const int32_t sl = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -914,6 +918,19 @@ __global__ void k_build_sell(int32_t n, int32_t nslices, const int32_t *__restri
   const int64_t base = sptr[sl];
   const int32_t width = (int32_t)((sptr[sl + 1] - base) / kSlice);
   const int32_t pad_col = row < n ? row : n - 1;
+  auto put = [&](int32_t e, int32_t c, MV m) {
+    if constexpr (std::is_same<MV, float>::value) {
+      if (spair) {
+        int32_t *w = reinterpret_cast<int32_t *>(spair + (base >> 1) + (int64_t)(e >> 1) * kSlice + lane) + 2 * (e & 1);
+        w[0] = c;
+        w[1] = __float_as_int(m);
+        return;
+      }
+    }
+    const int64_t at = base + (int64_t)e * kSlice + lane;
+    scol[at] = c;
+    sval[at] = m;
+  };
   int32_t e = 0;
   double dii = 0.0, comp = 0.0;
   if (row < n)
@@ -925,17 +942,11 @@ __global__ void k_build_sell(int32_t n, int32_t nslices, const int32_t *__restri
         continue;
       }
       const MV m = conv_val<MV>(v);
-      const int64_t at = base + (int64_t)e * kSlice + lane;
-      scol[at] = c;
-      sval[at] = m;
+      put(e, c, m);
       if (sdiag) comp = __dadd_rn(comp, __dadd_rn(v, -back_to_double<MV>(m)));
       ++e;
     }
-  for (; e < width; ++e) {
-    const int64_t at = base + (int64_t)e * kSlice + lane;
-    scol[at] = pad_col;
-    sval[at] = conv_val<MV>(0.0);
-  }
+  for (; e < width; ++e) put(e, pad_col, conv_val<MV>(0.0));
   if (sdiag && row < n) sdiag[row] = __double2float_rn(__dadd_rn(dii, comp));
 }
 
@@ -1865,43 +1876,44 @@ void build_solve_matrix(Hierarchy &h, Level &L, cudaStream_t s, bool fresh) {
   const int32_t n = L.n;
   L.nslices = (n + kSlice - 1) / kSlice;
   const unsigned g = blocks_for((int64_t)L.nslices * 32);
-  auto layout = [&](bool split, int64_t *&sptr, int32_t *&scol, int64_t &entries) {
+  // pairs: FP32 values, stored with their columns in L.spair (no scol / sval)
+  auto layout = [&](bool split, bool pairs, int64_t *&sptr, int32_t *&scol, int64_t &entries) {
     DevBuf<int64_t> w32(L.nslices + 1);
-    AMG_COUNT(), klaunch_sm(k_slice_width, g, 256, 0, s, n, L.nslices, L.rp, L.ci, split, w32.p);
+    AMG_COUNT(), klaunch_sm(k_slice_width, g, 256, 0, s, n, L.nslices, L.rp, L.ci, split, pairs, w32.p);
     AMG_LAUNCH_CHECK();
     sptr = h.arena.get<int64_t>(L.nslices + 1);
     exclusive_scan<int64_t, int64_t>(w32.p, sptr, L.nslices, s, &entries);
-    scol = h.arena.get<int32_t>(entries);
+    if (pairs) L.spair = h.arena.get<int4>(entries / 2);
+    else scol = h.arena.get<int32_t>(entries);
   };
   const bool split = h.p.precision != AMG_PREC_F64;
-  if (fresh) layout(split, L.sptr, L.scol, L.sell_entries);
+  if (fresh) layout(split, h.p.precision == AMG_PREC_F32, L.sptr, L.scol, L.sell_entries);
   const int64_t entries = L.sell_entries;
   if (fresh && split) L.sdiag = h.arena.get<float>(n);
   switch (h.p.precision) {
     case AMG_PREC_F64:
       if (fresh) L.sval = h.arena.get<double>(entries);
       AMG_COUNT(), klaunch_sm(k_build_sell<double>, g, 256, 0, s, n, L.nslices, L.rp, L.ci, L.val, L.sptr, L.scol,
-          (double *)L.sval, nullptr);
+          (double *)L.sval, nullptr, nullptr);
       break;
     case AMG_PREC_F32:
-      if (fresh) L.sval = h.arena.get<float>(entries);
-      AMG_COUNT(), klaunch_sm(k_build_sell<float>, g, 256, 0, s, n, L.nslices, L.rp, L.ci, L.val, L.sptr, L.scol,
-          (float *)L.sval, L.sdiag);
+      AMG_COUNT(), klaunch_sm(k_build_sell<float>, g, 256, 0, s, n, L.nslices, L.rp, L.ci, L.val, L.sptr, nullptr,
+          nullptr, L.spair, L.sdiag);
       break;
     default:
       if (fresh) L.sval = h.arena.get<__nv_bfloat16>(entries);
       AMG_COUNT(), klaunch_sm(k_build_sell<__nv_bfloat16>, g, 256, 0, s, n, L.nslices, L.rp, L.ci, L.val, L.sptr,
-          L.scol, (__nv_bfloat16 *)L.sval, L.sdiag);
+          L.scol, (__nv_bfloat16 *)L.sval, nullptr, L.sdiag);
   }
   AMG_LAUNCH_CHECK();
   if (&L != &h.lev[0]) return;
   if (split) {
     if (fresh) {
-      layout(false, L.sptr64, L.scol64, L.sell64_entries);
+      layout(false, false, L.sptr64, L.scol64, L.sell64_entries);
       L.sval64 = h.arena.get<double>(L.sell64_entries);
     }
     AMG_COUNT(), klaunch_sm(k_build_sell<double>, g, 256, 0, s, n, L.nslices, L.rp, L.ci, L.val, L.sptr64, L.scol64,
-        L.sval64, nullptr);
+        L.sval64, nullptr, nullptr);
     AMG_LAUNCH_CHECK();
   } else {
     L.sptr64 = L.sptr;

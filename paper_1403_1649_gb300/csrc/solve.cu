@@ -35,6 +35,7 @@ struct SellArgs {
   const int64_t *sptr;
   const int32_t *scol;
   const void *sval;
+  const int4 *spair;   // FP32 values: entries as {column, value} pairs (scol / sval null)
   const float *sdiag;  // split diagonal (reduced precision), else null
   const unsigned char *live;  // batch: 0 for slices whose systems all stopped (skipped); else null
   const VT *x;    // SpMV input
@@ -68,6 +69,8 @@ enum Epi { E_Y = 0, E_RESID = 1, E_POST = 2, E_DSCALE = 3, E_POLYPRE = 4, E_RESI
            E_HORNER_LAST = 7 };
 
 template <class MV> __device__ __forceinline__ MV ld_stream(const MV *p) { return __ldcs(p); }
+// FP32 matrices are stored as {column, value} pairs (Level::spair)
+template <class MV> constexpr bool kPairs = std::is_same<MV, float>::value;
 
 // per-block partial sums of up to three dot products -> partials[k*kRedBlocks + block]
 __device__ __forceinline__ void block_store_dots3(double a0, double a1, double a2, int ndot, double *partials) {
@@ -176,32 +179,72 @@ __global__ void __launch_bounds__(kThreads, UW ? 1 : sell_launch_blocks<MV, VT, 
     }
     const int64_t base = a.sptr[sl];
     const int32_t width = (int32_t)((a.sptr[sl + 1] - base) >> 5);
-    const int32_t *__restrict__ cp = a.scol + base + lane;
-    const MV *__restrict__ vp = sval + base + lane;
     // otherwise the split diagonal (FP32 / BF16 values only) and x_row are loaded
     // right behind the first step's matrix loads, so that their latency overlaps
     // the gathers
-    for (int32_t e = 0; e < width; e += U) {
-      int32_t c[U];
-      MV v[U];
+    if constexpr (kPairs<MV>) {
+      // FP32 values: a lane's entries 2j and 2j+1 come in one 16-byte load
+      // (widths are even, U is even).  FULL: all U entries of the step exist
+      static_assert(U % 2 == 0, "pairs need an even step");
+      const int4 *__restrict__ pp = a.spair + (base >> 1) + lane;
+      auto step = [&](int32_t e, auto full) {
+        constexpr bool FULL = decltype(full)::value;
+        int32_t c[U];
+        float v[U];
 #pragma unroll
-      for (int q = 0; q < U; ++q) {
-        if (e + q < width) {
-          c[q] = ld_stream(cp + 32 * (e + q));
-          v[q] = ld_stream(vp + 32 * (e + q));
+        for (int q = 0; q < U; q += 2) {
+          if (FULL || e + q < width) {
+            const int4 pr = ld_stream(pp + 16 * (e + q));
+            c[q] = pr.x;
+            v[q] = __int_as_float(pr.y);
+            c[q + 1] = pr.z;
+            v[q + 1] = __int_as_float(pr.w);
+          }
         }
-      }
-      if (UW == 0 && e == 0 && diag) {
-        dg = (VT)ld_stream(a.sdiag + row);
-        xr = __ldg(a.x + row);
-      }
-      VT xv[U];
+        if (UW == 0 && e == 0 && diag) {
+          dg = (VT)ld_stream(a.sdiag + row);
+          xr = __ldg(a.x + row);
+        }
+        VT xv[U];
 #pragma unroll
-      for (int q = 0; q < U; ++q)
-        if (e + q < width) xv[q] = __ldg(a.x + c[q]);
+        for (int q = 0; q < U; ++q)
+          if (FULL || e + q < width) xv[q] = __ldg(a.x + c[q]);
 #pragma unroll
-      for (int q = 0; q < U; ++q)
-        if (e + q < width) y += to_acc(v[q], VT(0)) * xv[q];
+        for (int q = 0; q < U; ++q)
+          if (FULL || e + q < width) y += v[q] * xv[q];
+      };
+      // the common slice (a 7-point row: one full step) takes the step without
+      // predicates, whose loads all go out before the first gather
+      if (UW == 0 && width == U) {
+        step(0, std::true_type{});
+      } else {
+        for (int32_t e = 0; e < width; e += U) step(e, std::false_type{});
+      }
+    } else {
+      const int32_t *__restrict__ cp = a.scol + base + lane;
+      const MV *__restrict__ vp = sval + base + lane;
+      for (int32_t e = 0; e < width; e += U) {
+        int32_t c[U];
+        MV v[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+          if (e + q < width) {
+            c[q] = ld_stream(cp + 32 * (e + q));
+            v[q] = ld_stream(vp + 32 * (e + q));
+          }
+        }
+        if (UW == 0 && e == 0 && diag) {
+          dg = (VT)ld_stream(a.sdiag + row);
+          xr = __ldg(a.x + row);
+        }
+        VT xv[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q)
+          if (e + q < width) xv[q] = __ldg(a.x + c[q]);
+#pragma unroll
+        for (int q = 0; q < U; ++q)
+          if (e + q < width) y += to_acc(v[q], VT(0)) * xv[q];
+      }
     }
     if (diag) {
       if (width == 0) {  // a row without off-diagonal entries
@@ -1007,6 +1050,12 @@ inline int default_sell_grid(const Level &L) {
   return grid_for((int64_t)L.nslices, kWarps, sell_min_blocks<VT>() * 152);
 }
 inline int sell_grid(const Level &L) { return L.sell_blocks; }
+// launches without inner products have no partial-sum buffer to fill, so the
+// autotuner may give them up to one warp per slice; by default they take the
+// same wave of resident blocks (one warp per slice measured slower on the 128^3
+// level 0: 34.4 against 27.4 us under ncu)
+inline int full_plain_grid(const Level &L) { return grid_for((int64_t)L.nslices, kWarps, 1 << 30); }
+inline int plain_grid(const Level &L) { return L.sell_plain_blocks; }
 // levels of at most kSmallSlices slices (fewer warps than the GPU holds at a
 // quarter of its occupancy) run the products with kSmallU entries a step, with
 // FP32 vectors (measured: no gain with FP64 vectors)
@@ -1041,6 +1090,7 @@ struct Engine {
     a.sptr = L.sptr;
     a.scol = L.scol;
     a.sval = L.sval;
+    a.spair = L.spair;
     a.sdiag = L.sdiag;
     if (h.batched) a.live = L.slive;
     a.x = x;
@@ -1056,7 +1106,7 @@ struct Engine {
     // post-smoothing step of level 0 (z^T q of the outer flexible CG)
     if (h.batched) {  // no fused inner products in a batch: they are per system (segdot)
       if (a.ndot) throw Error{AMG_ERR_UNSUPPORTED, "batched SpMV was given fused inner products"};
-      klaunch(k_sell<MV, VT, EPI, false, true>, sell_grid(h.lev[k]), kThreads, s, a);
+      klaunch(k_sell<MV, VT, EPI, false, true>, plain_grid(h.lev[k]), kThreads, s, a);
       check();
       return;
     }
@@ -1078,11 +1128,11 @@ struct Engine {
     }
     if constexpr ((EPI == E_Y || EPI == E_RESID || EPI == E_POST) && sizeof(VT) == 4)
       if (small) {
-        klaunch(k_sell<MV, VT, EPI, false, false, kSmallU>, sell_grid(h.lev[k]), kThreads, s, a);
+        klaunch(k_sell<MV, VT, EPI, false, false, kSmallU>, plain_grid(h.lev[k]), kThreads, s, a);
         check();
         return;
       }
-    klaunch(k_sell<MV, VT, EPI, false, false>, sell_grid(h.lev[k]), kThreads, s, a);
+    klaunch(k_sell<MV, VT, EPI, false, false>, plain_grid(h.lev[k]), kThreads, s, a);
     check();
   }
 
@@ -1423,6 +1473,7 @@ void alloc_level_vectors(Hierarchy &h, Level &L, int k) {
     L.w = vec();
   }
   if (L.sell_blocks <= 0) L.sell_blocks = default_sell_grid<VT>(L);
+  if (L.sell_plain_blocks <= 0) L.sell_plain_blocks = L.sell_blocks;
   L.slots = h.arena.get<double>(kNumSlots);
   L.flag = h.arena.get<int>(4);
   L.partials = h.arena.get<double>((size_t)kRedBlocks * 8);
@@ -1458,6 +1509,7 @@ void configure_tail(Hierarchy &h, cudaStream_t s) {
     T.sptr = L.sptr;
     T.scol = L.scol;
     T.sval = L.sval;
+    T.spair = L.spair;
     T.sdiag = L.sdiag;
     T.wd = L.wd;
     T.pw = L.pw;
@@ -2007,8 +2059,9 @@ void prepare_batched(Hierarchy &h, cudaStream_t s) {
 
 // Autotuner of the launch shapes (setup time).  For every level the SpMV is
 // timed with CUDA events over candidate grid sizes (multiples of the 152 SMs up
-// to the partial-sum capacity) and the smallest grid within 3 % of the fastest
-// is kept; for a batch, the row tile of the per-system inner products is chosen
+// to one warp per slice) and the smallest grid within 3 % of the fastest is
+// kept, for the launches that fuse inner products among the grids within the
+// partial-sum capacity; for a batch, the row tile of the per-system inner products is chosen
 // the same way.  The shapes change the grouping of partial sums only.
 template <class MV, class VT>
 void autotune_t(Hierarchy &h, cudaStream_t s) {
@@ -2039,16 +2092,20 @@ void autotune_t(Hierarchy &h, cudaStream_t s) {
       Level &L = h.lev[k];
       DevBuf<VT> x((size_t)L.n + 1), y((size_t)L.n + 1);
       AMG_CUDA(cudaMemsetAsync(x.p, 0, sizeof(VT) * (L.n + 1), s));
-      const int gmax = grid_for((int64_t)L.nslices, kWarps, kRedBlocks);
-      std::vector<std::pair<int, float>> t;
-      for (int g : {152, 304, 608, 912, 1216}) {
-        const int gg = std::min(g, gmax);
+      // the plain product at each grid; launches with fused inner products take
+      // the best grid within the partial-sum capacity
+      const int gfull = full_plain_grid(L);
+      std::vector<std::pair<int, float>> t, tr;
+      for (int g : {152, 304, 608, 912, 1216, 2432, 4864, 1 << 30}) {
+        const int gg = std::min(g, gfull);
         if (!t.empty() && t.back().first == gg) continue;
-        L.sell_blocks = gg;
+        L.sell_plain_blocks = gg;
         const SellArgs<VT> a = eng.sell_args(k, x.p, y.p, nullptr);
         t.push_back({gg, time_it([&] { eng.template sell<E_Y>(a, k); })});
+        if (gg <= kRedBlocks) tr.push_back(t.back());
       }
-      L.sell_blocks = pick(t);
+      L.sell_plain_blocks = pick(t);
+      L.sell_blocks = pick(tr);
       if (h.batched && k < h.L - 1) {
         std::vector<std::pair<int, float>> tt;
         for (int tile : {1024, 2048, 4096, 8192}) {

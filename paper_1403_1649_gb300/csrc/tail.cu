@@ -79,16 +79,29 @@ __device__ __forceinline__ VT sell_row(const TailLevel &L, int32_t sl, int lane,
   const int32_t width = (int32_t)((L.sptr[sl + 1] - base) >> 5);
   const int32_t *cp = L.scol + base + lane;
   const MV *vp = static_cast<const MV *>(L.sval) + base + lane;
+  const int4 *pp = L.spair + (base >> 1) + lane;  // FP32 values: {column, value} pairs
   VT y = VT(0);
   for (int32_t e = 0; e < width; e += 4) {
     int32_t cc[4];
     MV vv[4];
+    if constexpr (std::is_same<MV, float>::value) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-      if (e + q < width) {
-        cc[q] = cp[32 * (e + q)];
-        vv[q] = vp[32 * (e + q)];
-      }
+      for (int q = 0; q < 4; q += 2)
+        if (e + q < width) {
+          const int4 pr = pp[16 * (e + q)];
+          cc[q] = pr.x;
+          vv[q] = __int_as_float(pr.y);
+          cc[q + 1] = pr.z;
+          vv[q + 1] = __int_as_float(pr.w);
+        }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (e + q < width) {
+          cc[q] = cp[32 * (e + q)];
+          vv[q] = vp[32 * (e + q)];
+        }
+    }
 #pragma unroll
     for (int q = 0; q < 4; ++q)
       if (e + q < width) y += to_vt(vv[q], VT(0)) * xf(cc[q]);
