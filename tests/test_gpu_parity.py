@@ -189,6 +189,66 @@ def test_reduced_precision_level0_spmv_full_size(gpu, prec, grid):
     assert (err <= bound).all(), (err / bound).max()
 
 
+def irregular_spd(n=1013, iso=40, seed=11):
+    """A symmetric, diagonally dominant matrix whose rows have 0 to ~20
+    off-diagonal entries, so that SELL slices get odd and even widths, rows
+    shorter than their slice's longest, a ragged last slice, and (the last
+    `iso` rows have no neighbours) a slice without off-diagonal entries."""
+    m = n - iso
+    deg = (P.uniform01(seed, 0, m) * 10).astype(np.int64)
+    src = np.repeat(np.arange(m), deg)
+    dst = (P.uniform01(seed, 1, src.size) * m).astype(np.int64)
+    keep = src != dst
+    src, dst = src[keep], dst[keep]
+    w = -(0.5 + P.uniform01(seed, 2, src.size))
+    a = {}
+    for i, j, v in zip(src.tolist(), dst.tolist(), w.tolist()):
+        key = (min(i, j), max(i, j))
+        a[key] = a.get(key, 0.0) + v
+    rows = [[] for _ in range(n)]
+    for (i, j), v in a.items():
+        rows[i].append((j, v))
+        rows[j].append((i, v))
+    rp, ci, va = [0], [], []
+    for i in range(n):
+        d = 1.0 + sum(abs(v) for _, v in rows[i])
+        ent = sorted(rows[i] + [(i, d)])
+        ci += [j for j, _ in ent]
+        va += [v for _, v in ent]
+        rp.append(len(ci))
+    return P.CSR(n, np.array(rp, np.int32), np.array(ci, np.int32), np.array(va, np.float64))
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_spmv_irregular_rows(gpu, prec):
+    """Level-0 product on rows of irregular length in every precision: FP32
+    values take the {column, value} pair layout with even slice widths and the
+    predicated step (only 6-wide slices take the unpredicated one), BF16 and
+    FP64 the column and value arrays; an all-diagonal slice and the ragged last
+    slice included.  The stored SELL passes the library's own structural check."""
+    import torch
+    A = irregular_spd()
+    lens = np.diff(A.rowptr) - 1
+    widths = np.array([lens[q:q + 32].max() for q in range(0, A.n, 32)])
+    assert (widths % 2 == 1).any() and (widths % 2 == 0).any() and widths[-1] == 0 and A.n % 32
+    g = gpu.Hierarchy(A, alpha=0.25, seed=3, precision=prec)
+    assert gpu.lib().amg_validate_hierarchy(g.h) == 0, gpu.amg_last_error()
+    vt = np.float64 if prec == 0 else np.float32
+    x = P.rhs_uniform(A.n, 41).astype(vt)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.zeros_like(xd)
+    gpu.amg_spmv(g.h, 0, xd, yd)
+    torch.cuda.synchronize()
+    x64 = x.astype(np.float64)
+    ref = A.matvec(x64)
+    err = np.abs(yd.cpu().numpy().astype(np.float64) - ref)
+    if prec == 0:
+        assert err.max() <= 1e-14 * np.abs(ref).max()
+    else:
+        bound = reduced_spmv_bound(A, x64, 2.0 ** -24 if prec == 1 else 2.0 ** -8)
+        assert (err <= bound).all(), (err / bound).max()
+
+
 @pytest.mark.parametrize("prec", [1, 2])
 def test_reduced_precision_spmv_every_level_varcoef(gpu, orc, prec):
     """Reduced-precision products of every level of a variable-coefficient
