@@ -1547,15 +1547,10 @@ __global__ void k_dense_from_csr(int32_t n, const int32_t *__restrict__ rp, cons
 }
 
 // In-place dense Cholesky (lower) by one thread block, then the inverse
-// A^-1 = L^-T L^-1 column by column (one thread per column).
+// A^-1 = L^-T L^-1 column by column (one thread per column): the blocks of a
+// batch larger than the shared-memory Gauss-Jordan sweeps take.
 __device__ void cholesky_inverse_body(int32_t n, double *__restrict__ A, double *__restrict__ Ainv,
                                       int *__restrict__ err);
-
-__global__ void k_cholesky_inverse(int32_t n, double *__restrict__ A, double *__restrict__ Ainv,
-                                   int *__restrict__ err) {
-  pdl_wait_and_trigger();
-  cholesky_inverse_body(n, A, Ainv, err);
-}
 
 // one thread block per system block of a batch
 __global__ void k_cholesky_inverse_batched(int32_t nsys, const int32_t *__restrict__ off,
@@ -1683,6 +1678,146 @@ __global__ void k_gj_inverse_batched(int32_t nsys, const int32_t *__restrict__ o
   const int32_t s = blockIdx.x;
   if (s >= nsys) return;
   gj_inverse_body(off[s + 1] - off[s], A + boff[s], Ainv + boff[s], err, gj_a);
+}
+
+// ---- grid barrier of a cooperative launch -----------------------------------
+struct GridBarrier {
+  unsigned count;  // blocks arrived at the current barrier
+  unsigned gen;    // barriers completed
+  int err;         // a block gave up waiting: every block returns
+};
+constexpr long long kBarrierSpin = 1LL << 24;  // polls (~40 ns apart) before a block gives up
+
+// all blocks of a cooperative launch, which are co-resident by construction;
+// false once any block gave up waiting (every wait is bounded)
+__device__ bool grid_barrier(GridBarrier *b) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *gen = &b->gen;
+    const unsigned g = *gen;
+    __threadfence();
+    if (atomicAdd(&b->count, 1u) == gridDim.x - 1) {
+      atomicExch(&b->count, 0u);
+      __threadfence();
+      atomicAdd(&b->gen, 1u);
+    } else {
+      long long it = 0;
+      while (*gen == g) {
+        if (++it > kBarrierSpin || *(volatile int *)&b->err) {
+          atomicExch(&b->err, 1);
+          break;
+        }
+        __nanosleep(40);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *(volatile int *)&b->err == 0;
+}
+
+// ---- coarsest inverse across the GPU: blocked Gauss-Jordan --------------------
+// The sweeps of k_gj_inverse taken kGjb pivots at a time.  With the pivot block
+// P (rows and columns p0 .. p0 + kk) and B = M_PP^-1, one step is
+//   M_PP <- B,  M_Pj <- B M_Pj,  M_iP <- -M_iP B,  M_ij <- M_ij - M_iP B M_Pj
+// for i, j outside P; after the last block M = A^-1 (no pivoting: A is SPD, and
+// so is every pivot block).  One cooperative launch: a thread block owns whole
+// columns, inverts the kk x kk pivot block itself (the same arithmetic in every
+// block), and the steps alternate between two copies of the matrix with a grid
+// barrier between steps.  GB300 runs FP64 at ~2 multiply-adds per clock per SM,
+// so the n^3 multiply-adds of the inverse are spread over all SMs.
+// The matrix copies are read through L2 only (ld.cg): other blocks wrote them
+// in the previous step, and a block's L1 may still hold lines of an older step.
+// err: 1 a pivot block is not positive definite, 2 a barrier gave up.
+constexpr int kGjb = 16;
+constexpr int32_t kGjOneBlock = 64;  // up to this size one block in shared memory is faster
+
+__global__ void __launch_bounds__(256) k_gj_blocked(int32_t n, const double *__restrict__ A, double *M0, double *M1,
+                                                    double *__restrict__ Ainv, GridBarrier *bar,
+                                                    int *__restrict__ err) {
+  __shared__ double sB[kGjb][kGjb + 1];  // pivot block, inverted in place
+  __shared__ double sW[kGjb];            // B M_Pj of the current column
+  __shared__ double sF[kGjb];            // multipliers of the current sweep
+  const int tid = threadIdx.x;
+  const int64_t nn = (int64_t)n * n;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + tid; t < nn; t += (int64_t)gridDim.x * blockDim.x) M0[t] = A[t];
+  if (!grid_barrier(bar)) {
+    if (tid == 0) *err = 2;
+    return;
+  }
+  const int nb = (n + kGjb - 1) / kGjb;
+  for (int st = 0; st < nb; ++st) {
+    const double *cur = (st & 1) ? M1 : M0;
+    double *nxt = (st & 1) ? M0 : M1;
+    const int32_t p0 = st * kGjb;
+    const int kk = min(kGjb, n - p0);
+    for (int t = tid; t < kk * kk; t += blockDim.x) sB[t / kk][t % kk] = __ldcg(cur + (int64_t)(p0 + t / kk) * n + p0 + t % kk);
+    __syncthreads();
+    for (int p = 0; p < kk; ++p) {  // unblocked sweeps of the pivot block
+      const double piv = sB[p][p];  // the same in every thread and every block
+      if (!(piv > 0.0)) {
+        if (blockIdx.x == 0 && tid == 0) *err = 1;
+        return;  // every block stops here: no barrier is left waiting
+      }
+      const double inv = 1.0 / piv;
+      if (tid < kk) sF[tid] = sB[tid][p] * inv;
+      __syncthreads();
+      if (tid < kk * kk) {
+        const int i = tid / kk, j = tid % kk;
+        if (i != p && j != p) sB[i][j] = fma(-sF[i], sB[p][j], sB[i][j]);
+      }
+      __syncthreads();
+      if (tid < kk && tid != p) {
+        sB[p][tid] *= inv;
+        sB[tid][p] = -sF[tid];
+      }
+      if (tid == 0) sB[p][p] = inv;
+      __syncthreads();
+    }
+    for (int32_t j = blockIdx.x; j < n; j += gridDim.x) {
+      if (j < p0 || j >= p0 + kk) {
+        if (tid < kk) {
+          double w = 0.0;
+          for (int m = 0; m < kk; ++m) w = fma(sB[tid][m], __ldcg(cur + (int64_t)(p0 + m) * n + j), w);
+          sW[tid] = w;
+        }
+        __syncthreads();
+        for (int32_t i = tid; i < n; i += blockDim.x) {
+          double v;
+          if (i >= p0 && i < p0 + kk) {
+            v = sW[i - p0];
+          } else {
+            const double *aip = cur + (int64_t)i * n + p0;
+            v = __ldcg(cur + (int64_t)i * n + j);
+            for (int l = 0; l < kk; ++l) v = fma(-__ldcg(aip + l), sW[l], v);
+          }
+          nxt[(int64_t)i * n + j] = v;
+        }
+      } else {
+        const int c = j - p0;
+        for (int32_t i = tid; i < n; i += blockDim.x) {
+          double v;
+          if (i >= p0 && i < p0 + kk) {
+            v = sB[i - p0][c];
+          } else {
+            const double *aip = cur + (int64_t)i * n + p0;
+            v = 0.0;
+            for (int l = 0; l < kk; ++l) v = fma(__ldcg(aip + l), sB[l][c], v);
+            v = -v;
+          }
+          nxt[(int64_t)i * n + j] = v;
+        }
+      }
+      __syncthreads();  // sW is rewritten by the next column
+    }
+    if (!grid_barrier(bar)) {
+      if (tid == 0) *err = 2;
+      return;
+    }
+  }
+  const double *fin = (nb & 1) ? M1 : M0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + tid; t < nn; t += (int64_t)gridDim.x * blockDim.x)
+    Ainv[t] = __ldcg(fin + t);
 }
 
 __global__ void k_gather_i32(int32_t n, const int32_t *__restrict__ idx, const int32_t *__restrict__ src,
@@ -2280,18 +2415,38 @@ void finish_levels(Hierarchy &h, cudaStream_t s, bool fresh) {
     AMG_CUDA(cudaMemsetAsync(dense.p, 0, sizeof(double) * (size_t)Lc.n * Lc.n, s));
     AMG_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
     AMG_COUNT(), klaunch_sm(k_dense_from_csr, blocks_for(Lc.n), 256, 0, s, Lc.n, Lc.rp, Lc.ci, Lc.val, dense.p);
-    if (p.symmetric && Lc.n <= kGjMax) {  // in shared memory
+    if (p.symmetric && Lc.n <= kGjOneBlock) {  // one block, in shared memory
       const size_t sm = sizeof(double) * ((size_t)Lc.n * Lc.n + Lc.n);
       AMG_CUDA(cudaFuncSetAttribute(k_gj_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
       AMG_COUNT(), klaunch_sm(k_gj_inverse, 1, 1024, sm, s, Lc.n, (const double *)dense.p, h.coarse_inv, err.p);
-    } else if (p.symmetric) {
-      AMG_COUNT(), klaunch_sm(k_cholesky_inverse, 1, 1024, 0, s, Lc.n, dense.p, h.coarse_inv, err.p);
+    } else if (p.symmetric) {  // blocked sweeps over the whole GPU, one cooperative launch
+      DevBuf<double> m1((size_t)Lc.n * Lc.n);
+      DevBuf<GridBarrier> bar(1);
+      AMG_CUDA(cudaMemsetAsync(bar.p, 0, sizeof(GridBarrier), s));
+      int dev = 0, sms = 0, per = 0;
+      AMG_CUDA(cudaGetDevice(&dev));
+      AMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+      AMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_gj_blocked, 256, 0));
+      cudaLaunchConfig_t cfg{};
+      cfg.gridDim = std::max(1, std::min(per * sms, Lc.n));  // a block per column at most
+      cfg.blockDim = 256;
+      cfg.stream = s;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeCooperative;
+      at[0].val.cooperative = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      AMG_COUNT();
+      AMG_CUDA(cudaLaunchKernelEx(&cfg, k_gj_blocked, Lc.n, (const double *)dense.p, dense.p, m1.p, h.coarse_inv,
+                                  bar.p, err.p));
     } else {
       DevBuf<double> fac(Lc.n);
       AMG_COUNT(), klaunch_sm(k_lu_inverse, 1, 1024, 0, s, Lc.n, dense.p, h.coarse_inv, fac.p, err.p);
     }
     AMG_LAUNCH_CHECK();
-    if (read_scalar(err.p, s))
+    const int e = read_scalar(err.p, s);
+    if (e == 2) throw Error{AMG_ERR_CUDA, "coarsest inverse: a grid barrier timed out"};
+    if (e)
       throw Error{AMG_ERR_SETUP, p.symmetric ? "coarsest level matrix is not positive definite"
                                              : "coarsest level matrix is singular"};
   }

@@ -88,6 +88,25 @@ def test_preconditioner_parity(gpu, orc, name):
     assert np.linalg.norm(zg - zo) <= 1e-11 * np.linalg.norm(zo)
 
 
+@pytest.mark.parametrize("name,cmax", [("poisson2d_64", 600), ("varcoef3d_24", 600), ("fem2d_48", 400),
+                                       ("poisson3d_20", 600)])
+def test_large_coarsest_level(gpu, orc, name, cmax):
+    """A coarsest level of more than 64 rows (the paper keeps about 600 on the
+    GPU, Sec. 3): its inverse comes from the blocked Gauss-Jordan sweeps of one
+    cooperative launch over the whole GPU.  Same hierarchy as the oracle (whose
+    coarsest solve is a Cholesky factorisation), preconditioner to 1e-11 and six
+    outer iterations to 1e-10."""
+    A, g, o = pair(gpu, orc, name, coarse_max=cmax, max_iter=6)
+    nl = g.level(g.nlevels - 1)["n"]
+    assert 64 < nl <= cmax and o.nlevels == g.nlevels and o.level(o.nlevels - 1).n == nl
+    b = P.rhs_uniform(A.n, 13)
+    zg, zo = g.precond(b), o.precond(b)
+    assert np.linalg.norm(zg - zo) <= 1e-11 * np.linalg.norm(zo)
+    xg, ig = g.solve(b, tol=0.0, allow=(gpu.AMG_OK, gpu.AMG_ERR_NOT_CONVERGED))
+    xo, io = o.solve(b, tol=0.0, max_iter=6)
+    assert np.linalg.norm(xg - xo) <= 1e-10 * np.linalg.norm(xo)
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_solve_iterates_parity(gpu, orc, name):
     A, g, o = pair(gpu, orc, name, max_iter=6)
