@@ -30,6 +30,9 @@ sys.path.insert(0, ROOT)
 METRIC = "solve ms & DoF/s to 1e-8 rel. residual, mixed/learned vs FP64 AMG; SpMV % HBM"
 M_GRID = 128
 ALPHA, SEED, TOL = 0.5, 1, 1e-8
+# coarsest level: the paper keeps about 600 unknowns on the GPU (Sec. 3); the
+# batch keeps the library default of 64 (one dense block per system)
+COARSE_MAX = 600
 PREC = {"f64": 0, "f32": 1, "bf16": 2}
 PREC_DTYPE = {"f64": "f64", "f32": "f32+f64", "bf16": "bf16+f32+f64"}
 
@@ -122,7 +125,7 @@ def workload_results(name: str, reps: int = 1):
                         ("fcg_f64", dict(outer=0, precision=0)), ("fgmres30_bf16", dict(outer=1, precision=2)),
                         ("fgmres30_f64", dict(outer=1, precision=0))):
             cap = 600 if pk["outer"] == 1 else 2000
-            go, info = run_single(A, b, alpha=0.5, seed=2, restart=30, max_iter=cap, **pk)
+            go, info = run_single(A, b, alpha=0.5, seed=2, restart=30, max_iter=cap, coarse_max=COARSE_MAX, **pk)
             info["allow"] = (amg.AMG_OK, amg.AMG_ERR_NOT_CONVERGED)
             t, i = timed(go, reps)
             res[var] = summary(t, i)
@@ -140,7 +143,8 @@ def workload_results(name: str, reps: int = 1):
         res = {}
         for var, pk in (("learned_f32", dict(precision=1, smoother=1)), ("jacobi_f64", dict(precision=0)),
                         ("jacobi_f32", dict(precision=1)), ("learned_f64", dict(precision=0, smoother=1))):
-            go, info = run_single(A, b, alpha=0.25, seed=3, omega_mode=1, omega=2.0 / 3.0, max_iter=2000, **pk)
+            go, info = run_single(A, b, alpha=0.25, seed=3, omega_mode=1, omega=2.0 / 3.0, max_iter=2000,
+                                  coarse_max=COARSE_MAX, **pk)
             info["w16"] = w16
             t, i = timed(go, reps)
             res[var] = summary(t, i)
@@ -274,7 +278,8 @@ def profile_spmv():
     dev = torch.device("cuda", 0)
     rp, ci, va = (torch.from_numpy(a).to(dev) for a in (A.rowptr, A.col, A.val))
     for prec in ("f32", "f64"):
-        h = amg.amg_setup(rp, ci, va, amg.amg_default_params(alpha=ALPHA, seed=SEED, precision=PREC[prec]))
+        h = amg.amg_setup(rp, ci, va, amg.amg_default_params(alpha=ALPHA, seed=SEED, precision=PREC[prec],
+                                                             coarse_max=COARSE_MAX))
         vt = torch.float64 if prec == "f64" else torch.float32
         x = torch.rand(A.n, dtype=vt, device=dev)
         y = torch.empty_like(x)
@@ -328,7 +333,7 @@ def oracle_sample(grid: int = M_GRID, omp: bool = True):
     A = P.poisson3d(grid)
     b = P.rhs_uniform(A.n, SEED)
     t0 = time.perf_counter()
-    H = oracle.Hierarchy(A, omp=omp, alpha=ALPHA, seed=SEED)
+    H = oracle.Hierarchy(A, omp=omp, alpha=ALPHA, seed=SEED, coarse_max=COARSE_MAX)
     t1 = time.perf_counter()
     x, info = H.solve(b, tol=TOL, max_iter=500)
     dt = time.perf_counter() - t0
@@ -359,7 +364,7 @@ def run_reference(args, ws, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "3D 7-point Poisson 128^3 (n=2,097,152, nnz=14,581,760), RHS U[-1,1] seed 1; "
-                               "aggregation AMG (alpha 0.5, PMIS(2) seed 1, coarse <= 64) K-cycle preconditioner "
+                               "aggregation AMG (alpha 0.5, PMIS(2) seed 1, coarsest <= 600 rows) K-cycle preconditioner "
                                "in FP64 flexible CG to 1e-8: the FP64 CPU oracle (OpenMP timing build)"},
         "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": last["cores"], "kind": "oracle",
                          "sample": f"{args.steps} x oracle setup + FP64 FCG solve on the 128^3 workload itself, "
@@ -552,7 +557,8 @@ def main():
     stream = torch.cuda.current_stream(dev)
 
     def params(prec, **kw):
-        return amg.amg_default_params(alpha=ALPHA, seed=SEED, precision=PREC[prec], max_iter=500, **kw)
+        return amg.amg_default_params(alpha=ALPHA, seed=SEED, precision=PREC[prec], max_iter=500,
+                                      coarse_max=COARSE_MAX, **kw)
 
     stats = {}
 
@@ -759,7 +765,7 @@ def main():
             "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": PREC_DTYPE[prec], "data": "synthetic",
             "config": {"workload": "3D 7-point Poisson 128^3 (n=2,097,152, nnz=14,581,760), RHS U[-1,1] seed 1; "
-                                   "aggregation AMG (alpha 0.5, PMIS(2) seed 1, coarse <= 64) K-cycle "
+                                   "aggregation AMG (alpha 0.5, PMIS(2) seed 1, coarsest <= 600 rows) K-cycle "
                                    f"preconditioner ({prec} values/vectors) in FP64 flexible CG to 1e-8",
                        "step": "amg_setup + amg_solve + amg_free, inputs resident in HBM",
                        "l2": "inputs larger than L2 (level-0 FP64 CSR 175 MB > 129 MB)",
