@@ -1046,16 +1046,16 @@ __global__ void __launch_bounds__(256) k_arn_start(int32_t n, uint64_t seed, int
 template <bool LZ>
 __device__ __forceinline__ void arn_accumulate(double (&v)[kArnSlots], int j, int32_t n, int32_t i,
                                                const double *__restrict__ Q, double qi, double wi) {
-  if (LZ) {
+  if constexpr (LZ) {
     v[0] += qi * wi;
     v[1] += wi * wi;
-    return;
-  }
+  } else {
 #pragma unroll
-  for (int l = 0; l < kArnSlots; ++l) {  // static indices: the sums stay in registers
-    if (l < j) v[l] += Q[(size_t)l * n + i] * wi;
-    else if (l == j) v[l] += qi * wi;
-    else if (l == j + 1) v[l] += wi * wi;
+    for (int l = 0; l < kArnSlots; ++l) {  // static indices: the sums stay in registers
+      if (l < j) v[l] += Q[(size_t)l * n + i] * wi;
+      else if (l == j) v[l] += qi * wi;
+      else if (l == j + 1) v[l] += wi * wi;
+    }
   }
 }
 
@@ -1680,144 +1680,129 @@ __global__ void k_gj_inverse_batched(int32_t nsys, const int32_t *__restrict__ o
   gj_inverse_body(off[s + 1] - off[s], A + boff[s], Ainv + boff[s], err, gj_a);
 }
 
-// ---- grid barrier of a cooperative launch -----------------------------------
-struct GridBarrier {
-  unsigned count;  // blocks arrived at the current barrier
-  unsigned gen;    // barriers completed
-  int err;         // a block gave up waiting: every block returns
-};
-constexpr long long kBarrierSpin = 1LL << 24;  // polls (~40 ns apart) before a block gives up
-
-// all blocks of a cooperative launch, which are co-resident by construction;
-// false once any block gave up waiting (every wait is bounded)
-__device__ bool grid_barrier(GridBarrier *b) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned *gen = &b->gen;
-    const unsigned g = *gen;
-    __threadfence();
-    if (atomicAdd(&b->count, 1u) == gridDim.x - 1) {
-      atomicExch(&b->count, 0u);
-      __threadfence();
-      atomicAdd(&b->gen, 1u);
-    } else {
-      long long it = 0;
-      while (*gen == g) {
-        if (++it > kBarrierSpin || *(volatile int *)&b->err) {
-          atomicExch(&b->err, 1);
-          break;
-        }
-        __nanosleep(40);
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-  return *(volatile int *)&b->err == 0;
-}
-
 // ---- coarsest inverse across the GPU: blocked Gauss-Jordan --------------------
 // The sweeps of k_gj_inverse taken kGjb pivots at a time.  With the pivot block
 // P (rows and columns p0 .. p0 + kk) and B = M_PP^-1, one step is
 //   M_PP <- B,  M_Pj <- B M_Pj,  M_iP <- -M_iP B,  M_ij <- M_ij - M_iP B M_Pj
 // for i, j outside P; after the last block M = A^-1 (no pivoting: A is SPD, and
-// so is every pivot block).  One cooperative launch: a thread block owns whole
-// columns, inverts the kk x kk pivot block itself (the same arithmetic in every
-// block), and the steps alternate between two copies of the matrix with a grid
-// barrier between steps.  GB300 runs FP64 at ~2 multiply-adds per clock per SM,
-// so the n^3 multiply-adds of the inverse are spread over all SMs.
-// The matrix copies are read through L2 only (ld.cg): other blocks wrote them
-// in the previous step, and a block's L1 may still hold lines of an older step.
-// err: 1 a pivot block is not positive definite, 2 a barrier gave up.
+// so is every pivot block).  One launch per step, from src to dst (the launches
+// are chained by programmatic dependent launch): a thread block owns whole
+// columns and inverts the kk x kk pivot block itself, the same arithmetic in
+// every block.  GB300 runs FP64 at ~2 multiply-adds per clock per SM, so the n^3
+// multiply-adds of the inverse are spread over all SMs.
+// err = 1: a pivot block is not positive definite.
 constexpr int kGjb = 16;
 constexpr int32_t kGjOneBlock = 64;  // up to this size one block in shared memory is faster
 
-__global__ void __launch_bounds__(256) k_gj_blocked(int32_t n, const double *__restrict__ A, double *M0, double *M1,
-                                                    double *__restrict__ Ainv, GridBarrier *bar,
-                                                    int *__restrict__ err) {
+// 1/x in FP64 from an FP32 estimate and two Newton-Raphson steps
+// r <- r + r (1 - x r): the relative error squares each step (2^-24 -> 2^-48 ->
+// below FP64 rounding), so the result is within an ulp of 1/x; it is the same
+// in every block, which is all the sweeps need.  Outside the FP32 range the
+// division is taken as is.
+__device__ __forceinline__ double recip_nr(double x) {
+  const double ax = fabs(x);
+  if (!(ax > 1e-30 && ax < 1e30)) return 1.0 / x;
+  double r = (double)__frcp_rn((float)x);
+  r = fma(r, fma(-x, r, 1.0), r);
+  r = fma(r, fma(-x, r, 1.0), r);
+  return r;
+}
+
+__global__ void __launch_bounds__(256) k_gj_step(int32_t n, int32_t p0, const double *__restrict__ src,
+                                                 double *__restrict__ dst, int *__restrict__ err) {
   __shared__ double sB[kGjb][kGjb + 1];  // pivot block, inverted in place
   __shared__ double sW[kGjb];            // B M_Pj of the current column
-  __shared__ double sF[kGjb];            // multipliers of the current sweep
-  const int tid = threadIdx.x;
-  const int64_t nn = (int64_t)n * n;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + tid; t < nn; t += (int64_t)gridDim.x * blockDim.x) M0[t] = A[t];
-  if (!grid_barrier(bar)) {
-    if (tid == 0) *err = 2;
-    return;
-  }
-  const int nb = (n + kGjb - 1) / kGjb;
-  for (int st = 0; st < nb; ++st) {
-    const double *cur = (st & 1) ? M1 : M0;
-    double *nxt = (st & 1) ? M0 : M1;
-    const int32_t p0 = st * kGjb;
-    const int kk = min(kGjb, n - p0);
-    for (int t = tid; t < kk * kk; t += blockDim.x) sB[t / kk][t % kk] = __ldcg(cur + (int64_t)(p0 + t / kk) * n + p0 + t % kk);
-    __syncthreads();
-    for (int p = 0; p < kk; ++p) {  // unblocked sweeps of the pivot block
+  __shared__ int bad;                    // a pivot of the block was not positive
+  pdl_wait_and_trigger();
+  const int tid = threadIdx.x;           // 256 threads: one per entry of the pivot block
+  const int kk = min(kGjb, n - p0);
+  for (int t = tid; t < kk * kk; t += blockDim.x) sB[t / kk][t % kk] = src[(int64_t)(p0 + t / kk) * n + p0 + t % kk];
+  __syncthreads();
+  // unblocked sweeps of the pivot block, a thread per entry: every new value
+  // comes from the block before the sweep (the updates of k_gj_inverse, with the
+  // pivot's reciprocal from recip_nr), so that a sweep is one short chain of
+  // dependent FP64 operations and two barriers; FP64 latency, not throughput,
+  // sets the time of the 16 sweeps
+  if (tid == 0) bad = 0;
+  {
+    const int bi = tid / kGjb, bj = tid % kGjb;
+    const bool mine = bi < kk && bj < kk;
+    for (int p = 0; p < kk; ++p) {
       const double piv = sB[p][p];  // the same in every thread and every block
       if (!(piv > 0.0)) {
-        if (blockIdx.x == 0 && tid == 0) *err = 1;
-        return;  // every block stops here: no barrier is left waiting
+        if (tid == 0) bad = 1;
+        break;
       }
-      const double inv = 1.0 / piv;
-      if (tid < kk) sF[tid] = sB[tid][p] * inv;
+      const double inv = recip_nr(piv);
+      double v = 0.0;
+      if (mine) {
+        const double f = sB[bi][p] * inv;
+        if (bi != p && bj != p) v = fma(-f, sB[p][bj], sB[bi][bj]);
+        else if (bi == p && bj != p) v = sB[p][bj] * inv;
+        else if (bi != p) v = -f;
+        else v = inv;
+      }
       __syncthreads();
-      if (tid < kk * kk) {
-        const int i = tid / kk, j = tid % kk;
-        if (i != p && j != p) sB[i][j] = fma(-sF[i], sB[p][j], sB[i][j]);
-      }
+      if (mine) sB[bi][bj] = v;
       __syncthreads();
-      if (tid < kk && tid != p) {
-        sB[p][tid] *= inv;
-        sB[tid][p] = -sF[tid];
-      }
-      if (tid == 0) sB[p][p] = inv;
-      __syncthreads();
-    }
-    for (int32_t j = blockIdx.x; j < n; j += gridDim.x) {
-      if (j < p0 || j >= p0 + kk) {
-        if (tid < kk) {
-          double w = 0.0;
-          for (int m = 0; m < kk; ++m) w = fma(sB[tid][m], __ldcg(cur + (int64_t)(p0 + m) * n + j), w);
-          sW[tid] = w;
-        }
-        __syncthreads();
-        for (int32_t i = tid; i < n; i += blockDim.x) {
-          double v;
-          if (i >= p0 && i < p0 + kk) {
-            v = sW[i - p0];
-          } else {
-            const double *aip = cur + (int64_t)i * n + p0;
-            v = __ldcg(cur + (int64_t)i * n + j);
-            for (int l = 0; l < kk; ++l) v = fma(-__ldcg(aip + l), sW[l], v);
-          }
-          nxt[(int64_t)i * n + j] = v;
-        }
-      } else {
-        const int c = j - p0;
-        for (int32_t i = tid; i < n; i += blockDim.x) {
-          double v;
-          if (i >= p0 && i < p0 + kk) {
-            v = sB[i - p0][c];
-          } else {
-            const double *aip = cur + (int64_t)i * n + p0;
-            v = 0.0;
-            for (int l = 0; l < kk; ++l) v = fma(__ldcg(aip + l), sB[l][c], v);
-            v = -v;
-          }
-          nxt[(int64_t)i * n + j] = v;
-        }
-      }
-      __syncthreads();  // sW is rewritten by the next column
-    }
-    if (!grid_barrier(bar)) {
-      if (tid == 0) *err = 2;
-      return;
     }
   }
-  const double *fin = (nb & 1) ? M1 : M0;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + tid; t < nn; t += (int64_t)gridDim.x * blockDim.x)
-    Ainv[t] = __ldcg(fin + t);
+  __syncthreads();
+  if (bad) {  // the same in every block
+    if (blockIdx.x == 0 && tid == 0) *err = 1;
+    return;
+  }
+  for (int32_t j = blockIdx.x; j < n; j += gridDim.x) {
+    if (j < p0 || j >= p0 + kk) {
+      if (tid < kk) {  // the kGjb loads go out together (a short last block reads zeros)
+        double pc[kGjb];
+#pragma unroll
+        for (int m = 0; m < kGjb; ++m) pc[m] = m < kk ? src[(int64_t)(p0 + m) * n + j] : 0.0;
+        double w = 0.0;
+#pragma unroll
+        for (int m = 0; m < kGjb; ++m)
+          if (m < kk) w = fma(sB[tid][m], pc[m], w);
+        sW[tid] = w;
+      }
+      __syncthreads();
+      for (int32_t i = tid; i < n; i += blockDim.x) {
+        double v;
+        if (i >= p0 && i < p0 + kk) {
+          v = sW[i - p0];
+        } else {
+          const double *aip = src + (int64_t)i * n + p0;
+          double a[kGjb];
+#pragma unroll
+          for (int l = 0; l < kGjb; ++l) a[l] = l < kk ? aip[l] : 0.0;
+          v = src[(int64_t)i * n + j];
+#pragma unroll
+          for (int l = 0; l < kGjb; ++l)
+            if (l < kk) v = fma(-a[l], sW[l], v);
+        }
+        dst[(int64_t)i * n + j] = v;
+      }
+    } else {
+      const int c = j - p0;
+      for (int32_t i = tid; i < n; i += blockDim.x) {
+        double v;
+        if (i >= p0 && i < p0 + kk) {
+          v = sB[i - p0][c];
+        } else {
+          const double *aip = src + (int64_t)i * n + p0;
+          double a[kGjb];
+#pragma unroll
+          for (int l = 0; l < kGjb; ++l) a[l] = l < kk ? aip[l] : 0.0;
+          v = 0.0;
+#pragma unroll
+          for (int l = 0; l < kGjb; ++l)
+            if (l < kk) v = fma(a[l], sB[l][c], v);
+          v = -v;
+        }
+        dst[(int64_t)i * n + j] = v;
+      }
+    }
+    __syncthreads();  // sW is rewritten by the next column
+  }
 }
 
 __global__ void k_gather_i32(int32_t n, const int32_t *__restrict__ idx, const int32_t *__restrict__ src,
@@ -2419,34 +2404,22 @@ void finish_levels(Hierarchy &h, cudaStream_t s, bool fresh) {
       const size_t sm = sizeof(double) * ((size_t)Lc.n * Lc.n + Lc.n);
       AMG_CUDA(cudaFuncSetAttribute(k_gj_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
       AMG_COUNT(), klaunch_sm(k_gj_inverse, 1, 1024, sm, s, Lc.n, (const double *)dense.p, h.coarse_inv, err.p);
-    } else if (p.symmetric) {  // blocked sweeps over the whole GPU, one cooperative launch
+    } else if (p.symmetric) {  // blocked sweeps over the whole GPU, one launch per 16 pivots
       DevBuf<double> m1((size_t)Lc.n * Lc.n);
-      DevBuf<GridBarrier> bar(1);
-      AMG_CUDA(cudaMemsetAsync(bar.p, 0, sizeof(GridBarrier), s));
-      int dev = 0, sms = 0, per = 0;
-      AMG_CUDA(cudaGetDevice(&dev));
-      AMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-      AMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_gj_blocked, 256, 0));
-      cudaLaunchConfig_t cfg{};
-      cfg.gridDim = std::max(1, std::min(per * sms, Lc.n));  // a block per column at most
-      cfg.blockDim = 256;
-      cfg.stream = s;
-      cudaLaunchAttribute at[1];
-      at[0].id = cudaLaunchAttributeCooperative;
-      at[0].val.cooperative = 1;
-      cfg.attrs = at;
-      cfg.numAttrs = 1;
-      AMG_COUNT();
-      AMG_CUDA(cudaLaunchKernelEx(&cfg, k_gj_blocked, Lc.n, (const double *)dense.p, dense.p, m1.p, h.coarse_inv,
-                                  bar.p, err.p));
+      const int nb = (Lc.n + kGjb - 1) / kGjb;
+      const int grid = std::min(Lc.n, 152 * 4);  // a block per column, up to four waves of SMs
+      const double *src = dense.p;
+      for (int st = 0; st < nb; ++st) {  // the last step writes the inverse itself
+        double *dst = (nb - 1 - st) % 2 == 0 ? h.coarse_inv : m1.p;
+        AMG_COUNT(), klaunch_sm(k_gj_step, grid, 256, 0, s, Lc.n, st * kGjb, src, dst, err.p);
+        src = dst;
+      }
     } else {
       DevBuf<double> fac(Lc.n);
       AMG_COUNT(), klaunch_sm(k_lu_inverse, 1, 1024, 0, s, Lc.n, dense.p, h.coarse_inv, fac.p, err.p);
     }
     AMG_LAUNCH_CHECK();
-    const int e = read_scalar(err.p, s);
-    if (e == 2) throw Error{AMG_ERR_CUDA, "coarsest inverse: a grid barrier timed out"};
-    if (e)
+    if (read_scalar(err.p, s))
       throw Error{AMG_ERR_SETUP, p.symmetric ? "coarsest level matrix is not positive definite"
                                              : "coarsest level matrix is singular"};
   }

@@ -92,8 +92,8 @@ def test_preconditioner_parity(gpu, orc, name):
                                        ("poisson3d_20", 600)])
 def test_large_coarsest_level(gpu, orc, name, cmax):
     """A coarsest level of more than 64 rows (the paper keeps about 600 on the
-    GPU, Sec. 3): its inverse comes from the blocked Gauss-Jordan sweeps of one
-    cooperative launch over the whole GPU.  Same hierarchy as the oracle (whose
+    GPU, Sec. 3): its inverse comes from the blocked Gauss-Jordan sweeps spread
+    over the whole GPU, one launch per 16 pivots.  Same hierarchy as the oracle (whose
     coarsest solve is a Cholesky factorisation), preconditioner to 1e-11 and six
     outer iterations to 1e-10."""
     A, g, o = pair(gpu, orc, name, coarse_max=cmax, max_iter=6)
