@@ -808,7 +808,8 @@ or_hier *or_setup(int32_t n, const int32_t *rp, const int32_t *ci, const double 
       or_free(h);
       return NULL;
     }
-    /* reading of "until n_L is small": also stop when coarsening stalls */
+    /* the stopping rule (coarsen while the coarse system is too large for a
+       direct solve): also stop when coarsening stalls */
     if (10LL * nc >= 9LL * nk) {
       free(agg);
       break;
