@@ -91,11 +91,12 @@ typedef struct amg_params {
                             (and, for a batch, the row tile of the per-system inner
                             products) and keep the fastest; the choice is reported in
                             amg_level_info.  Changes rounding order only                  */
-  int32_t symmetric;     /* 1: A is symmetric (omega from the symmetric part of the
-                            Arnoldi matrix, Cholesky coarsest factor).  0: nonsymmetric
-                            (omega from the eigenvalues of the Arnoldi Hessenberg matrix,
-                            LU coarsest factor); needs outer = 1 (FGMRES, Sec. 2.2) and
-                            a single system                                                */
+  int32_t symmetric;     /* 1: A is symmetric (omega from the Lanczos form of the
+                            Arnoldi process; coarsest inverse by Gauss-Jordan sweeps
+                            without pivoting, A_L being SPD).  0: nonsymmetric (omega
+                            from the eigenvalues of the Arnoldi Hessenberg matrix;
+                            coarsest inverse with partial pivoting); needs outer = 1
+                            (FGMRES, Sec. 2.2) and a single system                        */
   int32_t mis_k;         /* aggregate roots form an MIS(k), 1..8: 2 is the paper's PMIS(2)
                             (Alg. 2); k > 2 coarsens more aggressively (Sec. 2.1.2): k max
                             rounds per PMIS iteration, aggregates reach distance k        */
@@ -135,7 +136,7 @@ void amg_default_params(amg_params *p);
 /* Alg. 1: build the hierarchy of A on the GPU.
  * Per level: strength (Sec. 2.1.1), PMIS(2) (Alg. 2), aggregation (Sec. 2.1.2),
  * interpolation (Alg. 3), Galerkin keyed sum (Sec. 3.1), omega (Eq. damped
- * Jacobi), and finally the dense factorisation of the coarsest level (the paper
+ * Jacobi), and finally the dense inverse of the coarsest level (the paper
  * uses SuperLU there, Sec. 3).  The aggregates, interpolation weights and coarse
  * matrices are bit-identical to a sequential FP64 evaluation of those steps.
  * Returns AMG_ERR_BAD_INPUT for a malformed CSR or zero diagonal, AMG_ERR_SETUP
