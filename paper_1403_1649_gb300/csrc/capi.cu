@@ -559,7 +559,7 @@ int amg_validate_hierarchy(const amg_hierarchy *H) {
       for (int32_t c : ci) expect(c >= 0 && c < L.n, k, "column out of range");
       auto sp = fetch(L.sptr, (size_t)L.nslices + 1);
       expect(sp[0] == 0 && sp[L.nslices] == L.sell_entries, k, "SELL pointer ends");
-      const int64_t unit = L.spair ? 64 : 32;  // pairs: slice widths are even
+      const int64_t unit = h.p.precision != AMG_PREC_F64 ? 64 : 32;  // pairs: slice widths are even
       for (int32_t q = 0; q < L.nslices; ++q)
         expect(sp[q] <= sp[q + 1] && (sp[q + 1] - sp[q]) % unit == 0, k, "SELL slice");
       if (L.spair) {  // {column, value bits} pairs: the columns are the even words

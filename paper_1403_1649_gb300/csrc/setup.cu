@@ -905,6 +905,8 @@ template <> __device__ __forceinline__ double back_to_double<__nv_bfloat16>(__nv
 // over the row's off-diagonals, in FP64 then rounded once to FP32.
 // spair (FP32 values only): the entries go to the pair layout instead of scol /
 // sval, entry e of the lane as half (e & 1) of int4 sptr[sl] / 2 + 32 (e / 2) + lane.
+// BF16 values: entry e of the lane at sptr[sl] + 64 (e / 2) + 2 lane + (e & 1) of
+// scol / sval (slice widths even).
 template <class MV>
 __global__ void k_build_sell(int32_t n, int32_t nslices, const int32_t *__restrict__ rp,
                              const int32_t *__restrict__ ci, const double *__restrict__ val,
@@ -927,7 +929,10 @@ __global__ void k_build_sell(int32_t n, int32_t nslices, const int32_t *__restri
         return;
       }
     }
-    const int64_t at = base + (int64_t)e * kSlice + lane;
+    // BF16: a lane's entries 2j and 2j+1 adjacent in both arrays
+    const int64_t at = std::is_same<MV, __nv_bfloat16>::value
+                           ? base + (int64_t)(e >> 1) * (2 * kSlice) + 2 * lane + (e & 1)
+                           : base + (int64_t)e * kSlice + lane;
     scol[at] = c;
     sval[at] = m;
   };
@@ -1996,18 +2001,19 @@ void build_solve_matrix(Hierarchy &h, Level &L, cudaStream_t s, bool fresh) {
   const int32_t n = L.n;
   L.nslices = (n + kSlice - 1) / kSlice;
   const unsigned g = blocks_for((int64_t)L.nslices * 32);
-  // pairs: FP32 values, stored with their columns in L.spair (no scol / sval)
+  // pairs: entries two by two, slice widths even (FP32: stored with their
+  // columns in L.spair, no scol / sval; BF16: adjacent in scol and sval)
   auto layout = [&](bool split, bool pairs, int64_t *&sptr, int32_t *&scol, int64_t &entries) {
     DevBuf<int64_t> w32(L.nslices + 1);
     AMG_COUNT(), klaunch_sm(k_slice_width, g, 256, 0, s, n, L.nslices, L.rp, L.ci, split, pairs, w32.p);
     AMG_LAUNCH_CHECK();
     sptr = h.arena.get<int64_t>(L.nslices + 1);
     exclusive_scan<int64_t, int64_t>(w32.p, sptr, L.nslices, s, &entries);
-    if (pairs) L.spair = h.arena.get<int4>(entries / 2);
+    if (pairs && h.p.precision == AMG_PREC_F32) L.spair = h.arena.get<int4>(entries / 2);
     else scol = h.arena.get<int32_t>(entries);
   };
   const bool split = h.p.precision != AMG_PREC_F64;
-  if (fresh) layout(split, h.p.precision == AMG_PREC_F32, L.sptr, L.scol, L.sell_entries);
+  if (fresh) layout(split, split, L.sptr, L.scol, L.sell_entries);
   const int64_t entries = L.sell_entries;
   if (fresh && split) L.sdiag = h.arena.get<float>(n);
   switch (h.p.precision) {

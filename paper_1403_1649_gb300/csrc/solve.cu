@@ -69,8 +69,11 @@ enum Epi { E_Y = 0, E_RESID = 1, E_POST = 2, E_DSCALE = 3, E_POLYPRE = 4, E_RESI
            E_HORNER_LAST = 7 };
 
 template <class MV> __device__ __forceinline__ MV ld_stream(const MV *p) { return __ldcs(p); }
-// FP32 matrices are stored as {column, value} pairs (Level::spair)
+// FP32 matrices are stored as {column, value} pairs (Level::spair); BF16
+// matrices keep separate column and value arrays with a lane's entries 2j and
+// 2j+1 adjacent in each (one 8-byte column load, one 4-byte value load)
 template <class MV> constexpr bool kPairs = std::is_same<MV, float>::value;
+template <class MV> constexpr bool kHalfPairs = std::is_same<MV, __nv_bfloat16>::value;
 
 // per-block partial sums of up to three dot products -> partials[k*kRedBlocks + block]
 __device__ __forceinline__ void block_store_dots3(double a0, double a1, double a2, int ndot, double *partials) {
@@ -182,11 +185,14 @@ __global__ void __launch_bounds__(kThreads, UW ? 1 : sell_launch_blocks<MV, VT, 
     // otherwise the split diagonal (FP32 / BF16 values only) and x_row are loaded
     // right behind the first step's matrix loads, so that their latency overlaps
     // the gathers
-    if constexpr (kPairs<MV>) {
-      // FP32 values: a lane's entries 2j and 2j+1 come in one 16-byte load
-      // (widths are even, U is even).  FULL: all U entries of the step exist
+    if constexpr (kPairs<MV> || kHalfPairs<MV>) {
+      // FP32 values: a lane's entries 2j and 2j+1 come in one 16-byte load;
+      // BF16 values: their columns in one 8-byte load and their values in one
+      // 4-byte load (widths are even, U is even).  FULL: all U entries exist
       static_assert(U % 2 == 0, "pairs need an even step");
       const int4 *__restrict__ pp = a.spair + (base >> 1) + lane;
+      const int2 *__restrict__ cp2 = reinterpret_cast<const int2 *>(a.scol + base) + lane;
+      const __nv_bfloat162 *__restrict__ vp2 = reinterpret_cast<const __nv_bfloat162 *>(sval + base) + lane;
       auto step = [&](int32_t e, auto full) {
         constexpr bool FULL = decltype(full)::value;
         int32_t c[U];
@@ -194,11 +200,20 @@ __global__ void __launch_bounds__(kThreads, UW ? 1 : sell_launch_blocks<MV, VT, 
 #pragma unroll
         for (int q = 0; q < U; q += 2) {
           if (FULL || e + q < width) {
-            const int4 pr = ld_stream(pp + 16 * (e + q));
-            c[q] = pr.x;
-            v[q] = __int_as_float(pr.y);
-            c[q + 1] = pr.z;
-            v[q + 1] = __int_as_float(pr.w);
+            if constexpr (kPairs<MV>) {
+              const int4 pr = ld_stream(pp + 16 * (e + q));
+              c[q] = pr.x;
+              v[q] = __int_as_float(pr.y);
+              c[q + 1] = pr.z;
+              v[q + 1] = __int_as_float(pr.w);
+            } else {
+              const int2 cc = ld_stream(cp2 + 16 * (e + q));
+              const float2 vv = __bfloat1622float2(ld_stream(vp2 + 16 * (e + q)));
+              c[q] = cc.x;
+              c[q + 1] = cc.y;
+              v[q] = vv.x;
+              v[q + 1] = vv.y;
+            }
           }
         }
         if (UW == 0 && e == 0 && diag) {

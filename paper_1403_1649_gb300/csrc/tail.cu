@@ -94,6 +94,16 @@ __device__ __forceinline__ VT sell_row(const TailLevel &L, int32_t sl, int lane,
           cc[q + 1] = pr.z;
           vv[q + 1] = __int_as_float(pr.w);
         }
+    } else if constexpr (std::is_same<MV, __nv_bfloat16>::value) {  // entries 2j, 2j+1 adjacent
+#pragma unroll
+      for (int q = 0; q < 4; q += 2)
+        if (e + q < width) {
+          const int64_t at = base + 32 * (int64_t)(e + q) + 2 * lane;
+          cc[q] = L.scol[at];
+          cc[q + 1] = L.scol[at + 1];
+          vv[q] = static_cast<const MV *>(L.sval)[at];
+          vv[q + 1] = static_cast<const MV *>(L.sval)[at + 1];
+        }
     } else {
 #pragma unroll
       for (int q = 0; q < 4; ++q)
