@@ -134,6 +134,8 @@ def workload_results(name: str, reps: int = 1):
                               "(compensated FP32 diagonal) / FP32 vectors vs FP64, to 1e-8",
                   "headline": "flexible CG with the BF16 preconditioner (FGMRES(30) stalls on this "
                               "problem: see fgmres30_* final_relres after 600 iterations)"}
+        # level-0 SpMV of the headline (BF16) preconditioner: 2 x 197 MB > L2
+        res["level0_spmv_bf16"] = level0_spmv_roofline(A, "bf16", 2, alpha=0.5, seed=2, coarse_max=COARSE_MAX)
         head = res["fcg_bf16"]
         return A.n / (head["ms"] / 1e3), head["ms"], "bf16+f32+f64", config, res
     if name == "fem2d_1024":
@@ -154,6 +156,8 @@ def workload_results(name: str, reps: int = 1):
                               "omega=2/3, flexible CG to 1e-8",
                   "training": f"150 Adam steps on 4 two-level FEM problems (48^2..96^2), {train_s:.2f} s, "
                               f"two-grid factor {hist[0]:.4f} -> {hist[-1]:.4f}"}
+        # level-0 SpMV of the FP32 preconditioner: 4 x 67 MB > L2
+        res["level0_spmv_f32"] = level0_spmv_roofline(A, "f32", 4, alpha=0.25, seed=3, coarse_max=COARSE_MAX)
         head = res["learned_f32"]
         return A.n / (head["ms"] / 1e3), head["ms"], "f32+f64", config, res
     # batch512
@@ -507,6 +511,67 @@ def source_hash() -> str:
     return hashlib.sha256(text[a:b].encode()).hexdigest()[:16]
 
 
+def level0_spmv_roofline(A, prec: str, copies: int, **pk):
+    """Level-0 SELL SpMV of the preconditioner in precision prec on GPU 0:
+    `copies` hierarchies of A (together larger than L2) take turns in 40
+    back-to-back launches captured in one CUDA graph, so that every launch reads
+    its matrix from HBM and none waits for the host; median of 7 replays (CUDA
+    events).  Returns the roofline record (algorithmic bytes / launch time)."""
+    import torch
+    from paper_1403_1649_gb300 import amg
+    dev = torch.device("cuda", 0)
+    rp, ci, va = (torch.from_numpy(a).to(dev) for a in (A.rowptr, A.col, A.val))
+    n, nnz = A.n, A.nnz
+    hs = [amg.amg_setup(rp, ci, va, amg.amg_default_params(precision=PREC[prec], **pk)) for _ in range(copies)]
+    vt = torch.float64 if prec == "f64" else torch.float32
+    xs = [torch.rand(n, dtype=vt, device=dev) for _ in range(copies)]
+    ys = [torch.empty_like(x) for x in xs]
+    reps = 40
+    torch.cuda.synchronize()
+    cap = torch.cuda.Stream()  # graph capture needs a stream other than the legacy default
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=cap, capture_error_mode="relaxed"):
+        for r in range(reps):
+            amg.amg_spmv(hs[r % copies], 0, xs[r % copies], ys[r % copies], cap.cuda_stream)
+    with torch.cuda.stream(cap):
+        graph.replay()
+    torch.cuda.synchronize()
+    durs = []
+    for _ in range(7):
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(cap):
+            s0.record(cap)
+            graph.replay()
+            s1.record(cap)
+        s1.synchronize()
+        durs.append(s0.elapsed_time(s1) / 1e3 / reps)
+    del graph
+    for hh in hs:
+        amg.amg_free(hh)
+    alg_bytes = spmv_bytes(n, nnz, prec)
+    t_avg = float(np.median(durs))
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    achieved = alg_bytes / t_avg / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "kernel": f"k_sell level-0 SpMV ({prec} values, SELL-32)", "algorithmic_bytes": alg_bytes,
+            "avg_launch_us": t_avg * 1e6,
+            "timing": f"median of 7 graph replays of 40 back-to-back launches over {copies} hierarchies "
+                      f"(CUDA events)",
+            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs, burst)" if peaks else "fallback"}
+
+
+def spmv_bytes(n: int, nnz: int, prec: str) -> int:
+    """Bytes the SELL-32 SpMV must move: the entries (index + value; in FP32 / BF16
+    the diagonal is split off into an FP32 vector), slice pointers, x and y."""
+    vb = {"f64": 8, "f32": 4, "bf16": 2}[prec]
+    xb = 8 if prec == "f64" else 4
+    slices = (n + 31) // 32
+    if prec == "f64":
+        return nnz * 12 + 8 * (slices + 1) + 2 * xb * n
+    return (nnz - n) * (4 + vb) + 4 * n + 8 * (slices + 1) + 2 * xb * n
+
+
 def ncu_traffic(precision: str):
     """dram bytes per launch of the level-0 SpMV from the committed ncu summary,
     only if it was taken on the current kernel source."""
@@ -684,15 +749,7 @@ def main():
         del graph
         for hh in hs:
             amg.amg_free(hh)
-        vb = {"f64": 8, "f32": 4, "bf16": 2}[prec]
-        xb = 8 if prec == "f64" else 4
-        # bytes the SELL-32 SpMV must move: stored entries (index + value; in FP32 /
-        # BF16 the diagonal is split off into an FP32 vector), slice pointers, x, y
-        slices = (n + 31) // 32
-        if prec == "f64":
-            alg_bytes = nnz * 12 + 8 * (slices + 1) + 2 * xb * n
-        else:
-            alg_bytes = (nnz - n) * (4 + vb) + 4 * n + 8 * (slices + 1) + 2 * xb * n
+        alg_bytes = spmv_bytes(n, nnz, prec)
         t_avg = float(np.median(durs))
         t_single = float(np.median(single))
         peaks = measured_peaks()
