@@ -193,12 +193,13 @@ __global__ void __launch_bounds__(kThreads, UW ? 1 : sell_launch_blocks<MV, VT, 
       const int4 *__restrict__ pp = a.spair + (base >> 1) + lane;
       const int2 *__restrict__ cp2 = reinterpret_cast<const int2 *>(a.scol + base) + lane;
       const __nv_bfloat162 *__restrict__ vp2 = reinterpret_cast<const __nv_bfloat162 *>(sval + base) + lane;
-      auto step = [&](int32_t e, auto full) {
+      auto step = [&](int32_t e, auto full, auto size) {
         constexpr bool FULL = decltype(full)::value;
-        int32_t c[U];
-        float v[U];
+        constexpr int S = decltype(size)::value;  // entries of this step
+        int32_t c[S];
+        float v[S];
 #pragma unroll
-        for (int q = 0; q < U; q += 2) {
+        for (int q = 0; q < S; q += 2) {
           if (FULL || e + q < width) {
             if constexpr (kPairs<MV>) {
               const int4 pr = ld_stream(pp + 16 * (e + q));
@@ -220,20 +221,24 @@ __global__ void __launch_bounds__(kThreads, UW ? 1 : sell_launch_blocks<MV, VT, 
           dg = (VT)ld_stream(a.sdiag + row);
           xr = __ldg(a.x + row);
         }
-        VT xv[U];
+        VT xv[S];
 #pragma unroll
-        for (int q = 0; q < U; ++q)
+        for (int q = 0; q < S; ++q)
           if (FULL || e + q < width) xv[q] = __ldg(a.x + c[q]);
 #pragma unroll
-        for (int q = 0; q < U; ++q)
+        for (int q = 0; q < S; ++q)
           if (FULL || e + q < width) y += v[q] * xv[q];
       };
-      // the common slice (a 7-point row: one full step) takes the step without
-      // predicates, whose loads all go out before the first gather
+      // a slice of U or U + 2 entries a row (a 7-point row, a P1 FEM row) takes
+      // one step without predicates, whose loads all go out before the first gather
+      using UStep = std::integral_constant<int, U>;
+      using U2Step = std::integral_constant<int, U + 2>;
       if (UW == 0 && width == U) {
-        step(0, std::true_type{});
+        step(0, std::true_type{}, UStep{});
+      } else if (UW == 0 && width == U + 2) {
+        step(0, std::true_type{}, U2Step{});
       } else {
-        for (int32_t e = 0; e < width; e += U) step(e, std::false_type{});
+        for (int32_t e = 0; e < width; e += U) step(e, std::false_type{}, UStep{});
       }
     } else {
       const int32_t *__restrict__ cp = a.scol + base + lane;
