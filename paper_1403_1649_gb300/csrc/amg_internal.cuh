@@ -229,6 +229,7 @@ struct Hierarchy {
   int L = 0;
   // batched mode: nsys independent systems in one block-diagonal hierarchy
   bool batched = false;
+  bool sym_pattern = false;  // A_0 is structurally symmetric (found on level 0)
   int nsys = 1;
   double *binv = nullptr;        // coarsest level: per-system dense inverses, back to back
   int64_t *binv_off = nullptr;   // nsys+1 offsets into binv

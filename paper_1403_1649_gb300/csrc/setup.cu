@@ -1896,12 +1896,21 @@ Coarsening coarsen_level(Hierarchy &h, int k, cudaStream_t s, int32_t *agg_out, 
     AMG_CUDA(cudaMemsetAsync(nonsym.p, 0, sizeof(int), s));
     AMG_COUNT(), klaunch_sm(k_sym_mirror, grid_for(n, 256), 256, 0, s, n, L.rp, L.ci, C.p, S.p, ucount.p, nonsym.p);
     AMG_LAUNCH_CHECK();
-    // the flag rides on the scan's synchronisation
+    // The coarse levels of a structurally symmetric A_0 are structurally
+    // symmetric (P^T A P keeps the pattern's symmetry): no flag to read, and the
+    // graph is sized by the pattern instead of its count (no synchronisation).
+    // Otherwise the flag rides on the scan's synchronisation.
+    const bool known_sym = k > 0 && h.sym_pattern;
     int32_t *flag_host = reinterpret_cast<int32_t *>(h.host_pinned + kPinnedSetupFlags);
-    AMG_CUDA(cudaMemcpyAsync(flag_host, nonsym.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-    exclusive_scan<int32_t, int32_t>(ucount.p, Sptr.p, n, s, &ns);
-    if (!*flag_host) {
-      Scol.resize((size_t)ns + 1);
+    if (known_sym) {
+      exclusive_scan<int32_t, int32_t>(ucount.p, Sptr.p, n, s);
+    } else {
+      AMG_CUDA(cudaMemcpyAsync(flag_host, nonsym.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+      exclusive_scan<int32_t, int32_t>(ucount.p, Sptr.p, n, s, &ns);
+      if (k == 0) h.sym_pattern = !*flag_host;
+    }
+    if (known_sym || !*flag_host) {
+      Scol.resize(known_sym ? (size_t)nnz + 1 : (size_t)ns + 1);
       AMG_COUNT(), klaunch_sm(k_sym_mirror_fill, grid_for(n, 256), 256, 0, s, n, L.rp, L.ci, S.p, Sptr.p, Scol.p);
       AMG_LAUNCH_CHECK();
     } else {  // general pattern: collect C rows and transposed entries, sort, deduplicate
