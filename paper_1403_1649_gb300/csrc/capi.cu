@@ -90,7 +90,7 @@ double *pinned_scratch_get() {
     }
   }
   double *p = nullptr;
-  AMG_CUDA(cudaMallocHost(&p, 64 * sizeof(double)));
+  AMG_CUDA(cudaMallocHost(&p, 128 * sizeof(double)));  // layout: see kPinnedSetupFlags
   return p;
 }
 void pinned_scratch_put(double *p) {

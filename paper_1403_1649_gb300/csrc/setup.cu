@@ -1851,10 +1851,13 @@ __global__ void k_fill_f64(int64_t n, double *p, double v) {
 // ============================================================== host side
 namespace {
 
-// host_pinned (64 doubles): ints [0, 2) PMIS round counts, doubles [0, levels)
+// host_pinned (128 doubles): ints [0, 2) PMIS round counts, doubles [0, levels)
 // omega read-back, ints at double offset 40: setup flags (symmetry, aggregation
-// error), read at the next synchronisation
+// error), read at the next synchronisation; int64 at double offset 64: the SELL
+// entry counts of the levels (slot kMaxLevels: level 0's FP64 copy)
 constexpr int kPinnedSetupFlags = 40;
+constexpr int kPinnedSellEntries = 64;
+static_assert(kPinnedSellEntries + kMaxLevels + 1 <= 128, "pinned scratch holds 128 doubles");
 
 template <class T>
 T read_scalar(const T *dev, cudaStream_t s) {
@@ -2002,27 +2005,53 @@ Coarsening coarsen_level(Hierarchy &h, int k, cudaStream_t s, int32_t *agg_out, 
   return out;
 }
 
-// SELL-32 of level L: the preconditioner's matrix in its precision and, on
-// level 0, every entry in FP64 for the outer iteration
-// fresh: lay out and allocate; otherwise refill the values of the existing
-// layout (values-only re-setup, same pattern)
-void build_solve_matrix(Hierarchy &h, Level &L, cudaStream_t s, bool fresh) {
-  const int32_t n = L.n;
-  L.nslices = (n + kSlice - 1) / kSlice;
-  const unsigned g = blocks_for((int64_t)L.nslices * 32);
-  // pairs: entries two by two, slice widths even (FP32: stored with their
-  // columns in L.spair, no scol / sval; BF16: adjacent in scol and sval)
-  auto layout = [&](bool split, bool pairs, int64_t *&sptr, int32_t *&scol, int64_t &entries) {
+// SELL-32 layouts (slice pointers, index arrays) of every level: the slice
+// widths and their scans of all levels are queued first, and one
+// synchronisation reads every level's entry count (pinned words from
+// kPinnedSellEntries on) before the arrays are allocated.
+// pairs: entries two by two, slice widths even (FP32: stored with their
+// columns in L.spair, no scol / sval; BF16: adjacent in scol and sval)
+void layout_all(Hierarchy &h, cudaStream_t s) {
+  const bool split = h.p.precision != AMG_PREC_F64;
+  auto *ent = reinterpret_cast<int64_t *>(h.host_pinned + kPinnedSellEntries);
+  auto widths = [&](Level &L, bool pairs, int64_t *&sptr, int slot) {
     DevBuf<int64_t> w32(L.nslices + 1);
-    AMG_COUNT(), klaunch_sm(k_slice_width, g, 256, 0, s, n, L.nslices, L.rp, L.ci, split, pairs, w32.p);
+    AMG_COUNT(), klaunch_sm(k_slice_width, blocks_for((int64_t)L.nslices * 32), 256, 0, s, L.n, L.nslices, L.rp,
+        L.ci, pairs ? split : false, pairs, w32.p);
     AMG_LAUNCH_CHECK();
     sptr = h.arena.get<int64_t>(L.nslices + 1);
-    exclusive_scan<int64_t, int64_t>(w32.p, sptr, L.nslices, s, &entries);
-    if (pairs && h.p.precision == AMG_PREC_F32) L.spair = h.arena.get<int4>(entries / 2);
-    else scol = h.arena.get<int32_t>(entries);
+    exclusive_scan<int64_t, int64_t>(w32.p, sptr, L.nslices, s);
+    AMG_CUDA(cudaMemcpyAsync(ent + slot, sptr + L.nslices, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   };
+  for (int q = 0; q < h.L; ++q) {
+    Level &L = h.lev[q];
+    L.nslices = (L.n + kSlice - 1) / kSlice;
+    widths(L, split, L.sptr, q);
+  }
+  if (split) widths(h.lev[0], false, h.lev[0].sptr64, kMaxLevels);  // every entry in FP64
+  AMG_CUDA(cudaStreamSynchronize(s));
+  for (int q = 0; q < h.L; ++q) {
+    Level &L = h.lev[q];
+    L.sell_entries = ent[q];
+    if (h.p.precision == AMG_PREC_F32) L.spair = h.arena.get<int4>(L.sell_entries / 2);
+    else L.scol = h.arena.get<int32_t>(L.sell_entries);
+  }
+  if (split) {
+    Level &L0 = h.lev[0];
+    L0.sell64_entries = ent[kMaxLevels];
+    L0.scol64 = h.arena.get<int32_t>(L0.sell64_entries);
+    L0.sval64 = h.arena.get<double>(L0.sell64_entries);
+  }
+}
+
+// SELL-32 of level L: the preconditioner's matrix in its precision and, on
+// level 0, every entry in FP64 for the outer iteration (layouts from
+// layout_all).  fresh: allocate the value arrays; otherwise refill the values
+// of the existing layout (values-only re-setup, same pattern)
+void build_solve_matrix(Hierarchy &h, Level &L, cudaStream_t s, bool fresh) {
+  const int32_t n = L.n;
+  const unsigned g = blocks_for((int64_t)L.nslices * 32);
   const bool split = h.p.precision != AMG_PREC_F64;
-  if (fresh) layout(split, split, L.sptr, L.scol, L.sell_entries);
   const int64_t entries = L.sell_entries;
   if (fresh && split) L.sdiag = h.arena.get<float>(n);
   switch (h.p.precision) {
@@ -2043,10 +2072,6 @@ void build_solve_matrix(Hierarchy &h, Level &L, cudaStream_t s, bool fresh) {
   AMG_LAUNCH_CHECK();
   if (&L != &h.lev[0]) return;
   if (split) {
-    if (fresh) {
-      layout(false, false, L.sptr64, L.scol64, L.sell64_entries);
-      L.sval64 = h.arena.get<double>(L.sell64_entries);
-    }
     AMG_COUNT(), klaunch_sm(k_build_sell<double>, g, 256, 0, s, n, L.nslices, L.rp, L.ci, L.val, L.sptr64, L.scol64,
         L.sval64, nullptr, nullptr);
     AMG_LAUNCH_CHECK();
@@ -2336,6 +2361,7 @@ void finish_levels(Hierarchy &h, cudaStream_t s, bool fresh) {
   DevBuf<double> Hs((size_t)kMaxLevels * 72), wns((size_t)kMaxLevels * 8);
   OmegaJobs jobs{};
   int nj = 0;
+  if (fresh) layout_all(h, s);
   for (int q = 0; q < h.L; ++q) {
     Level &L = h.lev[q];
     build_solve_matrix(h, L, s, fresh);
